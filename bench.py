@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Benchmark: ray-bounce queries/s of the batched ray-propagation path.
+
+Workload: the procedural open-air theatre (436,796 triangles, 20,459
+surfaces, 6 materials, ISO 9613-1 air at 20 C / 50 % RH), one source 1.6 m
+above the stage, 16 receiver spheres of radius 2 m on the tiers, 1,000,000
+Fibonacci rays x up to 30 bounces.  One step is the whole path on one batch:
+rt_build_tree (LBVH from the resident mesh) + rt_trace (rays, bounces,
+records, image sources) + rt_rir (8-band histograms, 2 s at 48 kHz).
+
+value      nearest-element queries resolved (hits + escapes) per second, over
+           all ranks, inputs resident in HBM, timed with CUDA events on the
+           launching stream, L2 flushed (256 MB write) before every step.
+e2e        the same metric through the C ABI from pinned host buffers: mesh
+           H2D, trace, histograms and their D2H copy inside the timed region.
+roofline   the bounce kernel's algorithmic L2-path bytes (64 B per node
+           visited + 48 B per triangle tested, counted by an instrumented
+           pass) over its live duration, against the L2 read bandwidth
+           measured in the same run; HBM fraction beside it.
+cpu_baseline  the FP64 oracle (oracle/, C + numpy) on a bounded sample of the
+           same workload on this host's cores.
+
+--impl reference runs that oracle as the reference arm.
+Under torchrun each rank traces its own ray shard of a world_size x 1M-ray
+job (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+METRIC = "ray-bounce hits/s at 436k tris, 1M rays"
+UNIT = "queries/s"
+DURATION = 2.0          # seconds of impulse response
+N_RAYS = 1_000_000
+N_BOUNCES = 30
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--tail-rays", type=int, default=None, help="override the autotuned tail threshold")
+    ap.add_argument("--cpu-sample-rays", type=int, default=200_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(world: int):
+    sc = scenes.theatre(n_rays=N_RAYS * world, n_bounces=N_BOUNCES)
+    return sc
+
+
+def workload_name(world):
+    return (f"open-air theatre 436,796 tris / 20,459 surfaces, {N_RAYS * world:,} rays x {N_BOUNCES} bounces, "
+            f"16 receivers r=2 m, air 20C/50%RH, RIR 8 bands x {DURATION:g} s at 48 kHz")
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if p[5 + k].lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# oracle (CPU) runs
+# ----------------------------------------------------------------------------
+def oracle_sample(sc, n_rays, seed=0):
+    """Trace a seeded subset of the workload's rays with the FP64 oracle
+    (median-split tree), build image sources and histograms; returns
+    (queries, seconds, threads)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    osc = oracle.OracleScene(sc, tree=True)
+    ids = np.sort(rng.choice(sc.n_rays, min(n_rays, sc.n_rays), replace=False))
+    tr = oracle.trace(osc, ray_ids=ids)
+    isrc = oracle.image_sources(sc, tr)
+    oracle.rir(isrc, len(sc.rcv_center), sc.fs, DURATION)
+    dt = time.perf_counter() - t0
+    return tr.queries, dt, oracle.default_threads()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    sc = workload(1)
+    n = args.cpu_sample_rays
+    for _ in range(args.warmup):
+        oracle_sample(sc, max(1000, n // 20))
+    q_tot, t_tot = 0, 0.0
+    for k in range(args.steps):
+        q, dt, threads = oracle_sample(sc, n, seed=k)
+        q_tot += q
+        t_tot += dt
+    v = q_tot / t_tot
+    sample = f"{n:,} seeded rays of the workload per step (of {sc.n_rays:,}), oracle tree + image sources + RIR"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": workload_name(1)},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ----------------------------------------------------------------------------
+# native GPU runs
+# ----------------------------------------------------------------------------
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    return 6800.0, "fallback"
+
+
+def l2_read_peak(torch, stream):
+    """L2 read bandwidth: one reduction that reads an L2-resident 32 MB buffer
+    32 times (zero-stride expand, no copy), best of 10."""
+    x = torch.ones(8 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    rep = 32
+    big = x.view(1, -1).expand(rep, -1)
+    best = math.inf
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            big.sum()
+        for _ in range(10):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            big.sum()
+            b.record(stream)
+            b.synchronize()
+            best = min(best, a.elapsed_time(b))
+    return rep * x.numel() * 4 / (best * 1e-3) / 1e9
+
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+    from paper_1811_05784_gb300 import rt
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream()
+    sc = workload(ws)
+    kw = rt.scene_args(sc)
+    kw.update(ray_begin=rank * N_RAYS, ray_count=N_RAYS)
+    # resident inputs
+    V = torch.as_tensor(sc.vertices, device=dev)
+    T = torch.as_tensor(sc.tris, device=dev)
+    Mt = torch.as_tensor(sc.material_id, device=dev)
+    St = torch.as_tensor(sc.surface_id, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(tail):
+        tree = rt.rt_build_tree(V, T, Mt, St, stream=stream)
+        isrc = rt.rt_trace(tree, tail_rays=tail, stream=stream, **kw)
+        resp = rt.rt_rir(isrc, sc.fs, duration=DURATION, stream=stream)
+        return tree, isrc, resp
+
+    # autotune the tail threshold (one launch finishes the trace below it)
+    with torch.cuda.stream(stream):
+        cand = [args.tail_rays] if args.tail_rays is not None else [-1, 0, 262_144, N_RAYS]
+        best_tail, best_ms = cand[0], math.inf
+        for tail in cand:
+            times = []
+            for _ in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                step(tail)
+                torch.cuda.synchronize()
+                times.append(time.perf_counter() - t0)
+            if min(times) < best_ms:
+                best_ms, best_tail = min(times), tail
+        tail = best_tail
+        for _ in range(args.warmup):
+            step(tail)
+        torch.cuda.synchronize()
+
+        # -- timed region (device-resident inputs) --------------------------
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        launches0 = rt.rt_launch_count()
+        ms, queries, ms_bounce = [], [], []
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            for _ in range(args.steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                tree, isrc, resp = step(tail)
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+                queries.append(isrc.queries)
+                ms_bounce.append(isrc.ms_bounces)
+        torch.cuda.synchronize()
+        launches = rt.rt_launch_count() - launches0
+        if ws > 1:
+            dist.barrier()
+        t_total = sum(ms) / 1e3
+        q_total = sum(queries)
+
+        # -- end to end through host buffers ----------------------------------
+        host = [torch.as_tensor(x).pin_memory() for x in (sc.vertices, sc.tris, sc.material_id, sc.surface_id)]
+        h2d = sum(x.numel() * x.element_size() for x in host)
+        h2d += sc.sources.nbytes + sc.rcv_center.nbytes + sc.rcv_radius.nbytes + sc.rcv_source.nbytes
+        h2d += sc.alpha.nbytes + sc.beta.nbytes
+        out = torch.empty((len(sc.rcv_center), 8, int(math.ceil(DURATION * sc.fs))), dtype=torch.float32).pin_memory()
+        d2h = out.numel() * 4
+        e2e_ms, e2e_q = [], 0
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            tree = rt.rt_build_tree(*host, stream=stream)
+            isrc = rt.rt_trace(tree, tail_rays=tail, stream=stream, **kw)
+            resp = rt.rt_rir(isrc, sc.fs, duration=DURATION, stream=stream)
+            resp.download(out, stream=stream)
+            dt = time.perf_counter() - t0
+            if k >= args.warmup:
+                e2e_ms.append(dt * 1e3)
+                e2e_q += isrc.queries
+
+        # -- roofline of the bounce kernel ------------------------------------
+        B = sc.n_bounces
+        cost = torch.zeros((B, N_RAYS, 2), dtype=torch.int32, device=dev)
+        tree = rt.rt_build_tree(V, T, Mt, St, stream=stream)
+        isrc = rt.rt_trace(tree, tail_rays=tail, stream=stream, debug_cost=cost, **kw)
+        torch.cuda.synchronize()
+        c = cost.double().sum((0, 1)).cpu().numpy()
+        n_q = isrc.queries
+        l2_bytes = 64.0 * c[0] + 48.0 * c[1]
+        hbm_bytes = n_q * 4.0 + N_RAYS * (80.0 + 44.0) + isrc.n_records * 24.0   # hist, state in/out, records
+        del cost
+        bounce_s = statistics.median(ms_bounce) / 1e3
+        l2_peak = l2_read_peak(torch, stream)
+        hbm_peak, hbm_src = measured_peaks()
+
+    # max over ranks
+    t_max = t_total
+    if ws > 1:
+        tt = torch.tensor([t_total, sum(e2e_ms) / 1e3], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        qq = torch.tensor([q_total, e2e_q], device=dev, dtype=torch.float64)
+        dist.all_reduce(qq, op=dist.ReduceOp.SUM)
+        t_max, e2e_t = float(tt[0]), float(tt[1])
+        q_all, e2e_q_all = float(qq[0]), float(qq[1])
+    else:
+        e2e_t, q_all, e2e_q_all = sum(e2e_ms) / 1e3, q_total, e2e_q
+    value = q_all / t_max
+    clocks = clk.summary()
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(ws), "rays_per_gpu": N_RAYS, "n_bounces": N_BOUNCES,
+                   "queries_per_step_per_gpu": int(statistics.median(queries)), "tail_rays": tail,
+                   "l2": "flushed (256 MB write) before every timed step", "parallelism": f"ray shards x{ws}"},
+        "e2e": {"value": e2e_q_all / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "roofline": {"bound": "l2", "kernel": "k_bounce (all launches of one trace)",
+                     "achieved": l2_bytes / bounce_s / 1e9, "peak": l2_peak, "unit": "GB/s",
+                     "frac": l2_bytes / bounce_s / 1e9 / l2_peak,
+                     "peak_source": "measured in this run (L2-resident 48 MB read)",
+                     "traffic": None, "algorithmic_bytes": l2_bytes,
+                     "hbm": {"achieved": hbm_bytes / bounce_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": hbm_bytes / bounce_s / 1e9 / hbm_peak, "peak_source": hbm_src},
+                     "ms_per_launch_set": bounce_s * 1e3,
+                     "nodes_per_query": c[0] / n_q, "tris_per_query": c[1] / n_q},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        q, dt, threads = oracle_sample(sc, args.cpu_sample_rays)
+        result["cpu_baseline"] = {"value": q / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                  "sample": f"{args.cpu_sample_rays:,} seeded rays of the workload "
+                                            f"(oracle median-split tree, image sources, RIR): {q:,} queries"}
+    if rank == 0:
+        print(json.dumps(result))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

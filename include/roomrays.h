@@ -1,0 +1,197 @@
+/*
+ * roomrays.h -- C ABI of the GB300 ray-propagation library.
+ *
+ * Hybrid ray-tracing / image-source room acoustics after Aussal & Gueguen
+ * (2018), "Open-source platforms for fast room acoustic simulations in
+ * complex structures" (arXiv:1811.05784).  Three calls make the path:
+ *
+ *   rt_build_tree  mesh of flat triangles with materials (Sec. 2.1) ->
+ *                  bounding-volume tree (replaces the median-split tree of
+ *                  Sec. 2.2 with a Morton-code LBVH built on the device)
+ *   rt_trace       rays from each source (Sec. 1.2), nearest element per
+ *                  bounce (Sec. 2.1, eq. 20-21), measurement spheres (eq. 22),
+ *                  specular reflection (eq. 15), band absorption (eq. 16),
+ *                  range cut (eq. 13), image sources by reflection sequence
+ *                  with energies (Sec. 1.4, eq. 19)
+ *   rt_rir         8-band energy impulse responses: arrival time d_s / c,
+ *                  histogram at fs (Sec. 1.4)
+ *
+ * Conventions
+ *   - Every call returns rt_status; nothing is thrown across the ABI.  On an
+ *     error, rt_last_error() returns a message for the calling thread and no
+ *     output handle is written.
+ *   - Input pointers are borrowed for the duration of the call.  Host arrays
+ *     are copied; device arrays must be readable on `stream`.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     enqueue work on it; rt_trace and rt_rir synchronise it once or twice to
+ *     size their outputs (record count, image-source count, bin count).
+ *   - Output handles own device memory and are freed by their *_free call.
+ *     Views hand out borrowed device pointers valid until that free.
+ *   - Band index f = 0..7 is the octave 62.5 Hz * 2^f (paper Table 1).
+ *   - Energies: each ray starts with 1/N per band (E_m = n/N, eq. 7).
+ */
+#ifndef ROOMRAYS_H
+#define ROOMRAYS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RT_N_BANDS 8
+#define RT_MAX_BOUNCES 4096
+#define RT_API_VERSION 1
+
+typedef enum {
+    RT_OK = 0,
+    RT_ERR_INVALID_ARG = 1,     /* null / negative / out-of-range argument, NaN input */
+    RT_ERR_DEGENERATE_MESH = 2, /* a triangle has zero area in float32 */
+    RT_ERR_OOM = 3,             /* device allocation failed */
+    RT_ERR_CUDA = 4,            /* a CUDA runtime call failed */
+    RT_ERR_CAPACITY = 5,        /* record buffer still too small after one retry */
+    RT_ERR_STEP_LIMIT = 6,      /* a traversal exceeded its node-visit cap */
+    RT_ERR_STACK = 7,           /* traversal stack overflow */
+    RT_ERR_INTERNAL = 8
+} rt_status;
+
+typedef enum { RT_MEM_HOST = 0, RT_MEM_DEVICE = 1 } rt_memory;
+
+typedef struct rt_tree rt_tree;                   /* immutable after build */
+typedef struct rt_image_sources rt_image_sources; /* device-resident results of rt_trace */
+typedef struct rt_response rt_response;           /* device-resident histograms */
+
+/* Mesh of flat triangles (Sec. 2.1).  `memory` says where the four arrays
+ * live.  surface_id groups coplanar triangles of one material; image sources
+ * are keyed by sequences of surface ids.  surface_id may be NULL only for
+ * host memory: the library then groups triangles by (plane, material). */
+typedef struct {
+    const double* vertices;      /* [n_vertices][3] metres */
+    int64_t n_vertices;
+    const int32_t* tris;         /* [n_tris][3] vertex indices */
+    int64_t n_tris;
+    const int32_t* material_id;  /* [n_tris] index into the absorption table */
+    const int32_t* surface_id;   /* [n_tris] or NULL (host memory only) */
+    rt_memory memory;
+} rt_mesh;
+
+/* Point sources (host memory). */
+typedef struct {
+    const double* pos;           /* [n][3] */
+    int32_t n;
+} rt_sources;
+
+/* Measurement spheres S(x_m, r) (Sec. 1.2, eq. 22), host memory.  Receiver k
+ * listens to source source_of[k] only. */
+typedef struct {
+    const double* center;        /* [n][3] */
+    const double* radius;        /* [n] */
+    const int32_t* source_of;    /* [n] */
+    int32_t n;
+} rt_receivers;
+
+typedef struct {
+    int64_t n_rays;        /* N rays per source: Fibonacci directions i = 0..N-1, energy 1/N */
+    int64_t ray_begin;     /* trace rays [ray_begin, ray_begin + ray_count) of every source */
+    int64_t ray_count;     /* <= 0: all N (shards of one run add up exactly) */
+    int32_t n_bounces;     /* nearest-element queries per ray, 1..RT_MAX_BOUNCES */
+    double max_distance;   /* > 0: eq. 13 range; rays stop once their path exceeds it */
+    const float* air_beta; /* [8] host, energy attenuation 1/m (eq. 19); NULL = none */
+    double c;              /* sound speed m/s (> 0) */
+    int32_t block_size;    /* bounce-kernel block size; 0 = library choice */
+    int32_t max_node_visits; /* traversal cap per query (0 = 65536); exceeding it fails
+                                the call with RT_ERR_STEP_LIMIT instead of looping on */
+    int32_t tail_rays;     /* once a bounce starts with at most this many live rays, one
+                              launch finishes all their remaining bounces (0 = the number
+                              of resident threads, < 0 = never: one launch per bounce) */
+    void* stream;          /* cudaStream_t */
+    /* optional device outputs for parity checks (NULL = off) */
+    float* debug_t;        /* [n_bounces][n_traced] hit distance, +inf on escape */
+    float* debug_state;    /* [n_bounces][n_traced][6] origin and direction before each query */
+    int32_t* debug_cost;   /* [n_bounces][n_traced][2] nodes visited, triangles tested per query */
+} rt_trace_params;
+
+/* Borrowed device views of rt_trace's results.  Traced ray q belongs to
+ * source q / ray_count and has Fibonacci index ray_begin + q % ray_count. */
+typedef struct {
+    int64_t n;                 /* unique image sources */
+    const int32_t* rcv;        /* [n] receiver */
+    const int32_t* order;      /* [n] reflection order m */
+    const int32_t* count;      /* [n] rays in the beam (eq. 7's n) */
+    const int32_t* rep_ray;    /* [n] lowest traced-ray index in the beam */
+    const double* pos;         /* [n][3] image-source position (FP64 mirror chain) */
+    const double* dist;        /* [n] |x_is - x_m| */
+    const double* time;        /* [n] dist / c */
+    const double* energy;      /* [n][8] eq. 19 */
+    int64_t n_traced;          /* rays traced */
+    int32_t n_bounces;
+    const int32_t* hist;       /* [n_bounces][n_traced] triangle hit per bounce, -1 = none */
+    const float* ray_energy;   /* [n_traced][8] band energy after the last hit */
+    const float* ray_length;   /* [n_traced] path length (compensated sum) */
+    const int32_t* ray_hits;   /* [n_traced] surfaces hit */
+    int64_t n_records;         /* sphere crossings */
+    const int32_t* rec_rcv;    /* [n_records] */
+    const int32_t* rec_ray;    /* [n_records] traced-ray index */
+    const int32_t* rec_order;  /* [n_records] */
+    const float* rec_length;   /* [n_records] path length at the closest point */
+    int64_t queries;           /* nearest-element queries resolved (hits + escapes) */
+    int64_t hash_collisions;   /* equal keys with different sequences (expected 0) */
+    float ms_rays;             /* device time of ray generation (CUDA events) */
+    float ms_bounces;          /* device time of all bounce launches */
+    float ms_image_sources;    /* device time of dedup + FP64 reconstruction */
+} rt_is_view;
+
+typedef struct {
+    int32_t n_rcv;
+    int64_t n_bins;
+    double fs;
+    const float* data;         /* device [n_rcv][8][n_bins] energy per bin */
+} rt_response_view;
+
+/* Build the LBVH of a mesh (Sec. 2.2 replaced; see file header).
+ * Errors: RT_ERR_INVALID_ARG (n_tris < 1, index out of range, NaN/Inf),
+ * RT_ERR_DEGENERATE_MESH, RT_ERR_OOM, RT_ERR_CUDA. */
+rt_status rt_build_tree(const rt_mesh* mesh, void* stream, rt_tree** out);
+void rt_tree_free(rt_tree* tree);
+/* Tree statistics: nodes, leaves, depth, triangles, surfaces. */
+rt_status rt_tree_info(const rt_tree* tree, int64_t* n_nodes, int64_t* n_tris, int32_t* depth,
+                       int32_t* n_surfaces);
+
+/* Propagate rays and build image sources.  band_absorption: host
+ * [n_materials][8] alpha(f) in [0,1] (eq. 16).
+ * Errors: RT_ERR_INVALID_ARG, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_CAPACITY (the
+ * record buffer is resized and the trace re-run once before this is
+ * returned), RT_ERR_STACK, RT_ERR_STEP_LIMIT. */
+rt_status rt_trace(const rt_tree* tree, const rt_sources* src, const rt_receivers* rcv,
+                   const float* band_absorption, int32_t n_materials, const rt_trace_params* params,
+                   rt_image_sources** out);
+rt_status rt_image_sources_view(const rt_image_sources* is, rt_is_view* out);
+void rt_image_sources_free(rt_image_sources* is);
+
+/* Energy impulse responses: H[k][f][floor(t_s fs)] += E_s(f) summed in FP64
+ * in a fixed order (deterministic), stored as float.  duration <= 0: up to
+ * the latest arrival.  Image sources later than duration are dropped. */
+rt_status rt_rir(const rt_image_sources* is, double fs, double duration, void* stream, rt_response** out);
+rt_status rt_response_get(const rt_response* rir, rt_response_view* out);
+/* Copy the histograms to host memory dst [n_rcv][8][n_bins] (synchronous). */
+rt_status rt_response_download(const rt_response* rir, float* dst, void* stream);
+void rt_response_free(rt_response* rir);
+
+/* Message of the last error on this thread ("" if none). */
+const char* rt_last_error(void);
+int32_t rt_api_version(void);
+/* Kernel launches made by this library in this process so far (for
+ * accounting; monotonic, thread-safe). */
+int64_t rt_launch_count(void);
+
+/* Optional device allocator (e.g. a framework's caching allocator).  Both
+ * NULL restores cudaMallocAsync / cudaFreeAsync on the call's stream.  An
+ * allocator that returns NULL makes the call fail with RT_ERR_OOM. */
+typedef void* (*rt_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*rt_free_fn)(void* ptr, void* stream, void* ctx);
+rt_status rt_set_allocator(rt_alloc_fn alloc, rt_free_fn free_fn, void* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ROOMRAYS_H */

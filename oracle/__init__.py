@@ -66,6 +66,8 @@ def lib():
             L.orc_scene_diameter.argtypes = [P]
             L.orc_fibonacci.argtypes = [i64, i64, P, P]
             L.orc_nearest.argtypes = [P, i64, P, P, P, i32, f64, i32, P, P, P, P]
+            L.orc_crossings.restype = i64
+            L.orc_crossings.argtypes = [i64, P, P, P, P, i64, P, P, P, i64, P, P, P]
             L.orc_trace.restype = i64
             L.orc_trace.argtypes = [P, P, i64, P, P, P, i64, i64, P, P, i32, f64, i32, f64, i32,
                                     P, P, P, P, P, P, i64, P, P, P, P, P, P, P]
@@ -130,6 +132,28 @@ class OracleScene:
         lib().orc_nearest(self.h, n, _p(org), _p(dirs), _p(ex), int(brute or not self.has_tree),
                           eps_edge_rel, threads or default_threads(), _p(tri), _p(d1), _p(d2), _p(amb))
         return tri, d1, d2, amb.astype(bool)
+
+
+def crossings(scene, org, dirs, seg, ray_src=None):
+    """Measurement-sphere crossings of given segments (eq. 22), lockstep use.
+
+    Returns (segment index, receiver, margin (r - dist)/r) arrays."""
+    org = np.ascontiguousarray(org, np.float64).reshape(-1, 3)
+    dirs = np.ascontiguousarray(dirs, np.float64).reshape(-1, 3)
+    seg = np.ascontiguousarray(seg, np.float64).reshape(-1)
+    n = len(org)
+    rs = np.zeros(n, np.int32) if ray_src is None else np.ascontiguousarray(ray_src, np.int32)
+    rc = np.ascontiguousarray(scene.rcv_center, np.float64)
+    rr = np.ascontiguousarray(scene.rcv_radius, np.float64)
+    rsrc = np.ascontiguousarray(scene.rcv_source, np.int32)
+    cap = max(1024, 2 * n)
+    while True:
+        a, b, c = np.empty(cap, np.int64), np.empty(cap, np.int32), np.empty(cap)
+        k = lib().orc_crossings(n, _p(org), _p(dirs), _p(seg), _p(rs), len(rc), _p(rc), _p(rr), _p(rsrc), cap,
+                                _p(a), _p(b), _p(c))
+        if k <= cap:
+            return a[:k], b[:k], c[:k]
+        cap = int(k)
 
 
 def fibonacci(N: int, ids=None) -> np.ndarray:

@@ -440,6 +440,51 @@ typedef struct {
     double pos[3], dir[3];
 } rec_t;
 
+/* Closest point of the segment [o, o + seg u] to the sphere centre x_m:
+ * t* = clamp((x_m - o).u, 0, seg); crossing iff |o + t* u - x_m| <= r
+ * (eq. 22), and, with the eq. 13 range on, L + t* <= dmax. */
+static int sphere_crossing(const double* o, const double* u, double seg, const double* xm, double rad, double L,
+                           double dmax, rec_t* out) {
+    double w[3] = {xm[0] - o[0], xm[1] - o[1], xm[2] - o[2]};
+    double ts = dot3(w, u);
+    if (ts < 0.0) ts = 0.0;
+    if (ts > seg) ts = seg;
+    double q[3] = {o[0] + ts * u[0] - xm[0], o[1] + ts * u[1] - xm[1], o[2] + ts * u[2] - xm[2]};
+    double dist = sqrt(dot3(q, q));
+    if (!(dist <= rad && (dmax <= 0.0 || L + ts <= dmax))) return 0;
+    out->L = L + ts;
+    out->margin = (rad - dist) / rad;
+    for (int k = 0; k < 3; k++) {
+        out->pos[k] = o[k] + ts * u[k];
+        out->dir[k] = u[k];
+    }
+    return 1;
+}
+
+/* Lockstep crossings: segment k starts at o[k] along u[k] for seg[k] (inf =
+ * escaped) from a ray of source ray_src[k].  Writes up to cap (segment,
+ * receiver, margin) triples and returns how many exist. */
+int64_t orc_crossings(int64_t n, const double* o, const double* u, const double* seg, const int32_t* ray_src,
+                      int64_t n_rcv, const double* rcv_c, const double* rcv_r, const int32_t* rcv_src, int64_t cap,
+                      int64_t* out_seg, int32_t* out_rcv, double* out_margin) {
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; i++) {
+        for (int64_t r = 0; r < n_rcv; r++) {
+            if (rcv_src[r] != ray_src[i]) continue;
+            rec_t rc;
+            if (sphere_crossing(o + 3 * i, u + 3 * i, seg[i], rcv_c + 3 * r, rcv_r[r], 0.0, 0.0, &rc)) {
+                if (k < cap) {
+                    out_seg[k] = i;
+                    out_rcv[k] = (int32_t)r;
+                    out_margin[k] = rc.margin;
+                }
+                k++;
+            }
+        }
+    }
+    return k;
+}
+
 typedef struct {
     const orc_scene* s;
     const double* src;
@@ -494,25 +539,11 @@ static void tr_range(void* p, int64_t b, int64_t e, int tid) {
             /* measurement spheres of this ray's source (eq. 22) */
             for (int64_t r = 0; r < c->n_rcv; r++) {
                 if (c->rsrc[r] != si) continue;
-                const double* xm = c->rc + 3 * r;
-                double w[3] = {xm[0] - o[0], xm[1] - o[1], xm[2] - o[2]};
-                double ts = dot3(w, u);
-                if (ts < 0.0) ts = 0.0;
-                if (ts > seg) ts = seg;
-                double q[3] = {o[0] + ts * u[0] - xm[0], o[1] + ts * u[1] - xm[1], o[2] + ts * u[2] - xm[2]};
-                double dist = sqrt(dot3(q, q));
-                double rad = c->rr[r];
-                if (dist <= rad && (c->dmax <= 0.0 || L + ts <= c->dmax)) {
-                    rec_t rc;
+                rec_t rc;
+                if (sphere_crossing(o, u, seg, c->rc + 3 * r, c->rr[r], L, c->dmax, &rc)) {
                     rc.rcv = (int32_t)r;
                     rc.m = bnc;
                     rc.ray = i;
-                    rc.L = L + ts;
-                    rc.margin = (rad - dist) / rad;
-                    for (int k = 0; k < 3; k++) {
-                        rc.pos[k] = o[k] + ts * u[k];
-                        rc.dir[k] = u[k];
-                    }
                     push_rec(c, tid, &rc);
                 }
             }

@@ -1,0 +1,636 @@
+// rt_build.cu -- rt_build_tree: mesh ingest and device LBVH construction.
+//
+// The paper accelerates the nearest-element search with a binary tree:
+// mother box, split along the largest dimension at the median, recursively,
+// one element per leaf (Sec. 2.2).  On the GPU the tree is a linear BVH
+// (Karras 2012, "Maximizing parallelism in the construction of BVHs, octrees
+// and k-d trees"): 63-bit Morton codes of triangle centroids are sorted with
+// the device radix sort, every internal node finds its key range and split
+// independently, boxes are refitted bottom-up with one atomic flag per node
+// (the second child to arrive computes the union and climbs on), and
+// subtrees of at most RR_LEAF_MAX triangles collapse into leaves.
+//
+// Layout in HBM (see also rt_internal.cuh):
+//   nodes   : 64 B per node = 4 x float4 = child-0 box, child-1 box, refs
+//   tris    : 48 B per triangle in tree order = 3 x float4 (v0|id, v1|surface, v2)
+//   tri_nrm : 16 B per triangle by id = float32 unit normal + surface id
+//   planes  : 32 B per surface, FP64 (n, d) for image-source mirroring
+#include "rt_internal.cuh"
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <map>
+#include <tuple>
+
+namespace rr {
+
+struct BuildMeta {
+    unsigned int cmin[3], cmax[3];  // centroid bounds, order-preserving float bits
+    int max_surf, min_surf, max_mat, min_mat;
+    unsigned int bad_index, non_finite, degenerate, mixed_material;
+    int depth;
+};
+
+__device__ __forceinline__ unsigned int f2ord(float f) {
+    unsigned int b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(unsigned int o) {
+    unsigned int b = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;
+    return __uint_as_float(b);
+}
+
+// pass 1: validate, convert to float32, per-triangle normal, bounds, id ranges
+__global__ void k_tri_prep(const double* __restrict__ V, int64_t nV, const int32_t* __restrict__ T, int64_t M,
+                           const int32_t* __restrict__ mat, const int32_t* __restrict__ surf,
+                           float4* __restrict__ tv, float4* __restrict__ nrm, BuildMeta* meta) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M) return;
+    int32_t ia = T[3 * t], ib = T[3 * t + 1], ic = T[3 * t + 2];
+    if (ia < 0 || ib < 0 || ic < 0 || ia >= nV || ib >= nV || ic >= nV) {
+        atomicAdd(&meta->bad_index, 1u);
+        ia = ib = ic = 0;
+    }
+    double a[3], b[3], c[3];
+    for (int k = 0; k < 3; k++) {
+        a[k] = V[3 * (int64_t)ia + k];
+        b[k] = V[3 * (int64_t)ib + k];
+        c[k] = V[3 * (int64_t)ic + k];
+    }
+    bool finite = true;
+    for (int k = 0; k < 3; k++) finite = finite && isfinite(a[k]) && isfinite(b[k]) && isfinite(c[k]);
+    if (!finite) {
+        atomicAdd(&meta->non_finite, 1u);
+        for (int k = 0; k < 3; k++) a[k] = b[k] = c[k] = 0.0;
+    }
+    double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (!(len > 0.0)) {
+        atomicAdd(&meta->degenerate, 1u);
+        len = 1.0;
+    }
+    int32_t s = surf[t], m = mat[t];
+    nrm[t] = make_float4((float)(n[0] / len), (float)(n[1] / len), (float)(n[2] / len), __int_as_float(s));
+    float4 fa = make_float4((float)a[0], (float)a[1], (float)a[2], __int_as_float((int)t));
+    float4 fb = make_float4((float)b[0], (float)b[1], (float)b[2], __int_as_float(s));
+    float4 fc = make_float4((float)c[0], (float)c[1], (float)c[2], 0.f);
+    tv[3 * t] = fa;
+    tv[3 * t + 1] = fb;
+    tv[3 * t + 2] = fc;
+    float cx = (fa.x + fb.x + fc.x) * (1.0f / 3.0f), cy = (fa.y + fb.y + fc.y) * (1.0f / 3.0f),
+          cz = (fa.z + fb.z + fc.z) * (1.0f / 3.0f);
+    atomicMin(&meta->cmin[0], f2ord(cx));
+    atomicMin(&meta->cmin[1], f2ord(cy));
+    atomicMin(&meta->cmin[2], f2ord(cz));
+    atomicMax(&meta->cmax[0], f2ord(cx));
+    atomicMax(&meta->cmax[1], f2ord(cy));
+    atomicMax(&meta->cmax[2], f2ord(cz));
+    atomicMax(&meta->max_surf, s);
+    atomicMin(&meta->min_surf, s);
+    atomicMax(&meta->max_mat, m);
+    atomicMin(&meta->min_mat, m);
+}
+
+// lowest triangle id per surface
+__global__ void k_surf_first(const int32_t* __restrict__ surf, int64_t M, int32_t* __restrict__ first) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < M) atomicMin(&first[surf[t]], (int32_t)t);
+}
+
+// FP64 plane of each surface from its lowest-id triangle; its material
+__global__ void k_planes(const double* __restrict__ V, const int32_t* __restrict__ T,
+                         const int32_t* __restrict__ mat, const int32_t* __restrict__ first, int S,
+                         Plane* __restrict__ planes, int32_t* __restrict__ mat_of_surf) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    int32_t t = first[s];
+    if (t == INT_MAX) {  // unused surface id
+        planes[s] = Plane{0.0, 0.0, 0.0, 0.0};
+        mat_of_surf[s] = 0;
+        return;
+    }
+    const double* a = V + 3 * (int64_t)T[3 * (int64_t)t];
+    const double* b = V + 3 * (int64_t)T[3 * (int64_t)t + 1];
+    const double* c = V + 3 * (int64_t)T[3 * (int64_t)t + 2];
+    double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (!(len > 0.0)) len = 1.0;
+    n[0] /= len;
+    n[1] /= len;
+    n[2] /= len;
+    planes[s] = Plane{n[0], n[1], n[2], n[0] * a[0] + n[1] * a[1] + n[2] * a[2]};
+    mat_of_surf[s] = mat[t];
+}
+
+__global__ void k_surf_check(const int32_t* __restrict__ surf, const int32_t* __restrict__ mat, int64_t M,
+                             const int32_t* __restrict__ mat_of_surf, BuildMeta* meta) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < M && mat[t] != mat_of_surf[surf[t]]) atomicAdd(&meta->mixed_material, 1u);
+}
+
+// 63-bit Morton code of the float32 centroid within the centroid bounds
+__global__ void k_morton(const float4* __restrict__ tv, int64_t M, const BuildMeta* meta,
+                         uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M) return;
+    float4 a = tv[3 * t], b = tv[3 * t + 1], c = tv[3 * t + 2];
+    float cen[3] = {(a.x + b.x + c.x) * (1.0f / 3.0f), (a.y + b.y + c.y) * (1.0f / 3.0f),
+                    (a.z + b.z + c.z) * (1.0f / 3.0f)};
+    uint32_t q[3];
+    for (int k = 0; k < 3; k++) {
+        float lo = ord2f(meta->cmin[k]), hi = ord2f(meta->cmax[k]);
+        float ext = hi - lo;
+        float x = ext > 0.f ? (cen[k] - lo) / ext : 0.f;
+        float s = x * 2097152.0f;  // 2^21
+        uint32_t v = s <= 0.f ? 0u : (s >= 2097151.0f ? 2097151u : (uint32_t)s);
+        q[k] = v;
+    }
+    uint64_t code = 0;
+    for (int bit = 0; bit < 21; bit++) {
+        code |= (uint64_t)((q[0] >> bit) & 1u) << (3 * bit + 2);
+        code |= (uint64_t)((q[1] >> bit) & 1u) << (3 * bit + 1);
+        code |= (uint64_t)((q[2] >> bit) & 1u) << (3 * bit);
+    }
+    keys[t] = code;
+    vals[t] = (uint32_t)t;
+}
+
+// Karras delta: common prefix length of (code, index) keys; -1 outside [0, M)
+__device__ __forceinline__ int kdelta(const uint64_t* __restrict__ codes, int64_t M, int64_t i, int64_t j) {
+    if (j < 0 || j >= M) return -1;
+    uint64_t a = codes[i], b = codes[j];
+    if (a != b) return __clzll((long long)(a ^ b));
+    return 64 + __clz((int)((uint32_t)i ^ (uint32_t)j));
+}
+
+// one thread per internal node i in [0, M-1): its key range and split
+__global__ void k_karras(const uint64_t* __restrict__ codes, int64_t M, int32_t* __restrict__ left,
+                         int32_t* __restrict__ right, int32_t* __restrict__ first, int32_t* __restrict__ last,
+                         int32_t* __restrict__ parent_int, int32_t* __restrict__ parent_leaf) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M - 1) return;
+    int d = (kdelta(codes, M, i, i + 1) - kdelta(codes, M, i, i - 1)) >= 0 ? 1 : -1;
+    int dmin = kdelta(codes, M, i, i - d);
+    int64_t lmax = 2;
+    while (lmax < 2 * M && kdelta(codes, M, i, i + lmax * d) > dmin) lmax *= 2;
+    int64_t l = 0;
+    for (int64_t t = lmax / 2; t >= 1; t /= 2)
+        if (kdelta(codes, M, i, i + (l + t) * d) > dmin) l += t;
+    int64_t j = i + l * d;
+    int dnode = kdelta(codes, M, i, j);
+    int64_t s = 0;
+    int64_t div = 2;
+    for (int it = 0; it < 64; it++) {
+        int64_t t = (l + div - 1) / div;
+        if (kdelta(codes, M, i, i + (s + t) * d) > dnode) s += t;
+        if (t <= 1) break;
+        div *= 2;
+    }
+    int64_t gamma = i + s * d + (d < 0 ? -1 : 0);
+    int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+    int32_t lc, rc;
+    if (lo == gamma) {
+        lc = ~(int32_t)gamma;
+        parent_leaf[gamma] = (int32_t)i;
+    } else {
+        lc = (int32_t)gamma;
+        parent_int[gamma] = (int32_t)i;
+    }
+    if (hi == gamma + 1) {
+        rc = ~(int32_t)(gamma + 1);
+        parent_leaf[gamma + 1] = (int32_t)i;
+    } else {
+        rc = (int32_t)(gamma + 1);
+        parent_int[gamma + 1] = (int32_t)i;
+    }
+    left[i] = lc;
+    right[i] = rc;
+    first[i] = (int32_t)lo;
+    last[i] = (int32_t)hi;
+}
+
+struct Box {
+    float lo[3], hi[3];
+};
+
+__device__ __forceinline__ Box tri_box(const float4* __restrict__ tv, int64_t t) {
+    float4 a = tv[3 * t], b = tv[3 * t + 1], c = tv[3 * t + 2];
+    Box r;
+    r.lo[0] = fminf(a.x, fminf(b.x, c.x));
+    r.lo[1] = fminf(a.y, fminf(b.y, c.y));
+    r.lo[2] = fminf(a.z, fminf(b.z, c.z));
+    r.hi[0] = fmaxf(a.x, fmaxf(b.x, c.x));
+    r.hi[1] = fmaxf(a.y, fmaxf(b.y, c.y));
+    r.hi[2] = fmaxf(a.z, fmaxf(b.z, c.z));
+    return r;
+}
+
+// leaf boxes in sorted order
+__global__ void k_leaf_boxes(const float4* __restrict__ tv, const uint32_t* __restrict__ order, int64_t M,
+                             float4* __restrict__ leaf_box) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    Box b = tri_box(tv, order[j]);
+    leaf_box[2 * j] = make_float4(b.lo[0], b.lo[1], b.lo[2], 0.f);
+    leaf_box[2 * j + 1] = make_float4(b.hi[0], b.hi[1], b.hi[2], 0.f);
+}
+
+__device__ __forceinline__ void child_box(int32_t c, const float4* leaf_box, const float4* node_box, float4& lo,
+                                          float4& hi) {
+    if (c < 0) {
+        lo = leaf_box[2 * (int64_t)(~c)];
+        hi = leaf_box[2 * (int64_t)(~c) + 1];
+    } else {
+        lo = __ldcg(node_box + 2 * (int64_t)c);
+        hi = __ldcg(node_box + 2 * (int64_t)c + 1);
+    }
+}
+
+// bottom-up refit: the second child to reach a node computes its box
+__global__ void k_refit(int64_t M, const int32_t* __restrict__ left, const int32_t* __restrict__ right,
+                        const int32_t* __restrict__ parent_int, const int32_t* __restrict__ parent_leaf,
+                        const float4* __restrict__ leaf_box, float4* node_box, unsigned int* flags) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    int32_t p = parent_leaf[j];
+    for (int64_t step = 0; p >= 0 && step < M; step++) {
+        __threadfence();
+        unsigned int old = atomicAdd(&flags[p], 1u);
+        if (old == 0) return;
+        __threadfence();
+        float4 al, ah, bl, bh;
+        child_box(left[p], leaf_box, node_box, al, ah);
+        child_box(right[p], leaf_box, node_box, bl, bh);
+        float4 lo = make_float4(fminf(al.x, bl.x), fminf(al.y, bl.y), fminf(al.z, bl.z), 0.f);
+        float4 hi = make_float4(fmaxf(ah.x, bh.x), fmaxf(ah.y, bh.y), fmaxf(ah.z, bh.z), 0.f);
+        __stcg(node_box + 2 * (int64_t)p, lo);
+        __stcg(node_box + 2 * (int64_t)p + 1, hi);
+        p = parent_int[p];
+    }
+}
+
+__global__ void k_depth(int64_t M, const int32_t* __restrict__ parent_int, const int32_t* __restrict__ parent_leaf,
+                        BuildMeta* meta) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    int depth = 1;
+    int32_t p = parent_leaf[j];
+    while (p >= 0 && depth < 100000) {
+        depth++;
+        p = parent_int[p];
+    }
+    atomicMax(&meta->depth, depth);
+}
+
+__global__ void k_keep(int64_t n_int, const int32_t* __restrict__ first, const int32_t* __restrict__ last,
+                       uint32_t* __restrict__ keep) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    keep[i] = (i == 0 || (last[i] - first[i] + 1) > RR_LEAF_MAX) ? 1u : 0u;
+}
+
+// leaf reference: ~(first triangle << 3 | count), count <= RR_LEAF_MAX
+__device__ __forceinline__ int32_t leaf_ref(int32_t first, int32_t count) { return ~((first << 3) | count); }
+
+__device__ __forceinline__ void emit_child(int32_t c, const uint32_t* keep, const uint32_t* newidx,
+                                           const int32_t* first, const int32_t* last, const float4* leaf_box,
+                                           const float4* node_box, float4& lo, float4& hi, int32_t& ref,
+                                           int32_t& cnt) {
+    if (c < 0) {
+        lo = leaf_box[2 * (int64_t)(~c)];
+        hi = leaf_box[2 * (int64_t)(~c) + 1];
+        cnt = 1;
+        ref = leaf_ref(~c, cnt);
+    } else {
+        lo = node_box[2 * (int64_t)c];
+        hi = node_box[2 * (int64_t)c + 1];
+        if (keep[c]) {
+            ref = (int32_t)newidx[c];
+            cnt = 0;
+        } else {
+            cnt = last[c] - first[c] + 1;
+            ref = leaf_ref(first[c], cnt);
+        }
+    }
+}
+
+__global__ void k_emit_nodes(int64_t n_int, const int32_t* __restrict__ left, const int32_t* __restrict__ right,
+                             const int32_t* __restrict__ first, const int32_t* __restrict__ last,
+                             const uint32_t* __restrict__ keep, const uint32_t* __restrict__ newidx,
+                             const float4* __restrict__ leaf_box, const float4* __restrict__ node_box,
+                             float4* __restrict__ nodes) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int || !keep[i]) return;
+    float4 l0, h0, l1, h1;
+    int32_t r0, r1, c0, c1;
+    if (i == 0 && (last[0] - first[0] + 1) <= RR_LEAF_MAX) {
+        // the whole mesh fits one leaf
+        l0 = node_box[0];
+        h0 = node_box[1];
+        c0 = last[0] - first[0] + 1;
+        r0 = leaf_ref(0, c0);
+        l1 = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+        h1 = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+        c1 = 0;
+        r1 = leaf_ref(0, 0);  // empty
+    } else {
+        emit_child(left[i], keep, newidx, first, last, leaf_box, node_box, l0, h0, r0, c0);
+        emit_child(right[i], keep, newidx, first, last, leaf_box, node_box, l1, h1, r1, c1);
+    }
+    float4* n = nodes + 4 * (int64_t)newidx[i];
+    n[0] = make_float4(l0.x, l0.y, l0.z, h0.x);
+    n[1] = make_float4(h0.y, h0.z, l1.x, l1.y);
+    n[2] = make_float4(l1.z, h1.x, h1.y, h1.z);
+    n[3] = make_float4(__int_as_float(r0), __int_as_float(r1), __int_as_float(c0), __int_as_float(c1));
+}
+
+// single-triangle mesh: one node holding one leaf
+__global__ void k_single(const float4* __restrict__ tv, float4* __restrict__ nodes, float4* __restrict__ tris) {
+    Box b = tri_box(tv, 0);
+    nodes[0] = make_float4(b.lo[0], b.lo[1], b.lo[2], b.hi[0]);
+    nodes[1] = make_float4(b.hi[1], b.hi[2], INFINITY, INFINITY);
+    nodes[2] = make_float4(INFINITY, -INFINITY, -INFINITY, -INFINITY);
+    nodes[3] = make_float4(__int_as_float(~1), __int_as_float(~0), __int_as_float(1), __int_as_float(0));
+    tris[0] = tv[0];
+    tris[1] = tv[1];
+    tris[2] = tv[2];
+}
+
+__global__ void k_reorder(const float4* __restrict__ tv, const uint32_t* __restrict__ order, int64_t M,
+                          float4* __restrict__ tris) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    int64_t t = order[j];
+    tris[3 * j] = tv[3 * t];
+    tris[3 * j + 1] = tv[3 * t + 1];
+    tris[3 * j + 2] = tv[3 * t + 2];
+}
+
+static unsigned grid_of(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// host grouping of triangles into surfaces by (material, plane) when the
+// caller gives no surface ids
+static std::vector<int32_t> group_surfaces(const double* V, const int32_t* T, const int32_t* mat, int64_t M) {
+    std::map<std::tuple<int32_t, long long, long long, long long, long long>, int32_t> ids;
+    std::vector<int32_t> out((size_t)M);
+    for (int64_t t = 0; t < M; t++) {
+        const double *a = V + 3 * (int64_t)T[3 * t], *b = V + 3 * (int64_t)T[3 * t + 1],
+                     *c = V + 3 * (int64_t)T[3 * t + 2];
+        double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]}, e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (len > 0) {
+            n[0] /= len, n[1] /= len, n[2] /= len;
+        }
+        // canonical orientation: first non-zero component positive
+        int k = std::fabs(n[0]) > 1e-12 ? 0 : (std::fabs(n[1]) > 1e-12 ? 1 : 2);
+        if (n[k] < 0) n[0] = -n[0], n[1] = -n[1], n[2] = -n[2];
+        double d = n[0] * a[0] + n[1] * a[1] + n[2] * a[2];
+        auto key = std::make_tuple(mat[t], std::llround(n[0] * 1e7), std::llround(n[1] * 1e7),
+                                   std::llround(n[2] * 1e7), std::llround(d * 1e5));
+        auto it = ids.find(key);
+        if (it == ids.end()) it = ids.emplace(key, (int32_t)ids.size()).first;
+        out[(size_t)t] = it->second;
+    }
+    return out;
+}
+
+static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out) {
+    if (!mesh || !out) {
+        set_error("rt_build_tree: null argument");
+        return RT_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    const int64_t M = mesh->n_tris, nV = mesh->n_vertices;
+    if (M < 1 || nV < 3 || !mesh->vertices || !mesh->tris || !mesh->material_id) {
+        set_error("rt_build_tree: need n_tris >= 1, n_vertices >= 3 and non-null arrays");
+        return RT_ERR_INVALID_ARG;
+    }
+    if (M >= ((int64_t)1 << 28)) {
+        set_error("rt_build_tree: %lld triangles exceed the 32-bit index range", (long long)M);
+        return RT_ERR_INVALID_ARG;
+    }
+    if (mesh->memory != RT_MEM_HOST && mesh->memory != RT_MEM_DEVICE) {
+        set_error("rt_build_tree: bad memory kind");
+        return RT_ERR_INVALID_ARG;
+    }
+    if (!mesh->surface_id && mesh->memory != RT_MEM_HOST) {
+        set_error("rt_build_tree: surface_id may be NULL only for host meshes");
+        return RT_ERR_INVALID_ARG;
+    }
+    Arena tmp(s), keep_arena(s);
+    const double* dV = mesh->vertices;
+    const int32_t *dT = mesh->tris, *dmat = mesh->material_id, *dsurf = mesh->surface_id;
+    std::vector<int32_t> host_surf;
+    if (mesh->memory == RT_MEM_HOST) {
+        double* v;
+        int32_t *t, *m, *sf;
+        RR_TRY(tmp.alloc(&v, 3 * nV));
+        RR_TRY(tmp.alloc(&t, 3 * M));
+        RR_TRY(tmp.alloc(&m, M));
+        RR_TRY(tmp.alloc(&sf, M));
+        const int32_t* hs = mesh->surface_id;
+        if (!hs) {
+            for (int64_t k = 0; k < 3 * M; k++) {
+                if (mesh->tris[k] < 0 || mesh->tris[k] >= nV) {
+                    set_error("rt_build_tree: vertex index out of range");
+                    return RT_ERR_INVALID_ARG;
+                }
+            }
+            host_surf = group_surfaces(mesh->vertices, mesh->tris, mesh->material_id, M);
+            hs = host_surf.data();
+        }
+        RR_CUDA(cudaMemcpyAsync(v, mesh->vertices, sizeof(double) * 3 * nV, cudaMemcpyHostToDevice, s));
+        RR_CUDA(cudaMemcpyAsync(t, mesh->tris, sizeof(int32_t) * 3 * M, cudaMemcpyHostToDevice, s));
+        RR_CUDA(cudaMemcpyAsync(m, mesh->material_id, sizeof(int32_t) * M, cudaMemcpyHostToDevice, s));
+        RR_CUDA(cudaMemcpyAsync(sf, hs, sizeof(int32_t) * M, cudaMemcpyHostToDevice, s));
+        dV = v, dT = t, dmat = m, dsurf = sf;
+    }
+    rt_tree* tree = new rt_tree();
+    struct Guard {
+        rt_tree*& t;
+        ~Guard() {
+            if (t) {
+                for (void* p : t->owned) dev_free(p, t->stream);
+                delete t;
+            }
+        }
+    } guard{tree};
+    tree->stream = s;
+    tree->n_tris = M;
+
+    BuildMeta* meta;
+    RR_TRY(tmp.alloc(&meta, 1));
+    BuildMeta hm;
+    for (int k = 0; k < 3; k++) hm.cmin[k] = 0xFFFFFFFFu, hm.cmax[k] = 0u;
+    hm.max_surf = INT_MIN, hm.min_surf = INT_MAX, hm.max_mat = INT_MIN, hm.min_mat = INT_MAX;
+    hm.bad_index = hm.non_finite = hm.degenerate = hm.mixed_material = 0;
+    hm.depth = 0;
+    RR_CUDA(cudaMemcpyAsync(meta, &hm, sizeof hm, cudaMemcpyHostToDevice, s));
+
+    float4 *tv, *tri_nrm;
+    RR_TRY(tmp.alloc(&tv, 3 * M));
+    RR_TRY(keep_arena.alloc(&tri_nrm, M));
+    RR_LAUNCH(k_tri_prep, grid_of(M, 256), 256, 0, s, dV, nV, dT, M, dmat, dsurf, tv, tri_nrm, meta);
+    RR_CUDA(cudaGetLastError());
+    RR_CUDA(cudaMemcpyAsync(&hm, meta, sizeof hm, cudaMemcpyDeviceToHost, s));
+    RR_CUDA(cudaStreamSynchronize(s));
+    if (hm.bad_index) {
+        set_error("rt_build_tree: %u triangles index vertices out of range", hm.bad_index);
+        return RT_ERR_INVALID_ARG;
+    }
+    if (hm.non_finite) {
+        set_error("rt_build_tree: %u triangles have non-finite coordinates", hm.non_finite);
+        return RT_ERR_INVALID_ARG;
+    }
+    if (hm.degenerate) {
+        set_error("rt_build_tree: %u triangles have zero area", hm.degenerate);
+        return RT_ERR_DEGENERATE_MESH;
+    }
+    if (hm.min_surf < 0 || hm.min_mat < 0 || hm.max_surf >= (1 << 30)) {
+        set_error("rt_build_tree: surface or material ids out of range");
+        return RT_ERR_INVALID_ARG;
+    }
+    const int S = hm.max_surf + 1;
+    tree->n_surfaces = S;
+    tree->n_materials = hm.max_mat + 1;
+
+    int32_t *sfirst, *mat_of_surf, *surf_of;
+    Plane* planes;
+    RR_TRY(tmp.alloc(&sfirst, S));
+    RR_TRY(keep_arena.alloc(&mat_of_surf, S));
+    RR_TRY(keep_arena.alloc(&planes, S));
+    RR_TRY(keep_arena.alloc(&surf_of, M));
+    RR_CUDA(cudaMemcpyAsync(surf_of, dsurf, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, s));
+    {
+        std::vector<int32_t> init((size_t)S, INT_MAX);
+        RR_CUDA(cudaMemcpyAsync(sfirst, init.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
+        RR_LAUNCH(k_surf_first, grid_of(M, 256), 256, 0, s, dsurf, M, sfirst);
+        RR_LAUNCH(k_planes, grid_of(S, 128), 128, 0, s, dV, dT, dmat, sfirst, S, planes, mat_of_surf);
+        RR_LAUNCH(k_surf_check, grid_of(M, 256), 256, 0, s, dsurf, dmat, M, mat_of_surf, meta);
+        RR_CUDA(cudaGetLastError());
+        // init is a pageable host buffer: the copy completes before returning
+    }
+
+    // Morton codes, sort
+    uint64_t *keys, *keys_alt;
+    uint32_t *vals, *vals_alt;
+    RR_TRY(tmp.alloc(&keys, M));
+    RR_TRY(tmp.alloc(&keys_alt, M));
+    RR_TRY(tmp.alloc(&vals, M));
+    RR_TRY(tmp.alloc(&vals_alt, M));
+    void* sort_tmp;
+    RR_TRY(tmp.alloc((char**)&sort_tmp, sort_temp_bytes(M)));
+    RR_LAUNCH(k_morton, grid_of(M, 256), 256, 0, s, tv, M, meta, keys, vals);
+    RR_CUDA(cudaGetLastError());
+    RR_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, M, 0, 64, sort_tmp, s));
+
+    float4* tris;
+    RR_TRY(keep_arena.alloc(&tris, 3 * M));
+    float4* nodes;
+    int64_t n_nodes = 1;
+    if (M == 1) {
+        RR_TRY(keep_arena.alloc(&nodes, 4));
+        RR_LAUNCH(k_single, 1, 1, 0, s, tv, nodes, tris);
+        RR_CUDA(cudaGetLastError());
+        hm.depth = 1;
+    } else {
+        const int64_t NI = M - 1;
+        int32_t *left, *right, *first, *last, *pint, *pleaf;
+        float4 *leaf_box, *node_box;
+        unsigned int* flags;
+        uint32_t *keep, *newidx, *total;
+        RR_TRY(tmp.alloc(&left, NI));
+        RR_TRY(tmp.alloc(&right, NI));
+        RR_TRY(tmp.alloc(&first, NI));
+        RR_TRY(tmp.alloc(&last, NI));
+        RR_TRY(tmp.alloc(&pint, NI));
+        RR_TRY(tmp.alloc(&pleaf, M));
+        RR_TRY(tmp.alloc(&leaf_box, 2 * M));
+        RR_TRY(tmp.alloc(&node_box, 2 * NI));
+        RR_TRY(tmp.alloc(&flags, NI));
+        RR_TRY(tmp.alloc(&keep, NI));
+        RR_TRY(tmp.alloc(&newidx, NI));
+        RR_TRY(tmp.alloc(&total, 1));
+        void* scan_tmp;
+        RR_TRY(tmp.alloc((char**)&scan_tmp, scan_temp_bytes(NI)));
+        RR_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned int) * NI, s));
+        RR_CUDA(cudaMemsetAsync(pint, 0xFF, sizeof(int32_t) * NI, s));  // root keeps -1
+        RR_LAUNCH(k_karras, grid_of(NI, 256), 256, 0, s, keys, M, left, right, first, last, pint, pleaf);
+        RR_LAUNCH(k_leaf_boxes, grid_of(M, 256), 256, 0, s, tv, vals, M, leaf_box);
+        RR_LAUNCH(k_refit, grid_of(M, 256), 256, 0, s, M, left, right, pint, pleaf, leaf_box, node_box, flags);
+        RR_LAUNCH(k_depth, grid_of(M, 256), 256, 0, s, M, pint, pleaf, meta);
+        RR_LAUNCH(k_keep, grid_of(NI, 256), 256, 0, s, NI, first, last, keep);
+        RR_CUDA(cudaGetLastError());
+        RR_TRY(exclusive_scan_u32(keep, newidx, NI, total, scan_tmp, s));
+        uint32_t nn = 0;
+        RR_CUDA(cudaMemcpyAsync(&nn, total, sizeof nn, cudaMemcpyDeviceToHost, s));
+        RR_CUDA(cudaStreamSynchronize(s));
+        n_nodes = nn;
+        RR_TRY(keep_arena.alloc(&nodes, 4 * n_nodes));
+        RR_LAUNCH(k_emit_nodes, grid_of(NI, 256), 256, 0, s, NI, left, right, first, last, keep, newidx, leaf_box,
+                                                      node_box, nodes);
+        RR_LAUNCH(k_reorder, grid_of(M, 256), 256, 0, s, tv, vals, M, tris);
+        RR_CUDA(cudaGetLastError());
+    }
+    RR_CUDA(cudaMemcpyAsync(&hm, meta, sizeof hm, cudaMemcpyDeviceToHost, s));
+    RR_CUDA(cudaStreamSynchronize(s));
+    if (hm.mixed_material) {
+        set_error("rt_build_tree: %u triangles differ in material from their surface", hm.mixed_material);
+        return RT_ERR_INVALID_ARG;
+    }
+    tree->depth = hm.depth;
+    tree->n_nodes = n_nodes;
+    tree->nodes = nodes;
+    tree->tris = tris;
+    tree->tri_nrm = tri_nrm;
+    tree->surf_of = surf_of;
+    tree->mat_of_surf = mat_of_surf;
+    tree->planes = planes;
+    float lo[3], hi[3];
+    for (int k = 0; k < 3; k++) {
+        unsigned int a = hm.cmin[k], b = hm.cmax[k];
+        unsigned int ba = (a & 0x80000000u) ? (a & 0x7FFFFFFFu) : ~a;
+        unsigned int bb = (b & 0x80000000u) ? (b & 0x7FFFFFFFu) : ~b;
+        memcpy(&lo[k], &ba, 4);
+        memcpy(&hi[k], &bb, 4);
+    }
+    double dd = 0;
+    for (int k = 0; k < 3; k++) dd += (double)(hi[k] - lo[k]) * (hi[k] - lo[k]);
+    tree->diameter = std::sqrt(dd) > 0 ? std::sqrt(dd) : 1.0;
+    tree->owned = keep_arena.release();
+    *out = tree;
+    tree = nullptr;  // disarm the guard
+    return RT_OK;
+}
+
+}  // namespace rr
+
+extern "C" rt_status rt_build_tree(const rt_mesh* mesh, void* stream, rt_tree** out) {
+    rr::clear_error();
+    return rr::build_impl(mesh, (cudaStream_t)stream, out);
+}
+
+extern "C" void rt_tree_free(rt_tree* tree) {
+    if (!tree) return;
+    for (void* p : tree->owned) rr::dev_free(p, tree->stream);
+    delete tree;
+}
+
+extern "C" rt_status rt_tree_info(const rt_tree* tree, int64_t* n_nodes, int64_t* n_tris, int32_t* depth,
+                                  int32_t* n_surfaces) {
+    if (!tree) {
+        rr::set_error("rt_tree_info: null tree");
+        return RT_ERR_INVALID_ARG;
+    }
+    if (n_nodes) *n_nodes = tree->n_nodes;
+    if (n_tris) *n_tris = tree->n_tris;
+    if (depth) *depth = tree->depth;
+    if (n_surfaces) *n_surfaces = tree->n_surfaces;
+    return RT_OK;
+}

@@ -1,0 +1,355 @@
+// rt_common.cu -- error reporting, device allocation, radix sort and scan.
+#include "rt_internal.cuh"
+
+#include <atomic>
+#include <mutex>
+
+namespace rr {
+
+// ---------------------------------------------------------------------------
+// errors (thread-local message)
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+void clear_error() { g_err.clear(); }
+
+rt_status cuda_status(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return RT_OK;
+    set_error("%s failed: %s", what, cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return RT_ERR_OOM;
+    return RT_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// allocation: cudaMallocAsync on the call's stream, or a user hook
+// ---------------------------------------------------------------------------
+static std::mutex g_alloc_mu;
+static rt_alloc_fn g_alloc = nullptr;
+static rt_free_fn g_free = nullptr;
+static void* g_ctx = nullptr;
+
+// The stream-ordered pool would hand memory back to the driver at every
+// synchronisation; keeping it makes repeated traces allocation-free.
+static void keep_pool_memory() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
+
+void* dev_alloc(size_t bytes, cudaStream_t s) {
+    rt_alloc_fn a;
+    void* ctx;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        a = g_alloc;
+        ctx = g_ctx;
+    }
+    if (a) return a(bytes, (void*)s, ctx);
+    keep_pool_memory();
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(void* p, cudaStream_t s) {
+    if (!p) return;
+    rt_free_fn f;
+    void* ctx;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        f = g_free;
+        ctx = g_ctx;
+    }
+    if (f) {
+        f(p, (void*)s, ctx);
+        return;
+    }
+    cudaFreeAsync(p, s);
+}
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+int device_sm_count() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of uint32 (three phases: tile sums, scan of sums, apply)
+// ---------------------------------------------------------------------------
+static constexpr int SCAN_THREADS = 512;
+static constexpr int SCAN_ITEMS = 8;
+static constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    return v;
+}
+
+// block-wide exclusive scan; every thread receives the block total in `total`
+template <int THREADS>
+__device__ uint32_t block_excl_scan(uint32_t v, uint32_t& total) {
+    constexpr int W = THREADS / 32;
+    static_assert(W <= 32, "block too large");
+    __shared__ uint32_t warp_sums[W];
+    __shared__ uint32_t s_total;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = warp_incl_scan(v);
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = (lane < W) ? warp_sums[lane] : 0u;
+        uint32_t wi = warp_incl_scan(w);
+        if (lane < W) warp_sums[lane] = wi - w;
+        if (lane == 31) s_total = wi;
+    }
+    __syncthreads();
+    uint32_t r = warp_sums[warp] + incl - v;
+    total = s_total;
+    __syncthreads();
+    return r;
+}
+
+__global__ void k_scan_tiles(const uint32_t* __restrict__ in, int64_t n, uint32_t* __restrict__ tile_sums) {
+    uint32_t tot;
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        int64_t i = base + k;
+        if (i < n) s += in[i];
+    }
+    block_excl_scan<SCAN_THREADS>(s, tot);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+// scan of the tile sums by one block (sequential chunks per thread)
+__global__ void k_scan_sums(uint32_t* sums, int64_t m, uint32_t* total_dev) {
+    uint32_t tot;
+    int64_t per = (m + SCAN_THREADS - 1) / SCAN_THREADS;
+    int64_t b = (int64_t)threadIdx.x * per, e = b + per < m ? b + per : m;
+    uint32_t s = 0;
+    for (int64_t i = b; i < e; i++) s += sums[i];
+    uint32_t off = block_excl_scan<SCAN_THREADS>(s, tot);
+    for (int64_t i = b; i < e; i++) {
+        uint32_t x = sums[i];
+        sums[i] = off;
+        off += x;
+    }
+    if (threadIdx.x == 0 && total_dev) *total_dev = tot;
+}
+
+__global__ void k_scan_apply(const uint32_t* __restrict__ in, uint32_t* __restrict__ out, int64_t n,
+                             const uint32_t* __restrict__ tile_off) {
+    uint32_t tot;
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        int64_t i = base + k;
+        v[k] = (i < n) ? in[i] : 0u;
+        s += v[k];
+    }
+    uint32_t off = block_excl_scan<SCAN_THREADS>(s, tot) + tile_off[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; k++) {
+        int64_t i = base + k;
+        if (i < n) out[i] = off;
+        off += v[k];
+    }
+}
+
+size_t scan_temp_bytes(int64_t n) {
+    int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    return (size_t)(tiles + 1) * sizeof(uint32_t);
+}
+
+rt_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev, void* temp,
+                             cudaStream_t s) {
+    if (n <= 0) {
+        if (total_dev) RR_CUDA(cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s));
+        return RT_OK;
+    }
+    int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    uint32_t* sums = (uint32_t*)temp;
+    RR_LAUNCH(k_scan_tiles, (unsigned)tiles, SCAN_THREADS, 0, s, in, n, sums);
+    RR_LAUNCH(k_scan_sums, 1, SCAN_THREADS, 0, s, sums, tiles, total_dev);
+    RR_LAUNCH(k_scan_apply, (unsigned)tiles, SCAN_THREADS, 0, s, in, out, n, sums);
+    RR_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// stable LSD radix sort, 8-bit digits
+//   pass = histogram per tile -> exclusive scan (digit-major) -> scatter.
+//   The scatter ranks keys inside a warp with __match_any_sync, keeping the
+//   input order among equal digits, so every pass is stable.
+// ---------------------------------------------------------------------------
+static constexpr int SORT_THREADS = 256;
+static constexpr int SORT_WARPS = SORT_THREADS / 32;
+static constexpr int SORT_ITEMS = 8;
+static constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 2048 keys
+static constexpr int RADIX = 256;
+
+__global__ void k_sort_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, int nblocks,
+                            uint32_t* __restrict__ counts) {
+    __shared__ uint32_t h[RADIX];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * SORT_TILE;
+#pragma unroll
+    for (int k = 0; k < SORT_ITEMS; k++) {
+        int64_t i = base + (int64_t)k * SORT_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 0xFFu], 1u);
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void k_sort_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                               uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
+                               int nblocks, const uint32_t* __restrict__ offsets) {
+    __shared__ uint32_t whist[SORT_WARPS][RADIX];
+    __shared__ uint32_t boff[RADIX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&whist[0][0])[i] = 0;
+    __syncthreads();
+    const int64_t wbase = (int64_t)blockIdx.x * SORT_TILE + (int64_t)warp * 32 * SORT_ITEMS;
+    uint64_t k[SORT_ITEMS];
+    uint32_t v[SORT_ITEMS], rank[SORT_ITEMS], dig[SORT_ITEMS];
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; it++) {
+        int64_t idx = wbase + it * 32 + lane;
+        bool valid = idx < n;
+        k[it] = valid ? kin[idx] : 0ull;
+        v[it] = valid ? vin[idx] : 0u;
+        uint32_t d = valid ? ((uint32_t)(k[it] >> shift) & 0xFFu) : 0xFFFFFFFFu;
+        dig[it] = d;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t below = peers & ((1u << lane) - 1u);
+        uint32_t r = 0;
+        if (valid) r = whist[warp][d] + __popc(below);
+        rank[it] = r;
+        __syncwarp();
+        if (valid && below == 0) whist[warp][d] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        int d = threadIdx.x;
+        uint32_t sum = 0;
+#pragma unroll
+        for (int w = 0; w < SORT_WARPS; w++) {
+            uint32_t c = whist[w][d];
+            whist[w][d] = sum;
+            sum += c;
+        }
+        boff[d] = offsets[(int64_t)d * nblocks + blockIdx.x];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; it++) {
+        uint32_t d = dig[it];
+        if (d != 0xFFFFFFFFu) {
+            uint32_t pos = boff[d] + whist[warp][d] + rank[it];
+            kout[pos] = k[it];
+            vout[pos] = v[it];
+        }
+    }
+}
+
+size_t sort_temp_bytes(int64_t n) {
+    int64_t nb = (n + SORT_TILE - 1) / SORT_TILE;
+    size_t counts = (size_t)nb * RADIX * sizeof(uint32_t);
+    counts = (counts + 255) & ~(size_t)255;
+    return counts + scan_temp_bytes(nb * RADIX) + 256;
+}
+
+rt_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
+                           int begin_bit, int end_bit, void* temp, cudaStream_t s) {
+    if (n <= 1 || end_bit <= begin_bit) return RT_OK;
+    if (n > (int64_t)0xFFFFFFFF) {
+        set_error("radix sort of %lld keys exceeds 32-bit positions", (long long)n);
+        return RT_ERR_INVALID_ARG;
+    }
+    int nb = (int)((n + SORT_TILE - 1) / SORT_TILE);
+    uint32_t* counts = (uint32_t*)temp;
+    size_t cbytes = ((size_t)nb * RADIX * sizeof(uint32_t) + 255) & ~(size_t)255;
+    void* scan_tmp = (char*)temp + cbytes;
+    uint64_t *ki = keys, *ko = keys_alt;
+    uint32_t *vi = vals, *vo = vals_alt;
+    int passes = 0;
+    for (int shift = begin_bit; shift < end_bit; shift += 8) {
+        RR_LAUNCH(k_sort_hist, nb, SORT_THREADS, 0, s, ki, n, shift, nb, counts);
+        RR_TRY(exclusive_scan_u32(counts, counts, (int64_t)nb * RADIX, nullptr, scan_tmp, s));
+        RR_LAUNCH(k_sort_scatter, nb, SORT_THREADS, 0, s, ki, vi, ko, vo, n, shift, nb, counts);
+        RR_CUDA(cudaGetLastError());
+        uint64_t* tk = ki;
+        ki = ko;
+        ko = tk;
+        uint32_t* tv = vi;
+        vi = vo;
+        vo = tv;
+        passes++;
+    }
+    if (passes & 1) {
+        RR_CUDA(cudaMemcpyAsync(keys, ki, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));
+        RR_CUDA(cudaMemcpyAsync(vals, vi, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    return RT_OK;
+}
+
+}  // namespace rr
+
+// ---------------------------------------------------------------------------
+// C ABI: misc
+// ---------------------------------------------------------------------------
+extern "C" const char* rt_last_error(void) { return rr::g_err.c_str(); }
+
+extern "C" int32_t rt_api_version(void) { return RT_API_VERSION; }
+
+extern "C" int64_t rt_launch_count(void) { return rr::launch_count(); }
+
+extern "C" rt_status rt_set_allocator(rt_alloc_fn alloc, rt_free_fn free_fn, void* ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) {
+        rr::set_error("rt_set_allocator: give both functions or neither");
+        return RT_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(rr::g_alloc_mu);
+    rr::g_alloc = alloc;
+    rr::g_free = free_fn;
+    rr::g_ctx = ctx;
+    return RT_OK;
+}

@@ -1,0 +1,1091 @@
+// rt_trace.cu -- rt_trace: batched ray propagation and image sources.
+//
+// Wavefront design: all live rays of one bounce are processed by one fused
+// kernel launch (k_bounce) that, per ray,
+//   1. finds the nearest triangle through the LBVH (paper Sec. 2.1-2.2):
+//      stack traversal, nearest child first, robust slab test (Williams et
+//      al. 2005 with the conservative rounding margin of Ize 2013) and the
+//      watertight ray/triangle test of Woop, Benthin & Wald (JCGT 2013) in
+//      float32 (edge functions recomputed in double only when exactly 0);
+//      exact distance ties go to the lowest triangle id;
+//   2. tests the segment against the measurement spheres of its source
+//      (eq. 22) and appends crossing records with one atomic per warp;
+//   3. reflects specularly (eq. 15: u - 2 (u.n) n), multiplies the 8 band
+//      energies by 1 - alpha(f) (eq. 16), adds the segment length to the path
+//      length with a compensated (Kahan) sum, folds the surface id into the
+//      ray's sequence hash, and starts the next segment a few ulps before
+//      the hit point along the incoming ray (inside every wall that meets
+//      the hit surface, so corner hits cannot leak), while candidates on
+//      the surface just left are skipped (a ray leaving a plane cannot meet
+//      it again), which makes an offset along the normal unnecessary;
+//   4. compacts survivors into the next queue (warp ballot + popc, one
+//      atomic per warp); rays that escape (open air, Sec. 2.1), reach the
+//      bounce cap or exceed the eq. 13 range write their final state.
+// Warps fetch 32 rays at a time from a per-bounce counter (persistent
+// grid), and the live count of each bounce stays in device memory, so the
+// B launches need no host round trip.
+//
+// Image sources (Sec. 1.4, eq. 19): records are radix-sorted by a 64-bit key
+// of (receiver, order, sequence hash); equal keys are verified against the
+// exact surface sequences read from the per-ray hit history; each segment
+// of equal keys is one image source with n = segment length.  Its position
+// is the source mirrored across the sequence's FP64 planes in hit order;
+// distance, arrival time and E_s(f) = (n/N) prod(1 - alpha_j(f)) e^(-beta d)
+// are computed in FP64.
+#include "rt_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace rr {
+
+static constexpr int DEFAULT_NODE_VISITS = 1 << 16;
+
+enum : unsigned int { ST_STACK = 1u, ST_STEPS = 2u, ST_HISTORY = 4u, ST_BOUNDS = 8u };
+
+struct Queue {
+    float4* o;   // origin xyz, path length L
+    float4* d;   // direction xyz, Kahan compensation of L
+    float4* e0;  // band energies 0..3
+    float4* e1;  // band energies 4..7
+    uint4* m;    // traced ray index, last surface id, sequence hash lo, hi
+};
+
+struct BounceArgs {
+    const float4* __restrict__ nodes;
+    const float4* __restrict__ tris;
+    int64_t n_nodes, n_tris;
+    const float4* __restrict__ tri_nrm;
+    const int32_t* __restrict__ mat_of_surf;
+    const float* __restrict__ refl;      // [n_mat][8] 1 - alpha
+    const float4* __restrict__ rcv;      // [R] centre, r^2 (sorted by source)
+    const int32_t* __restrict__ rcv_id;  // [R] original receiver index
+    const int32_t* __restrict__ rcv_beg; // [S+1] receiver range per source
+    Queue in, out;
+    int32_t* __restrict__ hist;          // [B][n_traced]
+    float4* __restrict__ ray_e;          // [n_traced][2]
+    float* __restrict__ ray_len;
+    int32_t* __restrict__ ray_hits;
+    int32_t* __restrict__ rec_rcv;
+    int32_t* __restrict__ rec_ray;
+    int32_t* __restrict__ rec_m;
+    float* __restrict__ rec_len;
+    uint64_t* __restrict__ rec_key;
+    unsigned long long rec_cap;
+    unsigned int* live;                  // [B+1]
+    unsigned int* fetch;                 // [B]
+    unsigned long long* n_rec;
+    unsigned int* status;
+    int64_t n_traced;
+    int64_t per_src;                     // rays per source traced
+    int b, B;
+    unsigned int tail_threshold;         // live rays at or below which one launch finishes the trace
+    unsigned long long* n_queries;
+    int step_cap;                        // node visits per query
+    float dmax;                          // <= 0: off
+    float* debug_t;
+    float* debug_state;
+    int32_t* debug_cost;
+};
+
+// ---------------------------------------------------------------------------
+// hashing of reflection sequences (MurmurHash3 64-bit finalizer, Appleby)
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t fmix64(uint64_t k) {
+    k ^= k >> 33;
+    k *= 0xff51afd7ed558ccdULL;
+    k ^= k >> 33;
+    k *= 0xc4ceb9fe1a85ec53ULL;
+    k ^= k >> 33;
+    return k;
+}
+static constexpr uint64_t HASH0 = 0x243F6A8885A308D3ULL;
+__device__ __forceinline__ uint64_t hash_step(uint64_t h, int32_t surf) {
+    return fmix64(h + (uint64_t)(uint32_t)(surf + 1) * 0x9E3779B97F4A7C15ULL);
+}
+__device__ __forceinline__ uint64_t record_key(uint64_t h, int32_t rcv, int32_t m) {
+    return fmix64(h ^ ((((uint64_t)(uint32_t)rcv << 32) | (uint32_t)m) * 0xD6E8FEB86659FD93ULL + 1ULL));
+}
+
+// ---------------------------------------------------------------------------
+// ray generation: Fibonacci rule (Sec. 1.2) in FP64, rounded to float32.
+// z_i = 1 - (2i+1)/N, rho = sqrt(1 - z^2), phi = 2 pi frac(i g), g = (3-sqrt5)/2.
+// Explicit _rn intrinsics keep every operation rounded as written.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float3 fibonacci_dir(int64_t i, int64_t N) {
+    const double g = __ddiv_rn(__dsub_rn(3.0, __dsqrt_rn(5.0)), 2.0);
+    double z = __dsub_rn(1.0, __ddiv_rn((double)(2 * i + 1), (double)N));
+    double rho = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(z, z)));
+    double f = __dmul_rn((double)i, g);
+    f = __dsub_rn(f, floor(f));
+    double phi = __dmul_rn(6.283185307179586, f);
+    double s, c;
+    sincos(phi, &s, &c);
+    return make_float3((float)__dmul_rn(rho, c), (float)__dmul_rn(rho, s), (float)z);
+}
+
+// Queue order of the primary rays: Fibonacci indices j, j+F, j+2F, ... (F a
+// Fibonacci number near sqrt(count)) lie along one spiral arm of the lattice,
+// so consecutive queue slots (one warp) get neighbouring directions.  The
+// map slot -> index is a bijection of [0, count); results do not depend on it.
+__device__ __forceinline__ int64_t coherent_offset(int64_t r, int64_t count, int64_t F) {
+    const int64_t q = count / F, rem = count % F;
+    int64_t j, k;
+    if (r < rem * (q + 1)) {
+        j = r / (q + 1);
+        k = r % (q + 1);
+    } else {
+        const int64_t r2 = r - rem * (q + 1);
+        j = rem + r2 / q;
+        k = r2 % q;
+    }
+    return j + k * F;
+}
+
+__global__ void k_gen_rays(Queue q, const float* __restrict__ src, int64_t n_traced, int64_t per_src,
+                           int64_t ray_begin, int64_t N, int64_t F) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_traced) return;
+    int64_t s = r / per_src;
+    int64_t off = coherent_offset(r % per_src, per_src, F);
+    int64_t i = ray_begin + off;
+    float3 u = fibonacci_dir(i, N);
+    float e = (float)(1.0 / (double)N);
+    q.o[r] = make_float4(src[3 * s], src[3 * s + 1], src[3 * s + 2], 0.f);
+    q.d[r] = make_float4(u.x, u.y, u.z, 0.f);
+    q.e0[r] = make_float4(e, e, e, e);
+    q.e1[r] = make_float4(e, e, e, e);
+    q.m[r] = make_uint4((unsigned)(s * per_src + off), 0xFFFFFFFFu, (unsigned)(HASH0 & 0xFFFFFFFFu),
+                        (unsigned)(HASH0 >> 32));
+}
+
+// ---------------------------------------------------------------------------
+// nearest hit
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float comp(const float3& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+struct RayPre {
+    float3 o, d, inv;
+    int kx, ky, kz;
+    float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ RayPre ray_pre(float3 o, float3 d) {
+    RayPre p;
+    p.o = o;
+    p.d = d;
+    // zero components become tiny so that 1/d stays finite (no 0 * inf)
+    float dx = fabsf(d.x) > 1e-30f ? d.x : copysignf(1e-30f, d.x);
+    float dy = fabsf(d.y) > 1e-30f ? d.y : copysignf(1e-30f, d.y);
+    float dz = fabsf(d.z) > 1e-30f ? d.z : copysignf(1e-30f, d.z);
+    p.inv = make_float3(1.0f / dx, 1.0f / dy, 1.0f / dz);
+    float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    int kz = (ax > ay) ? ((ax > az) ? 0 : 2) : ((ay > az) ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    if (comp(d, kz) < 0.f) {
+        int t = kx;
+        kx = ky;
+        ky = t;
+    }
+    p.kx = kx;
+    p.ky = ky;
+    p.kz = kz;
+    float dkz = comp(d, kz);
+    p.Sx = __fdiv_rn(comp(d, kx), dkz);
+    p.Sy = __fdiv_rn(comp(d, ky), dkz);
+    p.Sz = __fdiv_rn(1.0f, dkz);
+    return p;
+}
+
+// slab test of one box; returns entry distance, or +inf on a miss.
+// (lo - o) * (1/d) has a relative error of a few ulps of t itself, which the
+// conservative margin on tmax covers (Ize 2013).
+__device__ __forceinline__ float slab(const RayPre& r, float lx, float ly, float lz, float hx, float hy, float hz,
+                                      float tfar) {
+    float tx0 = __fmul_rn(__fsub_rn(lx, r.o.x), r.inv.x), tx1 = __fmul_rn(__fsub_rn(hx, r.o.x), r.inv.x);
+    float ty0 = __fmul_rn(__fsub_rn(ly, r.o.y), r.inv.y), ty1 = __fmul_rn(__fsub_rn(hy, r.o.y), r.inv.y);
+    float tz0 = __fmul_rn(__fsub_rn(lz, r.o.z), r.inv.z), tz1 = __fmul_rn(__fsub_rn(hz, r.o.z), r.inv.z);
+    float tmin = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+    float tmax = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tfar));
+    return (tmin <= tmax * 1.0000005f) ? tmin : INFINITY;
+}
+
+// watertight test; updates (best_t, best_id) on a nearer hit or an equal-
+// distance hit of a lower triangle id
+__device__ __forceinline__ void tri_test(const RayPre& r, const float4* __restrict__ tp, int exclude_surf,
+                                         float& best_t, int& best_id) {
+    float4 A4 = __ldg(tp), B4 = __ldg(tp + 1), C4 = __ldg(tp + 2);
+    int id = __float_as_int(A4.w);
+    // a ray leaving a planar surface cannot meet that plane again
+    if (__float_as_int(B4.w) == exclude_surf) return;
+    float3 A = make_float3(__fsub_rn(A4.x, r.o.x), __fsub_rn(A4.y, r.o.y), __fsub_rn(A4.z, r.o.z));
+    float3 B = make_float3(__fsub_rn(B4.x, r.o.x), __fsub_rn(B4.y, r.o.y), __fsub_rn(B4.z, r.o.z));
+    float3 C = make_float3(__fsub_rn(C4.x, r.o.x), __fsub_rn(C4.y, r.o.y), __fsub_rn(C4.z, r.o.z));
+    float Akz = comp(A, r.kz), Bkz = comp(B, r.kz), Ckz = comp(C, r.kz);
+    float Ax = __fsub_rn(comp(A, r.kx), __fmul_rn(r.Sx, Akz)), Ay = __fsub_rn(comp(A, r.ky), __fmul_rn(r.Sy, Akz));
+    float Bx = __fsub_rn(comp(B, r.kx), __fmul_rn(r.Sx, Bkz)), By = __fsub_rn(comp(B, r.ky), __fmul_rn(r.Sy, Bkz));
+    float Cx = __fsub_rn(comp(C, r.kx), __fmul_rn(r.Sx, Ckz)), Cy = __fsub_rn(comp(C, r.ky), __fmul_rn(r.Sy, Ckz));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        double u = __dsub_rn(__dmul_rn((double)Cx, (double)By), __dmul_rn((double)Cy, (double)Bx));
+        double v = __dsub_rn(__dmul_rn((double)Ax, (double)Cy), __dmul_rn((double)Ay, (double)Cx));
+        double w = __dsub_rn(__dmul_rn((double)Bx, (double)Ay), __dmul_rn((double)By, (double)Ax));
+        U = (float)u;
+        V = (float)v;
+        W = (float)w;
+        // keep the sign of tiny non-zero double values
+        if (U == 0.0f && u != 0.0) U = u > 0 ? 1e-45f : -1e-45f;
+        if (V == 0.0f && v != 0.0) V = v > 0 ? 1e-45f : -1e-45f;
+        if (W == 0.0f && w != 0.0) W = w > 0 ? 1e-45f : -1e-45f;
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return;
+    float det = __fadd_rn(__fadd_rn(U, V), W);
+    if (det == 0.0f) return;
+    float Az = __fmul_rn(r.Sz, Akz), Bz = __fmul_rn(r.Sz, Bkz), Cz = __fmul_rn(r.Sz, Ckz);
+    float T = __fadd_rn(__fadd_rn(__fmul_rn(U, Az), __fmul_rn(V, Bz)), __fmul_rn(W, Cz));
+    if (det < 0.0f) {
+        T = -T;
+        det = -det;
+    }
+    if (!(T > 0.0f)) return;
+    if (T > best_t * det * 1.000001f) return;  // cheap reject before the division
+    float t = __fdiv_rn(T, det);
+    if (t < best_t || (t == best_t && id < best_id)) {
+        best_t = t;
+        best_id = id;
+    }
+}
+
+// traversal stack in shared memory: STACK_SMEM entries per thread, laid out
+// [entry][thread] so that lanes at the same depth hit different banks
+static constexpr int BOUNCE_THREADS = 128;
+static constexpr int STACK_SMEM = 48;
+
+// Nearest hit, while-while traversal with postponed leaves (Aila & Laine
+// 2009): a lane that meets a leaf keeps it aside and goes on descending
+// until every lane of the warp holds a leaf, then all lanes test triangles
+// together.  Child references: >= 0 internal node, < 0 leaf
+// ~(first_triangle << 3 | count).
+__device__ __forceinline__ void nearest_hit(const BounceArgs& a, const RayPre& r, int exclude, float& best_t,
+                                            int& best_id, unsigned int& err, int& n_nodes, int& n_tests,
+                                            int* __restrict__ stack) {
+    const int SENTINEL = 0x7FFFFFFF;
+    int sp = 0;
+    int node = 0;
+    int leaf = 0;
+    int steps = 0;
+    best_t = INFINITY;
+    best_id = 0x7FFFFFFF;
+    while (node != SENTINEL) {
+        while ((unsigned)node < (unsigned)SENTINEL) {
+            if (++steps > a.step_cap) {
+                err |= ST_STEPS;
+                node = SENTINEL;
+                leaf = 0;
+                break;
+            }
+            if ((int64_t)node >= a.n_nodes) {  // never read outside the node array
+                err |= ST_BOUNDS;
+                node = SENTINEL;
+                leaf = 0;
+                break;
+            }
+            const float4* np = a.nodes + 4 * (int64_t)node;
+            const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
+            n_nodes++;
+            const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
+            const float t0 = slab(r, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, best_t);
+            const float t1 = slab(r, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, best_t);
+            const bool h0 = t0 < INFINITY, h1 = t1 < INFINITY;
+            if (!h0 && !h1) {
+                node = sp > 0 ? stack[--sp * BOUNCE_THREADS] : SENTINEL;
+            } else {
+                const bool swap = h1 && (!h0 || t1 < t0);  // nearest child first
+                node = swap ? r1 : r0;
+                if (h0 && h1) {
+                    if (sp >= STACK_SMEM) {
+                        err |= ST_STACK;
+                        node = SENTINEL;
+                        leaf = 0;
+                        break;
+                    }
+                    stack[sp++ * BOUNCE_THREADS] = swap ? r0 : r1;
+                }
+            }
+            if (node < 0 && leaf == 0) {  // postpone the leaf, keep descending
+                leaf = node;
+                node = sp > 0 ? stack[--sp * BOUNCE_THREADS] : SENTINEL;
+            }
+            if (__all_sync(__activemask(), leaf != 0)) break;
+        }
+        while (leaf != 0) {
+            const int code = ~leaf;
+            const int first = code >> 3, cnt = code & 7;
+            if ((int64_t)first + cnt > a.n_tris) {
+                err |= ST_BOUNDS;
+                node = SENTINEL;
+                break;
+            }
+            for (int k = 0; k < cnt; k++) tri_test(r, a.tris + 3 * (int64_t)(first + k), exclude, best_t, best_id);
+            n_tests += cnt;
+            leaf = 0;
+            if (node < 0) {  // a leaf popped from the stack
+                leaf = node;
+                node = sp > 0 ? stack[--sp * BOUNCE_THREADS] : SENTINEL;
+            }
+        }
+    }
+    if (best_id == 0x7FFFFFFF) best_id = -1;
+}
+
+struct RayState {
+    float4 o, d, e0, e1;
+    uint4 m;
+};
+
+__device__ __forceinline__ void load_ray(const Queue& q, unsigned int slot, RayState& s) {
+    s.o = q.o[slot];
+    s.d = q.d[slot];
+    s.e0 = q.e0[slot];
+    s.e1 = q.e1[slot];
+    s.m = q.m[slot];
+}
+
+// One bounce of the ray in s (bounce index bb).  Every lane of the warp calls
+// it; lanes without a ray pass active = false.  Returns true if the ray goes on.
+__device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool active, int bb, RayState& s,
+                                         int* __restrict__ stack) {
+    const int q = (int)s.m.x;
+    float best_t = INFINITY;
+    int hit = -1;
+    unsigned int err = 0;
+    float4 o4 = s.o, d4 = s.d;
+    RayPre rp = ray_pre(make_float3(o4.x, o4.y, o4.z), make_float3(d4.x, d4.y, d4.z));
+    int n_nodes = 0, n_tests = 0;
+    if (active) nearest_hit(a, rp, (int)s.m.y, best_t, hit, err, n_nodes, n_tests, stack);
+    if (err) atomicOr(a.status, err);
+    const unsigned int amask = __ballot_sync(0xffffffffu, active);
+    if (lane == 0 && amask) atomicAdd(a.n_queries, (unsigned long long)__popc(amask));
+    const float seg = hit >= 0 ? best_t : INFINITY;
+    // -- measurement spheres of this ray's source (eq. 22) -----------------
+    // each sphere test is evaluated once; crossings of one receiver slot are
+    // appended with one atomic per warp
+    const int src = active ? (int)(q / a.per_src) : 0;
+    const int rb = active ? a.rcv_beg[src] : 0;
+    const int nk = active ? a.rcv_beg[src + 1] - rb : 0;
+    const int nk_max = __reduce_max_sync(0xffffffffu, (unsigned)nk);
+    const uint64_t hseq = ((uint64_t)s.m.w << 32) | s.m.z;
+    for (int j = 0; j < nk_max; j++) {
+        bool x = false;
+        float lc = 0.f;
+        int rid = 0;
+        if (j < nk) {
+            float4 c = __ldg(a.rcv + rb + j);
+            float wx = c.x - o4.x, wy = c.y - o4.y, wz = c.z - o4.z;
+            float ts = fminf(fmaxf(wx * d4.x + wy * d4.y + wz * d4.z, 0.0f), seg);
+            float qx = fmaf(ts, d4.x, o4.x) - c.x, qy = fmaf(ts, d4.y, o4.y) - c.y, qz = fmaf(ts, d4.z, o4.z) - c.z;
+            lc = o4.w + ts;
+            x = (qx * qx + qy * qy + qz * qz <= c.w) && (a.dmax <= 0.0f || lc <= a.dmax);
+            rid = __ldg(a.rcv_id + rb + j);
+        }
+        const unsigned int msk = __ballot_sync(0xffffffffu, x);
+        if (msk) {
+            const int leader = __ffs(msk) - 1;
+            unsigned long long rbase = 0;
+            if (lane == leader) rbase = atomicAdd(a.n_rec, (unsigned long long)__popc(msk));
+            rbase = __shfl_sync(0xffffffffu, rbase, leader);
+            const unsigned long long pos = rbase + __popc(msk & ((1u << lane) - 1u));
+            if (x && pos < a.rec_cap) {
+                a.rec_rcv[pos] = rid;
+                a.rec_ray[pos] = q;
+                a.rec_m[pos] = bb;
+                a.rec_len[pos] = lc;
+                a.rec_key[pos] = record_key(hseq, rid, bb);
+            }
+        }
+    }
+    if (!active) return false;
+    bool survive = false;
+    const int64_t hb = (int64_t)bb * a.n_traced + q;
+    a.hist[hb] = hit;
+    if (a.debug_t) a.debug_t[hb] = seg;
+    if (a.debug_cost) {
+        a.debug_cost[2 * hb] = n_nodes;
+        a.debug_cost[2 * hb + 1] = n_tests;
+    }
+    if (a.debug_state) {
+        float* ds = a.debug_state + hb * 6;
+        ds[0] = o4.x, ds[1] = o4.y, ds[2] = o4.z, ds[3] = d4.x, ds[4] = d4.y, ds[5] = d4.z;
+    }
+    if (hit >= 0) {
+        // reflect (eq. 15), absorb (eq. 16), path length (Kahan), hash
+        float4 nr = __ldg(a.tri_nrm + hit);
+        int surf = __float_as_int(nr.w);
+        float dn = d4.x * nr.x + d4.y * nr.y + d4.z * nr.z;
+        // next origin: the hit point pulled back along the incoming ray by
+        // about four ulps of the largest coordinate
+        float px = fmaf(best_t, d4.x, o4.x), py = fmaf(best_t, d4.y, o4.y), pz = fmaf(best_t, d4.z, o4.z);
+        float scale = fmaxf(fmaxf(fabsf(px), fabsf(py)), fmaxf(fabsf(pz), 1e-3f));
+        float tb = fmaxf(best_t - scale * 4.76837158e-7f, 0.0f);  // 2^-21
+        o4.x = fmaf(tb, d4.x, o4.x);
+        o4.y = fmaf(tb, d4.y, o4.y);
+        o4.z = fmaf(tb, d4.z, o4.z);
+        float rx = d4.x - 2.0f * dn * nr.x, ry = d4.y - 2.0f * dn * nr.y, rz = d4.z - 2.0f * dn * nr.z;
+        float inv = rsqrtf(rx * rx + ry * ry + rz * rz);
+        float y = best_t - d4.w;
+        float t = o4.w + y;
+        d4.w = (t - o4.w) - y;
+        o4.w = t;
+        d4.x = rx * inv;
+        d4.y = ry * inv;
+        d4.z = rz * inv;
+        const float* rf = a.refl + 8 * a.mat_of_surf[surf];
+        s.e0.x *= __ldg(rf + 0);
+        s.e0.y *= __ldg(rf + 1);
+        s.e0.z *= __ldg(rf + 2);
+        s.e0.w *= __ldg(rf + 3);
+        s.e1.x *= __ldg(rf + 4);
+        s.e1.y *= __ldg(rf + 5);
+        s.e1.z *= __ldg(rf + 6);
+        s.e1.w *= __ldg(rf + 7);
+        uint64_t h = hash_step(hseq, surf);
+        s.m.y = (unsigned int)surf;
+        s.m.z = (unsigned int)(h & 0xFFFFFFFFu);
+        s.m.w = (unsigned int)(h >> 32);
+        s.o = o4;
+        s.d = d4;
+        survive = (bb + 1 < a.B) && !(a.dmax > 0.0f && o4.w > a.dmax) && !err;
+    }
+    if (!survive) {
+        a.ray_e[2 * (int64_t)q] = s.e0;
+        a.ray_e[2 * (int64_t)q + 1] = s.e1;
+        a.ray_len[q] = s.o.w;
+        a.ray_hits[q] = bb + (hit >= 0 ? 1 : 0);
+    }
+    return survive;
+}
+
+// ---------------------------------------------------------------------------
+// the bounce kernel
+//   wavefront mode (live rays > tail threshold): one bounce per ray, survivors
+//   compacted into the next queue with one atomic per warp;
+//   tail mode (few live rays): this launch finishes every remaining bounce,
+//   lanes whose ray dies fetch the next one, so the last bounces do not each
+//   wait for their slowest ray.  It writes no survivors, so the later
+//   launches of the same trace find no live rays and return at once.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(BounceArgs a) {
+    __shared__ int s_stack[STACK_SMEM * BOUNCE_THREADS];
+    int* stack = s_stack + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const unsigned int n_live = a.live[a.b];
+    const int b = a.b;
+    if (n_live == 0) return;
+    if (n_live > a.tail_threshold) {
+        for (;;) {
+            unsigned int base = 0;
+            if (lane == 0) base = atomicAdd(&a.fetch[b], 32u);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (base >= n_live) break;
+            const unsigned int slot = base + lane;
+            const bool active = slot < n_live;
+            RayState s;
+            s.o = make_float4(0, 0, 0, 0);
+            s.d = make_float4(0, 0, 1, 0);
+            s.e0 = s.e1 = s.o;
+            s.m = make_uint4(0, 0xFFFFFFFFu, 0, 0);
+            if (active) load_ray(a.in, slot, s);
+            const bool survive = step_ray(a, lane, active, b, s, stack);
+            const unsigned int mask = __ballot_sync(0xffffffffu, survive);
+            if (mask) {
+                unsigned int obase = 0;
+                const int leader = __ffs(mask) - 1;
+                if (lane == leader) obase = atomicAdd(&a.live[b + 1], (unsigned int)__popc(mask));
+                obase = __shfl_sync(0xffffffffu, obase, leader);
+                if (survive) {
+                    unsigned int p = obase + __popc(mask & ((1u << lane) - 1u));
+                    a.out.o[p] = s.o;
+                    a.out.d[p] = s.d;
+                    a.out.e0[p] = s.e0;
+                    a.out.e1[p] = s.e1;
+                    a.out.m[p] = s.m;
+                }
+            }
+        }
+        return;
+    }
+    // tail mode
+    RayState s;
+    s.o = make_float4(0, 0, 0, 0);
+    s.d = make_float4(0, 0, 1, 0);
+    s.e0 = s.e1 = s.o;
+    s.m = make_uint4(0, 0xFFFFFFFFu, 0, 0);
+    bool has = false, exhausted = false;
+    int bb = b;
+    for (int iter = 0; iter < 1 << 30; iter++) {
+        const unsigned int need = __ballot_sync(0xffffffffu, !has);
+        if (need && !exhausted) {
+            unsigned int base = 0;
+            const int leader = __ffs(need) - 1;
+            if (lane == leader) base = atomicAdd(&a.fetch[b], (unsigned int)__popc(need));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (!has) {
+                const unsigned int slot = base + __popc(need & ((1u << lane) - 1u));
+                if (slot < n_live) {
+                    load_ray(a.in, slot, s);
+                    bb = b;
+                    has = true;
+                }
+            }
+            exhausted = base + __popc(need) >= n_live;
+        }
+        if (__ballot_sync(0xffffffffu, has) == 0) break;
+        const bool survive = step_ray(a, lane, has, bb, s, stack);
+        if (has) {
+            if (survive)
+                bb++;
+            else
+                has = false;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// image sources
+// ---------------------------------------------------------------------------
+__global__ void k_dedup_init(const uint64_t* __restrict__ rec_key, int64_t n, uint64_t* __restrict__ keys,
+                             uint32_t* __restrict__ vals) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    keys[i] = rec_key[i];
+    vals[i] = (uint32_t)i;
+}
+
+__device__ __forceinline__ bool same_beam(int64_t ra, int64_t rb, const int32_t* rec_rcv, const int32_t* rec_ray,
+                                          const int32_t* rec_m, const int32_t* hist, const int32_t* surf_of,
+                                          int64_t n_traced) {
+    if (rec_rcv[ra] != rec_rcv[rb] || rec_m[ra] != rec_m[rb]) return false;
+    int m = rec_m[ra];
+    int64_t qa = rec_ray[ra], qb = rec_ray[rb];
+    for (int k = 0; k < m; k++) {
+        int ta = hist[(int64_t)k * n_traced + qa], tb = hist[(int64_t)k * n_traced + qb];
+        if (ta < 0 || tb < 0 || surf_of[ta] != surf_of[tb]) return false;
+    }
+    return true;
+}
+
+__global__ void k_seg_flags(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n,
+                            const int32_t* __restrict__ rec_rcv, const int32_t* __restrict__ rec_ray,
+                            const int32_t* __restrict__ rec_m, const int32_t* __restrict__ hist,
+                            const int32_t* __restrict__ surf_of, int64_t n_traced, uint32_t* __restrict__ flags,
+                            unsigned long long* collisions) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    uint32_t f = 1;
+    if (j > 0 && keys[j] == keys[j - 1]) {
+        f = 0;
+        if (!same_beam(vals[j - 1], vals[j], rec_rcv, rec_ray, rec_m, hist, surf_of, n_traced)) {
+            f = 1;
+            atomicAdd(collisions, 1ull);
+        }
+    }
+    flags[j] = f;
+}
+
+// lowest ray index of every beam (atomicMin over the beam's records); the
+// exclusive scan of the head flags gives a record's beam as segid + flag - 1
+__global__ void k_seg_min(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ flags,
+                          const uint32_t* __restrict__ segid, int64_t n, const int32_t* __restrict__ rec_ray,
+                          int32_t* __restrict__ rep) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) atomicMin(rep + (segid[j] + flags[j] - 1u), rec_ray[vals[j]]);
+}
+
+__global__ void k_seg_heads(const uint32_t* __restrict__ flags, const uint32_t* __restrict__ segid, int64_t n,
+                            uint32_t* __restrict__ heads) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    if (flags[j]) heads[segid[j]] = (uint32_t)j;
+    if (j == n - 1) heads[segid[j] + flags[j]] = (uint32_t)n;
+}
+
+struct ReconArgs {
+    const uint32_t* heads;
+    const uint32_t* vals;
+    const unsigned int* n_unique_dev;
+    unsigned int* status;
+    const int32_t* rec_rcv;
+    const int32_t* rec_ray;
+    const int32_t* rec_m;
+    const int32_t* hist;
+    const int32_t* surf_of;
+    const int32_t* mat_of_surf;
+    const Plane* planes;
+    const double* alpha64;   // [n_mat][8]
+    const double* beta64;    // [8]
+    const double* src64;     // [S][3]
+    const double* rcv64;     // [R][3] by original receiver id
+    int64_t n_traced, per_src;
+    double N, c;
+    int32_t *o_rcv, *o_order, *o_count, *o_rep;
+    double *o_pos, *o_dist, *o_time, *o_energy;
+};
+
+// one thread per image source: beam size, representative ray, FP64 mirror chain
+__global__ void k_reconstruct(ReconArgs a) {
+    const unsigned int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= *a.n_unique_dev) return;
+    const uint32_t lo = a.heads[u], hi = a.heads[u + 1];
+    const int32_t rep = a.o_rep[u];  // set by k_seg_min
+    const uint32_t r0 = a.vals[lo];
+    const int32_t rcv = a.rec_rcv[r0], m = a.rec_m[r0];
+    const int64_t s = rep / a.per_src;
+    double x = a.src64[3 * s], y = a.src64[3 * s + 1], z = a.src64[3 * s + 2];
+    double prod[RT_N_BANDS];
+#pragma unroll
+    for (int f = 0; f < RT_N_BANDS; f++) prod[f] = 1.0;
+    for (int k = 0; k < m; k++) {
+        int tri = a.hist[(int64_t)k * a.n_traced + rep];
+        if (tri < 0) {  // cannot happen for a consistent history; reported, never read
+            atomicOr(a.status, ST_HISTORY);
+            break;
+        }
+        int sid = a.surf_of[tri];
+        Plane P = a.planes[sid];
+        double dist = P.x * x + P.y * y + P.z * z - P.w;
+        x -= 2.0 * dist * P.x;
+        y -= 2.0 * dist * P.y;
+        z -= 2.0 * dist * P.z;
+        const double* al = a.alpha64 + 8 * a.mat_of_surf[sid];
+#pragma unroll
+        for (int f = 0; f < RT_N_BANDS; f++) prod[f] *= (1.0 - al[f]);
+    }
+    const double* xm = a.rcv64 + 3 * rcv;
+    double dx = x - xm[0], dy = y - xm[1], dz = z - xm[2];
+    double d = sqrt(dx * dx + dy * dy + dz * dz);
+    double n = (double)(hi - lo);
+    a.o_rcv[u] = rcv;
+    a.o_order[u] = m;
+    a.o_count[u] = (int32_t)(hi - lo);
+    a.o_pos[3 * (int64_t)u] = x;
+    a.o_pos[3 * (int64_t)u + 1] = y;
+    a.o_pos[3 * (int64_t)u + 2] = z;
+    a.o_dist[u] = d;
+    a.o_time[u] = d / a.c;
+#pragma unroll
+    for (int f = 0; f < RT_N_BANDS; f++) a.o_energy[8 * (int64_t)u + f] = (n / a.N) * prod[f] * exp(-a.beta64[f] * d);
+}
+
+static unsigned grid_of(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+struct TraceBuffers {
+    Queue q[2];
+    int32_t* hist;
+    float4* ray_e;
+    float* ray_len;
+    int32_t* ray_hits;
+    int32_t *rec_rcv, *rec_ray, *rec_m;
+    float* rec_len;
+    uint64_t* rec_key;
+    unsigned int* counters;  // live[B+1], fetch[B], status, pad
+    unsigned long long* n_rec;
+};
+
+static rt_status alloc_queue(Arena& ar, Queue& q, int64_t n) {
+    RR_TRY(ar.alloc(&q.o, n));
+    RR_TRY(ar.alloc(&q.d, n));
+    RR_TRY(ar.alloc(&q.e0, n));
+    RR_TRY(ar.alloc(&q.e1, n));
+    RR_TRY(ar.alloc(&q.m, n));
+    return RT_OK;
+}
+
+static rt_status trace_impl(const rt_tree* tree, const rt_sources* src, const rt_receivers* rcv,
+                            const float* alpha, int32_t n_mat, const rt_trace_params* p, rt_image_sources** out) {
+    if (!tree || !src || !rcv || !alpha || !p || !out) {
+        set_error("rt_trace: null argument");
+        return RT_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)p->stream;
+    const int64_t N = p->n_rays;
+    const int B = p->n_bounces;
+    if (N < 1 || B < 1 || B > RT_MAX_BOUNCES || !(p->c > 0) || src->n < 1 || !src->pos || rcv->n < 0 ||
+        (rcv->n > 0 && (!rcv->center || !rcv->radius || !rcv->source_of))) {
+        set_error("rt_trace: need n_rays >= 1, 1 <= n_bounces <= %d, c > 0, >= 1 source", RT_MAX_BOUNCES);
+        return RT_ERR_INVALID_ARG;
+    }
+    if (p->ray_begin < 0 || p->ray_begin >= N) {
+        set_error("rt_trace: ray_begin out of range");
+        return RT_ERR_INVALID_ARG;
+    }
+    const int64_t per_src = p->ray_count > 0 ? p->ray_count : N - p->ray_begin;
+    if (p->ray_begin + per_src > N) {
+        set_error("rt_trace: ray range exceeds n_rays");
+        return RT_ERR_INVALID_ARG;
+    }
+    const int S = src->n, R = rcv->n;
+    const int64_t n_traced = per_src * S;
+    if (n_traced > (int64_t)INT32_MAX) {
+        set_error("rt_trace: %lld rays exceed the 32-bit ray index", (long long)n_traced);
+        return RT_ERR_INVALID_ARG;
+    }
+    if (n_mat < tree->n_materials) {
+        set_error("rt_trace: absorption table has %d materials, mesh uses %d", n_mat, tree->n_materials);
+        return RT_ERR_INVALID_ARG;
+    }
+    for (int64_t k = 0; k < (int64_t)n_mat * RT_N_BANDS; k++)
+        if (!(alpha[k] >= 0.0f && alpha[k] <= 1.0f)) {
+            set_error("rt_trace: absorption coefficients must lie in [0, 1]");
+            return RT_ERR_INVALID_ARG;
+        }
+    for (int k = 0; k < 3 * S; k++)
+        if (!std::isfinite(src->pos[k])) {
+            set_error("rt_trace: non-finite source position");
+            return RT_ERR_INVALID_ARG;
+        }
+    // receivers grouped by source
+    std::vector<int> order((size_t)R);
+    for (int k = 0; k < R; k++) {
+        order[k] = k;
+        if (rcv->source_of[k] < 0 || rcv->source_of[k] >= S || !(rcv->radius[k] > 0) ||
+            !std::isfinite(rcv->center[3 * k]) || !std::isfinite(rcv->center[3 * k + 1]) ||
+            !std::isfinite(rcv->center[3 * k + 2])) {
+            set_error("rt_trace: receiver %d invalid (source index, radius or centre)", k);
+            return RT_ERR_INVALID_ARG;
+        }
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return rcv->source_of[a] < rcv->source_of[b]; });
+    std::vector<float4> h_rcv((size_t)std::max(R, 1));
+    std::vector<int32_t> h_rcv_id((size_t)std::max(R, 1)), h_beg((size_t)S + 1, 0);
+    for (int k = 0; k < R; k++) {
+        int o = order[k];
+        float r = (float)rcv->radius[o];
+        h_rcv[k] = make_float4((float)rcv->center[3 * o], (float)rcv->center[3 * o + 1], (float)rcv->center[3 * o + 2],
+                               r * r);
+        h_rcv_id[k] = o;
+        h_beg[rcv->source_of[o] + 1]++;
+    }
+    for (int k = 0; k < S; k++) h_beg[k + 1] += h_beg[k];
+    std::vector<float> h_src((size_t)3 * S), h_refl((size_t)n_mat * 8);
+    std::vector<double> h_alpha64((size_t)n_mat * 8), h_beta64(8, 0.0);
+    for (int k = 0; k < 3 * S; k++) h_src[k] = (float)src->pos[k];
+    for (int64_t k = 0; k < (int64_t)n_mat * 8; k++) {
+        h_refl[k] = 1.0f - alpha[k];
+        h_alpha64[k] = (double)alpha[k];
+    }
+    if (p->air_beta)
+        for (int f = 0; f < 8; f++) h_beta64[f] = (double)p->air_beta[f];
+
+    Arena tmp(s), keep(s);
+    float4* d_rcv;
+    int32_t *d_rcv_id, *d_beg;
+    float *d_src, *d_refl;
+    double *d_alpha64, *d_beta64, *d_src64, *d_rcv64;
+    RR_TRY(tmp.alloc(&d_rcv, std::max(R, 1)));
+    RR_TRY(tmp.alloc(&d_rcv_id, std::max(R, 1)));
+    RR_TRY(tmp.alloc(&d_beg, S + 1));
+    RR_TRY(tmp.alloc(&d_src, 3 * S));
+    RR_TRY(tmp.alloc(&d_refl, (int64_t)n_mat * 8));
+    RR_TRY(tmp.alloc(&d_alpha64, (int64_t)n_mat * 8));
+    RR_TRY(tmp.alloc(&d_beta64, 8));
+    RR_TRY(tmp.alloc(&d_src64, 3 * S));
+    RR_TRY(tmp.alloc(&d_rcv64, 3 * std::max(R, 1)));
+    RR_CUDA(cudaMemcpyAsync(d_rcv, h_rcv.data(), sizeof(float4) * std::max(R, 1), cudaMemcpyHostToDevice, s));
+    RR_CUDA(cudaMemcpyAsync(d_rcv_id, h_rcv_id.data(), sizeof(int32_t) * std::max(R, 1), cudaMemcpyHostToDevice, s));
+    RR_CUDA(cudaMemcpyAsync(d_beg, h_beg.data(), sizeof(int32_t) * (S + 1), cudaMemcpyHostToDevice, s));
+    RR_CUDA(cudaMemcpyAsync(d_src, h_src.data(), sizeof(float) * 3 * S, cudaMemcpyHostToDevice, s));
+    RR_CUDA(cudaMemcpyAsync(d_refl, h_refl.data(), sizeof(float) * n_mat * 8, cudaMemcpyHostToDevice, s));
+    RR_CUDA(cudaMemcpyAsync(d_alpha64, h_alpha64.data(), sizeof(double) * n_mat * 8, cudaMemcpyHostToDevice, s));
+    RR_CUDA(cudaMemcpyAsync(d_beta64, h_beta64.data(), sizeof(double) * 8, cudaMemcpyHostToDevice, s));
+    RR_CUDA(cudaMemcpyAsync(d_src64, src->pos, sizeof(double) * 3 * S, cudaMemcpyHostToDevice, s));
+    if (R > 0) RR_CUDA(cudaMemcpyAsync(d_rcv64, rcv->center, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, s));
+
+    // per-ray buffers (queues are scratch; history and final state are kept)
+    TraceBuffers tb{};
+    RR_TRY(alloc_queue(tmp, tb.q[0], n_traced));
+    RR_TRY(alloc_queue(tmp, tb.q[1], n_traced));
+    RR_TRY(keep.alloc(&tb.hist, (int64_t)B * n_traced));
+    RR_TRY(keep.alloc(&tb.ray_e, 2 * n_traced));
+    RR_TRY(keep.alloc(&tb.ray_len, n_traced));
+    RR_TRY(keep.alloc(&tb.ray_hits, n_traced));
+    const int n_counters = 2 * B + 4;
+    RR_TRY(tmp.alloc(&tb.counters, n_counters));
+    RR_TRY(tmp.alloc(&tb.n_rec, 2));  // records, queries
+
+    if (p->max_node_visits < 0) {
+        set_error("rt_trace: max_node_visits must be >= 0");
+        return RT_ERR_INVALID_ARG;
+    }
+    const int a_step_cap = p->max_node_visits > 0 ? p->max_node_visits : DEFAULT_NODE_VISITS;
+    const int block = p->block_size > 0 ? p->block_size : BOUNCE_THREADS;
+    if (block != BOUNCE_THREADS) {
+        set_error("rt_trace: block_size must be 0 or %d in this build", BOUNCE_THREADS);
+        return RT_ERR_INVALID_ARG;
+    }
+    int occ = 0;
+    RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bounce, block, 0));
+    const int grid = device_sm_count() * std::max(occ, 1);
+    // below this many live rays one launch finishes the trace (tail mode)
+    const unsigned int tail = p->tail_rays > 0 ? (unsigned int)p->tail_rays
+                            : (p->tail_rays < 0 ? 0u : (unsigned int)grid * (unsigned int)block);
+
+    unsigned long long cap = (unsigned long long)std::min<int64_t>(
+        std::max<int64_t>(1 << 20, 2 * n_traced), std::max<int64_t>(1, n_traced * (int64_t)B * std::max(R, 1)));
+    struct Events {
+        cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+        ~Events() {
+            for (auto x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    for (auto& x : ev.e) RR_CUDA(cudaEventCreate(&x));
+    unsigned long long n_rec = 0, n2[2] = {0, 0};
+    std::vector<unsigned int> h_cnt((size_t)n_counters);
+    Arena rec_arena(s);
+    for (int attempt = 0; attempt < 2; attempt++) {
+        RR_TRY(rec_arena.alloc(&tb.rec_rcv, (int64_t)cap));
+        RR_TRY(rec_arena.alloc(&tb.rec_ray, (int64_t)cap));
+        RR_TRY(rec_arena.alloc(&tb.rec_m, (int64_t)cap));
+        RR_TRY(rec_arena.alloc(&tb.rec_len, (int64_t)cap));
+        RR_TRY(rec_arena.alloc(&tb.rec_key, (int64_t)cap));
+        RR_CUDA(cudaMemsetAsync(tb.hist, 0xFF, sizeof(int32_t) * (size_t)B * n_traced, s));
+        RR_CUDA(cudaMemsetAsync(tb.counters, 0, sizeof(unsigned int) * n_counters, s));
+        RR_CUDA(cudaMemsetAsync(tb.n_rec, 0, 2 * sizeof(unsigned long long), s));
+        unsigned int n0 = (unsigned int)n_traced;
+        RR_CUDA(cudaMemcpyAsync(tb.counters, &n0, sizeof n0, cudaMemcpyHostToDevice, s));
+        RR_CUDA(cudaEventRecord(ev.e[0], s));
+        int64_t F = 1, F1 = 1;  // largest Fibonacci number <= sqrt(per_src)
+        while (F1 * F1 <= per_src) {
+            int64_t t = F + F1;
+            F = F1;
+            F1 = t;
+        }
+        RR_LAUNCH(k_gen_rays, grid_of(n_traced, 256), 256, 0, s, tb.q[0], d_src, n_traced, per_src, p->ray_begin, N, F);
+        RR_CUDA(cudaGetLastError());
+        RR_CUDA(cudaEventRecord(ev.e[1], s));
+        BounceArgs a{};
+        a.nodes = tree->nodes;
+        a.tris = tree->tris;
+        a.n_nodes = tree->n_nodes;
+        a.n_tris = tree->n_tris;
+        a.tri_nrm = tree->tri_nrm;
+        a.mat_of_surf = tree->mat_of_surf;
+        a.refl = d_refl;
+        a.rcv = d_rcv;
+        a.rcv_id = d_rcv_id;
+        a.rcv_beg = d_beg;
+        a.hist = tb.hist;
+        a.ray_e = tb.ray_e;
+        a.ray_len = tb.ray_len;
+        a.ray_hits = tb.ray_hits;
+        a.rec_rcv = tb.rec_rcv;
+        a.rec_ray = tb.rec_ray;
+        a.rec_m = tb.rec_m;
+        a.rec_len = tb.rec_len;
+        a.rec_key = tb.rec_key;
+        a.rec_cap = cap;
+        a.live = tb.counters;
+        a.fetch = tb.counters + (B + 1);
+        a.status = tb.counters + (2 * B + 1);
+        a.n_rec = tb.n_rec;
+        a.n_queries = tb.n_rec + 1;
+        a.tail_threshold = tail;
+        a.n_traced = n_traced;
+        a.per_src = per_src;
+        a.B = B;
+        a.dmax = (float)(p->max_distance > 0 ? p->max_distance : 0.0);
+        a.step_cap = a_step_cap;
+        a.debug_t = p->debug_t;
+        a.debug_state = p->debug_state;
+        a.debug_cost = p->debug_cost;
+        for (int b = 0; b < B; b++) {
+            a.b = b;
+            a.in = tb.q[b & 1];
+            a.out = tb.q[(b + 1) & 1];
+            RR_LAUNCH(k_bounce, grid, block, 0, s, a);
+        }
+        RR_CUDA(cudaGetLastError());
+        RR_CUDA(cudaEventRecord(ev.e[2], s));
+        RR_CUDA(cudaMemcpyAsync(h_cnt.data(), tb.counters, sizeof(unsigned int) * n_counters, cudaMemcpyDeviceToHost, s));
+        RR_CUDA(cudaMemcpyAsync(n2, tb.n_rec, sizeof n2, cudaMemcpyDeviceToHost, s));
+        RR_CUDA(cudaStreamSynchronize(s));
+        n_rec = n2[0];
+        unsigned int st = h_cnt[2 * B + 1];
+        if (st & ST_STACK) {
+            set_error("rt_trace: traversal stack overflow (tree deeper than %d)", STACK_SMEM);
+            return RT_ERR_STACK;
+        }
+        if (st & ST_BOUNDS) {
+            set_error("rt_trace: traversal met a node or leaf reference outside the tree");
+            return RT_ERR_INTERNAL;
+        }
+        if (st & ST_STEPS) {
+            set_error("rt_trace: a traversal exceeded %d node visits", a_step_cap);
+            return RT_ERR_STEP_LIMIT;
+        }
+        if (n_rec <= cap) break;
+        if (attempt == 1) {
+            set_error("rt_trace: %llu records exceed the capacity %llu", n_rec, cap);
+            return RT_ERR_CAPACITY;
+        }
+        // second attempt with the exact capacity
+        for (void* ptr : rec_arena.release()) dev_free(ptr, s);
+        cap = n_rec;
+    }
+    const int64_t queries = (int64_t)n2[1];
+
+    // -- dedup + reconstruction ---------------------------------------------
+    const int64_t nr = (int64_t)n_rec;
+    rt_image_sources* is = new rt_image_sources();
+    struct Guard {
+        rt_image_sources*& p;
+        ~Guard() {
+            if (p) {
+                for (void* q : p->owned) dev_free(q, p->stream);
+                delete p;
+            }
+        }
+    } guard{is};
+    is->stream = s;
+    is->n_rcv = R;
+    is->c = p->c;
+    int32_t *o_rcv, *o_order, *o_count, *o_rep;
+    double *o_pos, *o_dist, *o_time, *o_energy;
+    const int64_t ncap = std::max<int64_t>(nr, 1);
+    RR_TRY(keep.alloc(&o_rcv, ncap));
+    RR_TRY(keep.alloc(&o_order, ncap));
+    RR_TRY(keep.alloc(&o_count, ncap));
+    RR_TRY(keep.alloc(&o_rep, ncap));
+    RR_TRY(keep.alloc(&o_pos, 3 * ncap));
+    RR_TRY(keep.alloc(&o_dist, ncap));
+    RR_TRY(keep.alloc(&o_time, ncap));
+    RR_TRY(keep.alloc(&o_energy, 8 * ncap));
+    unsigned int n_unique = 0;
+    unsigned long long collisions = 0;
+    if (nr > 0) {
+        uint64_t *keys, *keys_alt;
+        uint32_t *vals, *vals_alt, *flags, *segid, *heads, *nuniq;
+        unsigned long long* d_coll;
+        RR_TRY(tmp.alloc(&keys, nr));
+        RR_TRY(tmp.alloc(&keys_alt, nr));
+        RR_TRY(tmp.alloc(&vals, nr));
+        RR_TRY(tmp.alloc(&vals_alt, nr));
+        RR_TRY(tmp.alloc(&flags, nr));
+        RR_TRY(tmp.alloc(&segid, nr));
+        RR_TRY(tmp.alloc(&heads, nr + 1));
+        RR_TRY(tmp.alloc(&nuniq, 1));
+        RR_TRY(tmp.alloc(&d_coll, 1));
+        void *sort_tmp, *scan_tmp;
+        RR_TRY(tmp.alloc((char**)&sort_tmp, sort_temp_bytes(nr)));
+        RR_TRY(tmp.alloc((char**)&scan_tmp, scan_temp_bytes(nr)));
+        RR_CUDA(cudaMemsetAsync(d_coll, 0, sizeof(unsigned long long), s));
+        RR_LAUNCH(k_dedup_init, grid_of(nr, 256), 256, 0, s, tb.rec_key, nr, keys, vals);
+        RR_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, nr, 0, 64, sort_tmp, s));
+        RR_LAUNCH(k_seg_flags, grid_of(nr, 256), 256, 0, s, keys, vals, nr, tb.rec_rcv, tb.rec_ray, tb.rec_m, tb.hist,
+                                                     tree->surf_of, n_traced, flags, d_coll);
+        RR_CUDA(cudaGetLastError());
+        RR_TRY(exclusive_scan_u32(flags, segid, nr, nuniq, scan_tmp, s));
+        RR_LAUNCH(k_seg_heads, grid_of(nr, 256), 256, 0, s, flags, segid, nr, heads);
+        RR_CUDA(cudaMemsetAsync(o_rep, 0x7F, sizeof(int32_t) * nr, s));
+        RR_LAUNCH(k_seg_min, grid_of(nr, 256), 256, 0, s, vals, flags, segid, nr, tb.rec_ray, o_rep);
+        ReconArgs ra;
+        ra.heads = heads;
+        ra.vals = vals;
+        ra.n_unique_dev = nuniq;
+        ra.status = tb.counters + (2 * B + 1);
+        ra.rec_rcv = tb.rec_rcv;
+        ra.rec_ray = tb.rec_ray;
+        ra.rec_m = tb.rec_m;
+        ra.hist = tb.hist;
+        ra.surf_of = tree->surf_of;
+        ra.mat_of_surf = tree->mat_of_surf;
+        ra.planes = tree->planes;
+        ra.alpha64 = d_alpha64;
+        ra.beta64 = d_beta64;
+        ra.src64 = d_src64;
+        ra.rcv64 = d_rcv64;
+        ra.n_traced = n_traced;
+        ra.per_src = per_src;
+        ra.N = (double)N;
+        ra.c = p->c;
+        ra.o_rcv = o_rcv, ra.o_order = o_order, ra.o_count = o_count, ra.o_rep = o_rep;
+        ra.o_pos = o_pos, ra.o_dist = o_dist, ra.o_time = o_time, ra.o_energy = o_energy;
+        RR_LAUNCH(k_reconstruct, grid_of(nr, 128), 128, 0, s, ra);
+        RR_CUDA(cudaGetLastError());
+        RR_CUDA(cudaMemcpyAsync(&n_unique, nuniq, sizeof n_unique, cudaMemcpyDeviceToHost, s));
+        RR_CUDA(cudaMemcpyAsync(&collisions, d_coll, sizeof collisions, cudaMemcpyDeviceToHost, s));
+        RR_CUDA(cudaEventRecord(ev.e[3], s));
+        unsigned int st = 0;
+        RR_CUDA(cudaMemcpyAsync(&st, ra.status, sizeof st, cudaMemcpyDeviceToHost, s));
+        RR_CUDA(cudaStreamSynchronize(s));
+        if (st & ST_HISTORY) {
+            set_error("rt_trace: an image source's ray has no hit history");
+            return RT_ERR_INTERNAL;
+        }
+    }
+    rt_is_view& v = is->v;
+    v.n = n_unique;
+    v.rcv = o_rcv;
+    v.order = o_order;
+    v.count = o_count;
+    v.rep_ray = o_rep;
+    v.pos = o_pos;
+    v.dist = o_dist;
+    v.time = o_time;
+    v.energy = o_energy;
+    v.n_traced = n_traced;
+    v.n_bounces = B;
+    v.hist = tb.hist;
+    v.ray_energy = (const float*)tb.ray_e;
+    v.ray_length = tb.ray_len;
+    v.ray_hits = tb.ray_hits;
+    v.n_records = nr;
+    v.rec_rcv = tb.rec_rcv;
+    v.rec_ray = tb.rec_ray;
+    v.rec_order = tb.rec_m;
+    v.rec_length = tb.rec_len;
+    v.queries = queries;
+    v.hash_collisions = (int64_t)collisions;
+    cudaEventElapsedTime(&v.ms_rays, ev.e[0], ev.e[1]);
+    cudaEventElapsedTime(&v.ms_bounces, ev.e[1], ev.e[2]);
+    if (nr > 0) cudaEventElapsedTime(&v.ms_image_sources, ev.e[2], ev.e[3]);
+    cudaGetLastError();
+    is->owned = keep.release();
+    for (void* ptr : rec_arena.release()) is->owned.push_back(ptr);
+    *out = is;
+    is = nullptr;
+    return RT_OK;
+}
+
+}  // namespace rr
+
+extern "C" rt_status rt_trace(const rt_tree* tree, const rt_sources* src, const rt_receivers* rcv,
+                              const float* band_absorption, int32_t n_materials, const rt_trace_params* params,
+                              rt_image_sources** out) {
+    rr::clear_error();
+    return rr::trace_impl(tree, src, rcv, band_absorption, n_materials, params, out);
+}
+
+extern "C" rt_status rt_image_sources_view(const rt_image_sources* is, rt_is_view* out) {
+    if (!is || !out) {
+        rr::set_error("rt_image_sources_view: null argument");
+        return RT_ERR_INVALID_ARG;
+    }
+    *out = is->v;
+    return RT_OK;
+}
+
+extern "C" void rt_image_sources_free(rt_image_sources* is) {
+    if (!is) return;
+    for (void* p : is->owned) rr::dev_free(p, is->stream);
+    delete is;
+}

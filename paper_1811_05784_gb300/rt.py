@@ -1,0 +1,350 @@
+"""Thin Python binding of libroomrays (include/roomrays.h), same names.
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+Host inputs may be numpy arrays or CPU torch tensors (pinned or not);
+device inputs are CUDA torch tensors.  Device outputs are exposed as torch
+tensors that keep their owning handle alive.  There is no CPU fallback: if
+the compiled library is missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libroomrays.so")
+N_BANDS = 8
+
+RT_OK, RT_ERR_INVALID_ARG, RT_ERR_DEGENERATE_MESH, RT_ERR_OOM, RT_ERR_CUDA, RT_ERR_CAPACITY, \
+    RT_ERR_STEP_LIMIT, RT_ERR_STACK, RT_ERR_INTERNAL = range(9)
+STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_DEGENERATE_MESH", 3: "RT_ERR_OOM",
+                4: "RT_ERR_CUDA", 5: "RT_ERR_CAPACITY", 6: "RT_ERR_STEP_LIMIT", 7: "RT_ERR_STACK",
+                8: "RT_ERR_INTERNAL"}
+RT_MEM_HOST, RT_MEM_DEVICE = 0, 1
+
+EXPORTED = ["rt_build_tree", "rt_tree_free", "rt_tree_info", "rt_trace", "rt_image_sources_view",
+            "rt_image_sources_free", "rt_rir", "rt_response_get", "rt_response_download", "rt_response_free",
+            "rt_last_error", "rt_api_version", "rt_launch_count", "rt_set_allocator"]
+
+
+class RtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+P = C.c_void_p
+
+
+class rt_mesh(C.Structure):
+    _fields_ = [("vertices", P), ("n_vertices", C.c_int64), ("tris", P), ("n_tris", C.c_int64),
+                ("material_id", P), ("surface_id", P), ("memory", C.c_int)]
+
+
+class rt_sources(C.Structure):
+    _fields_ = [("pos", P), ("n", C.c_int32)]
+
+
+class rt_receivers(C.Structure):
+    _fields_ = [("center", P), ("radius", P), ("source_of", P), ("n", C.c_int32)]
+
+
+class rt_trace_params(C.Structure):
+    _fields_ = [("n_rays", C.c_int64), ("ray_begin", C.c_int64), ("ray_count", C.c_int64),
+                ("n_bounces", C.c_int32), ("max_distance", C.c_double), ("air_beta", P), ("c", C.c_double),
+                ("block_size", C.c_int32), ("max_node_visits", C.c_int32), ("tail_rays", C.c_int32),
+                ("stream", P), ("debug_t", P),
+                ("debug_state", P), ("debug_cost", P)]
+
+
+class rt_is_view(C.Structure):
+    _fields_ = [("n", C.c_int64), ("rcv", P), ("order", P), ("count", P), ("rep_ray", P), ("pos", P),
+                ("dist", P), ("time", P), ("energy", P), ("n_traced", C.c_int64), ("n_bounces", C.c_int32),
+                ("hist", P), ("ray_energy", P), ("ray_length", P), ("ray_hits", P), ("n_records", C.c_int64),
+                ("rec_rcv", P), ("rec_ray", P), ("rec_order", P), ("rec_length", P), ("queries", C.c_int64),
+                ("hash_collisions", C.c_int64), ("ms_rays", C.c_float), ("ms_bounces", C.c_float),
+                ("ms_image_sources", C.c_float)]
+
+
+class rt_response_view(C.Structure):
+    _fields_ = [("n_rcv", C.c_int32), ("n_bins", C.c_int64), ("fs", C.c_double), ("data", P)]
+
+
+ALLOC_FN = C.CFUNCTYPE(P, C.c_size_t, P, P)
+FREE_FN = C.CFUNCTYPE(None, P, P, P)
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """Load libroomrays.so (built by paper_1811_05784_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(f"libroomrays.so is not built ({LIB_PATH}); run "
+                                  "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(LIB_PATH)
+            st = C.c_int
+            L.rt_build_tree.restype = st
+            L.rt_build_tree.argtypes = [C.POINTER(rt_mesh), P, C.POINTER(P)]
+            L.rt_tree_free.argtypes = [P]
+            L.rt_tree_info.restype = st
+            L.rt_tree_info.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_int32)]
+            L.rt_trace.restype = st
+            L.rt_trace.argtypes = [P, C.POINTER(rt_sources), C.POINTER(rt_receivers), P, C.c_int32,
+                                   C.POINTER(rt_trace_params), C.POINTER(P)]
+            L.rt_image_sources_view.restype = st
+            L.rt_image_sources_view.argtypes = [P, C.POINTER(rt_is_view)]
+            L.rt_image_sources_free.argtypes = [P]
+            L.rt_rir.restype = st
+            L.rt_rir.argtypes = [P, C.c_double, C.c_double, P, C.POINTER(P)]
+            L.rt_response_get.restype = st
+            L.rt_response_get.argtypes = [P, C.POINTER(rt_response_view)]
+            L.rt_response_download.restype = st
+            L.rt_response_download.argtypes = [P, P, P]
+            L.rt_response_free.argtypes = [P]
+            L.rt_last_error.restype = C.c_char_p
+            L.rt_api_version.restype = C.c_int32
+            L.rt_launch_count.restype = C.c_int64
+            L.rt_set_allocator.restype = st
+            L.rt_set_allocator.argtypes = [ALLOC_FN, FREE_FN, P]
+            _lib = L
+    return _lib
+
+
+def rt_last_error() -> str:
+    return lib().rt_last_error().decode()
+
+
+def rt_api_version() -> int:
+    return int(lib().rt_api_version())
+
+
+def rt_launch_count() -> int:
+    """Kernel launches made by libroomrays in this process."""
+    return int(lib().rt_launch_count())
+
+
+def _check(status):
+    if status != RT_OK:
+        raise RtError(status, rt_last_error())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return P(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return P(stream)
+    return P(stream.cuda_stream)
+
+
+def _is_cuda_tensor(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _host(x, dtype):
+    """Host array view (numpy, or CPU torch tensor such as pinned memory)."""
+    if hasattr(x, "is_cuda"):
+        t = x.contiguous()
+        assert str(t.dtype).replace("torch.", "") == np.dtype(dtype).name, (t.dtype, dtype)
+        return t, P(t.data_ptr())
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a, P(a.ctypes.data)
+
+
+def _device_tensor(ptr, shape, dtype, owner):
+    import torch
+    n = int(np.prod(shape)) if len(shape) else 1
+    if n == 0 or not ptr:
+        return torch.empty(shape, dtype=dtype, device="cuda")
+
+    class _CAI:
+        pass
+
+    typestr = {torch.float32: "<f4", torch.float64: "<f8", torch.int32: "<i4", torch.int64: "<i8"}[dtype]
+    h = _CAI()
+    h.__cuda_array_interface__ = {"shape": tuple(int(s) for s in shape), "typestr": typestr,
+                                  "data": (int(ptr), False), "version": 3, "strides": None, "stream": None}
+    h._owner = owner
+    return torch.as_tensor(h, device="cuda")
+
+
+# ----------------------------------------------------------------------------
+class Tree:
+    """rt_tree handle (LBVH of a mesh)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    def info(self):
+        nn, nt = C.c_int64(), C.c_int64()
+        dp, ns = C.c_int32(), C.c_int32()
+        _check(lib().rt_tree_info(self._h, C.byref(nn), C.byref(nt), C.byref(dp), C.byref(ns)))
+        return {"n_nodes": nn.value, "n_tris": nt.value, "depth": dp.value, "n_surfaces": ns.value}
+
+    def free(self):
+        if self._h:
+            lib().rt_tree_free(self._h)
+            self._h = None
+
+    __del__ = free
+
+
+def rt_build_tree(vertices, tris, material_id, surface_id=None, stream=None) -> Tree:
+    """Build the LBVH of a triangle mesh (host numpy / CPU tensors or CUDA tensors)."""
+    dev = _is_cuda_tensor(vertices)
+    keep = []
+    if dev:
+        import torch
+        v = vertices.contiguous().to(torch.float64)
+        t = tris.contiguous().to(torch.int32)
+        m = material_id.contiguous().to(torch.int32)
+        s = None if surface_id is None else surface_id.contiguous().to(torch.int32)
+        keep += [v, t, m, s]
+        mesh = rt_mesh(P(v.data_ptr()), v.shape[0], P(t.data_ptr()), t.shape[0], P(m.data_ptr()),
+                       P(s.data_ptr()) if s is not None else None, RT_MEM_DEVICE)
+    else:
+        v, pv = _host(vertices, np.float64)
+        t, pt = _host(tris, np.int32)
+        m, pm = _host(material_id, np.int32)
+        if surface_id is not None:
+            s, ps = _host(surface_id, np.int32)
+        else:
+            s, ps = None, None
+        keep += [v, t, m, s]
+        mesh = rt_mesh(pv, len(v), pt, len(t), pm, ps, RT_MEM_HOST)
+    out = P()
+    _check(lib().rt_build_tree(C.byref(mesh), _stream_ptr(stream), C.byref(out)))
+    return Tree(out)
+
+
+class ImageSources:
+    """rt_image_sources handle with its device arrays as torch tensors."""
+
+    def __init__(self, handle):
+        import torch
+        self._h = handle
+        v = rt_is_view()
+        _check(lib().rt_image_sources_view(handle, C.byref(v)))
+        self.view = v
+        n, nt, B, nr = v.n, v.n_traced, v.n_bounces, v.n_records
+        T = _device_tensor
+        self.n = n
+        self.rcv = T(v.rcv, (n,), torch.int32, self)
+        self.order = T(v.order, (n,), torch.int32, self)
+        self.count = T(v.count, (n,), torch.int32, self)
+        self.rep_ray = T(v.rep_ray, (n,), torch.int32, self)
+        self.pos = T(v.pos, (n, 3), torch.float64, self)
+        self.dist = T(v.dist, (n,), torch.float64, self)
+        self.time = T(v.time, (n,), torch.float64, self)
+        self.energy = T(v.energy, (n, N_BANDS), torch.float64, self)
+        self.n_traced, self.n_bounces = nt, B
+        self.hist = T(v.hist, (B, nt), torch.int32, self)
+        self.ray_energy = T(v.ray_energy, (nt, N_BANDS), torch.float32, self)
+        self.ray_length = T(v.ray_length, (nt,), torch.float32, self)
+        self.ray_hits = T(v.ray_hits, (nt,), torch.int32, self)
+        self.n_records = nr
+        self.rec_rcv = T(v.rec_rcv, (nr,), torch.int32, self)
+        self.rec_ray = T(v.rec_ray, (nr,), torch.int32, self)
+        self.rec_order = T(v.rec_order, (nr,), torch.int32, self)
+        self.rec_length = T(v.rec_length, (nr,), torch.float32, self)
+        self.queries = v.queries
+        self.hash_collisions = v.hash_collisions
+        self.ms_rays, self.ms_bounces, self.ms_image_sources = v.ms_rays, v.ms_bounces, v.ms_image_sources
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().rt_image_sources_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.free()
+
+
+def rt_trace(tree: Tree, sources, rcv_center, rcv_radius, rcv_source, band_absorption, n_rays, n_bounces,
+             ray_begin=0, ray_count=0, max_distance=0.0, air_beta=None, c=343.2, block_size=0,
+             max_node_visits=0, tail_rays=0, stream=None, debug_t=None, debug_state=None,
+             debug_cost=None) -> ImageSources:
+    """Propagate rays and build image sources (host inputs; see roomrays.h)."""
+    src, ps = _host(np.asarray(sources, np.float64).reshape(-1, 3), np.float64)
+    rc, prc = _host(np.asarray(rcv_center, np.float64).reshape(-1, 3), np.float64)
+    rr, prr = _host(np.asarray(rcv_radius, np.float64).reshape(-1), np.float64)
+    rs, prs = _host(np.asarray(rcv_source, np.int32).reshape(-1), np.int32)
+    al, pal = _host(np.asarray(band_absorption, np.float32).reshape(-1, N_BANDS), np.float32)
+    if air_beta is not None:
+        be, pbe = _host(np.asarray(air_beta, np.float32).reshape(N_BANDS), np.float32)
+    else:
+        be, pbe = None, None
+    S = rt_sources(ps, len(src))
+    R = rt_receivers(prc, prr, prs, len(rc))
+    prm = rt_trace_params(int(n_rays), int(ray_begin), int(ray_count), int(n_bounces), float(max_distance), pbe,
+                          float(c), int(block_size), int(max_node_visits), int(tail_rays), _stream_ptr(stream),
+                          P(debug_t.data_ptr()) if debug_t is not None else None,
+                          P(debug_state.data_ptr()) if debug_state is not None else None,
+                          P(debug_cost.data_ptr()) if debug_cost is not None else None)
+    out = P()
+    _check(lib().rt_trace(tree._h, C.byref(S), C.byref(R), pal, len(al), C.byref(prm), C.byref(out)))
+    return ImageSources(out)
+
+
+class Response:
+    """rt_response handle: [n_rcv, 8, n_bins] float32 device histograms."""
+
+    def __init__(self, handle):
+        import torch
+        self._h = handle
+        v = rt_response_view()
+        _check(lib().rt_response_get(handle, C.byref(v)))
+        self.n_rcv, self.n_bins, self.fs = v.n_rcv, v.n_bins, v.fs
+        self.data = _device_tensor(v.data, (max(v.n_rcv, 1), N_BANDS, v.n_bins), torch.float32, self)
+
+    def download(self, out=None, stream=None):
+        """Copy to host through rt_response_download (out: numpy or CPU tensor)."""
+        if out is None:
+            out = np.empty((max(self.n_rcv, 1), N_BANDS, self.n_bins), np.float32)
+        ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        _check(lib().rt_response_download(self._h, P(ptr), _stream_ptr(stream)))
+        return out
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().rt_response_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.free()
+
+
+def rt_rir(image_sources: ImageSources, fs, duration=0.0, stream=None) -> Response:
+    out = P()
+    _check(lib().rt_rir(image_sources._h, float(fs), float(duration), _stream_ptr(stream), C.byref(out)))
+    return Response(out)
+
+
+_alloc_keep = []
+
+
+def rt_set_allocator(alloc=None, free=None, ctx=None):
+    """Install Python allocation callbacks (both None restores the default)."""
+    if alloc is None and free is None:
+        _check(lib().rt_set_allocator(ALLOC_FN(), FREE_FN(), None))
+        _alloc_keep.clear()
+        return
+    a, f = ALLOC_FN(alloc), FREE_FN(free)
+    _alloc_keep[:] = [a, f]
+    _check(lib().rt_set_allocator(a, f, ctx))
+
+
+def scene_args(scene):
+    """Keyword arguments of rt_trace for a scenes.Scene."""
+    return dict(sources=scene.sources, rcv_center=scene.rcv_center, rcv_radius=scene.rcv_radius,
+                rcv_source=scene.rcv_source, band_absorption=scene.alpha, n_rays=scene.n_rays,
+                n_bounces=scene.n_bounces, max_distance=scene.max_distance,
+                air_beta=scene.beta if np.any(scene.beta) else None, c=scene.c)

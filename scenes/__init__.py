@@ -107,11 +107,18 @@ class _Soup:
         self.n_surf += 1
         return s
 
-    def add(self, tri_xyz: np.ndarray, material: int, surface: int):
+    def add(self, tri_xyz: np.ndarray, material: int, surface):
+        """Triangles of one material; `surface` is one id or one id per triangle."""
         tri_xyz = np.asarray(tri_xyz, dtype=np.float64).reshape(-1, 3, 3)
         self.coords.append(tri_xyz)
         self.mat.append(np.full(len(tri_xyz), material, np.int32))
-        self.surf.append(np.full(len(tri_xyz), surface, np.int32))
+        surface = np.asarray(surface, np.int32)
+        self.surf.append(np.broadcast_to(surface, (len(tri_xyz),)).astype(np.int32))
+
+    def new_surfaces(self, n: int) -> np.ndarray:
+        s = np.arange(self.n_surf, self.n_surf + n, dtype=np.int32)
+        self.n_surf += n
+        return s
 
     def grid(self, p0, a, b, na: int, nb: int, material: int, surface: int, keep=None):
         """Planar parallelogram p0 + i/na * a + j/nb * b, split into 2 triangles per cell.
@@ -371,15 +378,17 @@ def theatre(n_rays=1_000_000, n_bounces=30, n_receivers=16, seed=3, arc=512,
     for k in range(NT):
         r_in, r_out = R0 + k * w, R0 + (k + 1) * w
         z_lo, z_hi = k * rise, (k + 1) * rise
-        # riser: vertical cylindrical strip at r_in from z_lo to z_hi
-        sid = soup.new_surface()
-        tri = []
+        # riser: vertical faceted strip at r_in from z_lo to z_hi; every arc
+        # segment is a flat facet, so each is its own surface
+        sid = soup.new_surfaces(arc)
+        tri, sids = [], []
         for q in range(sub):
             za, zb = z_lo + (z_hi - z_lo) * q / sub, z_lo + (z_hi - z_lo) * (q + 1) / sub
             A, B = ring_pts(r_in, za), ring_pts(r_in, zb)
             tri.append(np.stack([A[:-1], A[1:], B[1:]], 1))
             tri.append(np.stack([A[:-1], B[1:], B[:-1]], 1))
-        soup.add(np.concatenate(tri), M_BLEACH, sid)
+            sids += [sid, sid]
+        soup.add(np.concatenate(tri), M_BLEACH, np.concatenate(sids))
         # tread: annulus sector at z_hi from r_in to r_out
         sid = soup.new_surface()
         tri = []
@@ -448,14 +457,14 @@ def theatre(n_rays=1_000_000, n_bounces=30, n_receivers=16, seed=3, arc=512,
         # reveals: jambs and the arch intrados through the wall thickness
         for xj in (xc - a, xc + a):
             soup.grid((xj, YB, SZ), (0, 3, 0), (0, 0, spring - SZ), 3, 6, M_WALL, soup.new_surface())
-        sid = soup.new_surface()
+        sids = soup.new_surfaces(K)
         tri = []
         for k in range(K):
             p, q = (ax[k], az[k]), (ax[k + 1], az[k + 1])
             A0, A1 = [p[0], YW, p[1]], [p[0], YB, p[1]]
             B0, B1 = [q[0], YW, q[1]], [q[0], YB, q[1]]
             tri += [[A0, A1, B1], [A0, B1, B0]]
-        soup.add(np.array(tri), M_WALL, sid)
+        soup.add(np.array(tri), M_WALL, np.repeat(sids, 2))
     # ledge for the upper storey of columns: box y in [-12,-10], z in [9.2,10.2]
     _box_faces(soup, (-50, -12, SZ + 8.0), (50, -10, SZ + 9.0), M_SIDE, cells=1.0)
     # columns

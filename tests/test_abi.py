@@ -1,0 +1,53 @@
+"""Host-side checks of the C ABI library and of the oracle's independence."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "roomrays.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(rt_[a-z_]+)\s*\(", src))
+    return sorted(n for n in names if not n.endswith("_fn"))
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1811_05784_gb300 import build, rt
+    build.build()
+    lib = rt.lib()
+    declared = _declared()
+    assert {"rt_build_tree", "rt_trace", "rt_rir"} <= set(declared)
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(rt.EXPORTED) == declared
+    assert rt.rt_api_version() == 1
+
+
+def test_error_reporting_without_gpu():
+    """Argument checks run before any CUDA call."""
+    from paper_1811_05784_gb300 import rt
+    mesh = rt.rt_mesh()
+    out = ctypes.c_void_p()
+    st = rt.lib().rt_build_tree(ctypes.byref(mesh), None, ctypes.byref(out))
+    assert st == rt.RT_ERR_INVALID_ARG
+    assert "n_tris" in rt.rt_last_error()
+    assert rt.lib().rt_trace(None, None, None, None, 0, None, ctypes.byref(out)) == rt.RT_ERR_INVALID_ARG
+
+
+def test_oracle_and_cuda_path_share_no_code():
+    pkg = os.path.join(ROOT, "paper_1811_05784_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle", txt, re.M), f
+                assert "rt_oracle" not in txt, f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c", ".h")):
+            txt = open(os.path.join(ROOT, "oracle", f)).read()
+            assert not re.search(r"^\s*(import|from)\s+paper_1811_05784_gb300", txt, re.M), f
+            assert not re.search(r"#include.*roomrays", txt), f

@@ -1,0 +1,395 @@
+"""GPU path vs the FP64 oracle (parity), through the C ABI.
+
+Tolerances (stated by the specification of the method's float32 path):
+  hit triangle / reflection sequence   bit-exact, except rays the oracle
+                                       reports as ambiguous (near ties, near
+                                       edges), which are counted
+  hit distance                         1e-5 relative
+  band energies                        1e-4 relative
+  RIR histograms                       1e-4 relative L2
+  image-source positions (FP64)        1e-9 relative
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1811_05784_gb300 import rt  # noqa: E402
+
+TOL_T, TOL_E, TOL_RIR, TOL_POS = 1e-5, 1e-4, 1e-4, 1e-9
+
+
+def _tree(sc):
+    return rt.rt_build_tree(sc.vertices, sc.tris, sc.material_id, sc.surface_id)
+
+
+def _trace(sc, tree=None, **kw):
+    tree = tree or _tree(sc)
+    args = rt.scene_args(sc)
+    args.update(kw)
+    return tree, rt.rt_trace(tree, **args)
+
+
+def _gpu_as_oracle_trace(sc, isrc):
+    """The GPU's sequences and crossings in the oracle's TraceResult layout."""
+    n, B = isrc.n_traced, isrc.n_bounces
+    hist = isrc.hist.cpu().numpy().T.copy()
+    z = np.zeros(0)
+    return oracle.TraceResult(np.zeros(n, np.int32), np.arange(n), hist, np.zeros((n, B)), z, z,
+                              np.full(n, B, np.int32), np.zeros(n, np.int32),
+                              isrc.rec_rcv.cpu().numpy(), isrc.rec_ray.cpu().numpy().astype(np.int64),
+                              isrc.rec_order.cpu().numpy(), isrc.rec_length.cpu().numpy().astype(np.float64),
+                              z, np.zeros((0, 3)), np.zeros((0, 3)), sc.n_rays, B)
+
+
+def _gpu_is_table(sc, isrc):
+    """{(rcv, surface sequence): (n, pos, dist, time, energy)} from the GPU output."""
+    hist = isrc.hist.cpu().numpy()
+    rep = isrc.rep_ray.cpu().numpy()
+    order = isrc.order.cpu().numpy()
+    rcv = isrc.rcv.cpu().numpy()
+    cnt = isrc.count.cpu().numpy()
+    pos, dist, tim, en = (x.cpu().numpy() for x in (isrc.pos, isrc.dist, isrc.time, isrc.energy))
+    out = {}
+    for k in range(isrc.n):
+        seq = tuple(int(sc.surface_id[hist[j, rep[k]]]) for j in range(order[k]))
+        key = (int(rcv[k]), seq)
+        assert key not in out, "duplicate image source"
+        out[key] = (int(cnt[k]), pos[k], dist[k], tim[k], en[k])
+    return out
+
+
+#: near-edge band for free-running comparisons: float32 trajectories drift from
+#: the FP64 ones by a few ulps per bounce, so decisions within this band of an
+#: edge may legitimately go either way
+EPS_FREE = 2e-5
+
+
+def _performed(hist):
+    p = np.ones_like(hist, dtype=bool)
+    p[1:] = hist[:-1] >= 0
+    return p
+
+
+def _lockstep(sc, osc, ds, dt, hist, pick=None):
+    """The oracle answers GPU queries from the GPU's own float32 state.
+
+    Returns (b, q, oracle tri, oracle delta, ambiguous, gpu tri, gpu delta)."""
+    bq = np.argwhere(_performed(hist)) if pick is None else pick
+    st = ds[bq[:, 0], bq[:, 1]].astype(np.float64)
+    excl = np.where(bq[:, 0] > 0, hist[np.maximum(bq[:, 0] - 1, 0), bq[:, 1]], -1).astype(np.int32)
+    tri, d1, d2, amb = osc.nearest(st[:, :3], st[:, 3:], exclude=excl)
+    return bq, tri, d1, amb, hist[bq[:, 0], bq[:, 1]], dt[bq[:, 0], bq[:, 1]].astype(np.float64)
+
+
+def _check_lockstep(sc, osc, ds, dt, hist, pick=None):
+    bq, tri, d1, amb, g_tri, g_t = _lockstep(sc, osc, ds, dt, hist, pick)
+    diff = (tri != g_tri) & ~amb
+    assert diff.sum() == 0, f"{diff.sum()} unexplained differences of {len(bq)} queries"
+    same = (tri >= 0) & (tri == g_tri)
+    assert same.sum() > 0.9 * (tri >= 0).sum()
+    # distance: 1e-5 relative, but never below what float32 coordinates can
+    # resolve at the ray origin (1e-6 of its largest coordinate)
+    oscale = np.abs(ds[bq[same, 0], bq[same, 1], :3]).max(1).astype(np.float64)
+    rel = np.abs(g_t[same] - d1[same]) / (d1[same] + 0.1 * oscale)
+    if rel.max() >= TOL_T:
+        v = sc.vertices[sc.tris[tri[same]]]
+        n = np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0])
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
+        st = ds[bq[same, 0], bq[same, 1]].astype(np.float64)
+        cos = np.abs(np.einsum("ij,ij->i", n, st[:, 3:]))
+        w = np.argsort(-rel)[:8]
+        msg = "; ".join(f"t={d1[same][i]:.6g} rel={rel[i]:.2e} cos={cos[i]:.2e} |o|={np.abs(st[i, :3]).max():.3g}"
+                        for i in w)
+        raise AssertionError("distance: " + msg)
+    return bq, amb
+
+
+def _check_free_running(sc, hist, ids, tr):
+    """Free-running float32 vs FP64 trajectories: the reflection sequences
+    (surface ids) agree up to each ray's first ambiguous bounce.  Triangle
+    ids inside one surface may differ once the trajectories have drifted by
+    more than the near-edge band; those are counted, not failed."""
+    surf = np.append(sc.surface_id, -1)            # index -1 -> -1
+    agree = tri_diff = 0
+    for k, q in enumerate(ids):
+        upto = tr.first_amb[k]
+        g, o = hist[:upto, q], tr.hist[k, :upto]
+        assert np.array_equal(surf[g], surf[o]), (q, g, o)
+        tri_diff += int((g != o).any())
+        agree += upto
+    assert agree > 0.5 * len(ids) * tr.B
+    assert tri_diff <= 0.01 * len(ids), tri_diff
+    return tri_diff
+
+
+# ---------------------------------------------------------------------------
+def test_fibonacci_directions_bitexact():
+    N = 100_003
+    sc = scenes.shoebox(n_rays=N, n_bounces=1)
+    ds = torch.empty((1, N, 6), dtype=torch.float32, device="cuda")
+    _trace(sc, debug_state=ds)
+    torch.cuda.synchronize()
+    d = ds[0, :, 3:].cpu().numpy().astype(np.float64)
+    ref = oracle.fibonacci(N)
+    mism = int((d != ref).any(1).sum())
+    assert mism == 0, f"{mism} directions differ"
+    o = ds[0, :, :3].cpu().numpy().astype(np.float64)
+    assert np.array_equal(o, np.broadcast_to(sc.sources[0], o.shape))
+
+
+@pytest.mark.parametrize("n_rays", [10_000, 4097])
+def test_shoebox_trace_parity(n_rays):
+    sc = scenes.shoebox(n_rays=n_rays)
+    B = sc.n_bounces
+    ds_t = torch.empty((B, n_rays, 6), dtype=torch.float32, device="cuda")
+    dt_t = torch.empty((B, n_rays), dtype=torch.float32, device="cuda")
+    tree, isrc = _trace(sc, debug_t=dt_t, debug_state=ds_t)
+    ds, dt = ds_t.cpu().numpy(), dt_t.cpu().numpy()
+    hist = isrc.hist.cpu().numpy()
+    osc = oracle.OracleScene(sc, tree=False)
+    # lockstep: every query, hit triangle exact (ambiguous excepted), distance 1e-5
+    bq, amb = _check_lockstep(sc, osc, ds, dt, hist)
+    assert amb.mean() < 0.01
+    # lockstep crossings of every segment
+    seg = np.where(hist[bq[:, 0], bq[:, 1]] >= 0, dt[bq[:, 0], bq[:, 1]], np.inf)
+    st = ds[bq[:, 0], bq[:, 1]].astype(np.float64)
+    k, r, margin = oracle.crossings(sc, st[:, :3], st[:, 3:], seg)
+    want = {(int(bq[i, 1]), int(bq[i, 0]), int(rr)) for i, rr, mg in zip(k, r, margin) if abs(mg) > 1e-5}
+    edge = {(int(bq[i, 1]), int(bq[i, 0]), int(rr)) for i, rr, mg in zip(k, r, margin) if abs(mg) <= 1e-5}
+    got = set(zip(isrc.rec_ray.cpu().numpy().tolist(), isrc.rec_order.cpu().numpy().tolist(),
+                  isrc.rec_rcv.cpu().numpy().tolist()))
+    assert want <= got and not (got - want - edge)
+    # free running from the source: sequences equal up to the first ambiguity
+    tr = oracle.trace(osc, eps_edge_rel=EPS_FREE)
+    ok = tr.first_amb == B
+    assert ok.mean() > 0.95
+    assert np.array_equal(hist.T[ok], tr.hist[ok])
+    # energies and path lengths of rays with identical sequences
+    E = isrc.ray_energy.cpu().numpy().astype(np.float64)
+    assert np.abs(E[ok] / tr.E[ok] - 1).max() < TOL_E
+    L = isrc.ray_length.cpu().numpy().astype(np.float64)
+    assert np.abs(L[ok] / tr.L[ok] - 1).max() < TOL_T
+    assert (isrc.ray_hits.cpu().numpy() == B).all()          # closed room, no escapes
+    assert isrc.queries == n_rays * B
+    assert isrc.hash_collisions == 0
+
+
+def test_shoebox_image_sources_and_rir_parity():
+    sc = scenes.shoebox()
+    tree, isrc = _trace(sc)
+    # (1) dedup + FP64 reconstruction: exactly the oracle's grouping of the GPU's own crossings
+    ref = oracle.image_sources(sc, _gpu_as_oracle_trace(sc, isrc))
+    got = _gpu_is_table(sc, isrc)
+    assert len(got) == len(ref.n)
+    for k in range(len(ref.n)):
+        key = (int(ref.rcv[k]), ref.seq[k])
+        n, pos, dist, tim, en = got[key]
+        assert n == ref.n[k]
+        assert np.abs(pos - ref.pos[k]).max() <= TOL_POS * max(1.0, np.abs(ref.pos[k]).max())
+        assert dist == pytest.approx(ref.d[k], rel=TOL_POS)
+        assert tim == pytest.approx(ref.t[k], rel=TOL_POS)
+        assert np.allclose(en, ref.E[k], rtol=1e-12, atol=0)
+    # (2) histogram stage alone
+    resp = rt.rt_rir(isrc, sc.fs, duration=0.5)
+    H = resp.download().astype(np.float64)
+    Href = oracle.rir(ref, 1, sc.fs, duration=0.5)
+    assert np.linalg.norm(H - Href) / np.linalg.norm(Href) < 1e-6
+    # (3) end to end against the free-running oracle
+    tr = oracle.trace(oracle.OracleScene(sc, tree=False))
+    Ho = oracle.rir(oracle.image_sources(sc, tr), 1, sc.fs, duration=0.5)
+    assert np.linalg.norm(H - Ho) / np.linalg.norm(Ho) < TOL_RIR
+
+
+def test_paper_shoebox_range_and_air():
+    """Sec. 3.2 setup: Table 1 materials, ISO air, eq. 13 range."""
+    sc = scenes.paper_shoebox(n_rays=20_000)
+    tree, isrc = _trace(sc)
+    tr = oracle.trace(oracle.OracleScene(sc, tree=False), eps_edge_rel=EPS_FREE)
+    hist = isrc.hist.cpu().numpy().T
+    ok = tr.first_amb == tr.B
+    assert np.array_equal(hist[ok], tr.hist[ok])
+    assert (isrc.rec_length.cpu().numpy() <= sc.max_distance * (1 + 1e-6)).all()
+    ref = oracle.image_sources(sc, _gpu_as_oracle_trace(sc, isrc))
+    got = _gpu_is_table(sc, isrc)
+    for k in range(len(ref.n)):
+        n, pos, dist, tim, en = got[(int(ref.rcv[k]), ref.seq[k])]
+        assert n == ref.n[k]
+        assert np.allclose(en, ref.E[k], rtol=1e-12, atol=0)
+    H = rt.rt_rir(isrc, sc.fs).download().astype(np.float64)
+    Ho = oracle.rir(oracle.image_sources(sc, tr), 1, sc.fs, duration=H.shape[-1] / sc.fs)
+    assert np.linalg.norm(H - Ho) / np.linalg.norm(Ho) < TOL_RIR
+
+
+@pytest.mark.parametrize("h,n_rays", [(0.5, 50_000), (0.125, 1_000_000)])
+def test_lroom_watertight_energy_conserved(h, n_rays):
+    sc = scenes.lroom(h=h, n_rays=n_rays, n_bounces=50, alpha=np.zeros((4, 8)))
+    tree, isrc = _trace(sc)
+    hits = isrc.ray_hits.cpu().numpy()
+    assert (hits == 50).all(), f"{(hits < 50).sum()} rays escaped a closed room"
+    E = isrc.ray_energy.cpu().numpy().astype(np.float64).sum(0)
+    assert np.allclose(E, 1.0, rtol=1e-6)
+
+
+def test_lroom_subset_against_oracle_tree():
+    sc = scenes.lroom(n_rays=1_000_000, n_bounces=50)      # 102,400 triangles
+    B, N = sc.n_bounces, sc.n_rays
+    ds_t = torch.empty((B, N, 6), dtype=torch.float32, device="cuda")
+    dt_t = torch.empty((B, N), dtype=torch.float32, device="cuda")
+    tree, isrc = _trace(sc, debug_t=dt_t, debug_state=ds_t)
+    hist = isrc.hist.cpu().numpy()
+    osc = oracle.OracleScene(sc, tree=True)
+    rng = np.random.default_rng(11)
+    # lockstep on 20,000 sampled queries
+    perf = np.argwhere(_performed(hist))
+    pick = perf[rng.choice(len(perf), 20_000, replace=False)]
+    _check_lockstep(sc, osc, ds_t.cpu().numpy(), dt_t.cpu().numpy(), hist, pick)
+    # free running on a seeded 4096-ray subset: reflection (surface) sequences
+    ids = np.sort(rng.choice(N, 4096, replace=False))
+    tr = oracle.trace(osc, ray_ids=ids, eps_edge_rel=EPS_FREE)
+    _check_free_running(sc, hist, ids, tr)
+
+
+def test_theatre_lockstep_and_free_running():
+    sc = scenes.theatre()                                    # 436,796 triangles, 1M rays, 30 bounces
+    B, N = sc.n_bounces, sc.n_rays
+    ds_t = torch.empty((B, N, 6), dtype=torch.float32, device="cuda")
+    dt_t = torch.empty((B, N), dtype=torch.float32, device="cuda")
+    tree, isrc = _trace(sc, debug_state=ds_t, debug_t=dt_t)
+    hist = isrc.hist.cpu().numpy()
+    osc = oracle.OracleScene(sc, tree=True)
+    rng = np.random.default_rng(5)
+    perf = np.argwhere(_performed(hist))
+    assert len(perf) == isrc.queries
+    pick = perf[rng.choice(len(perf), 20_000, replace=False)]
+    _check_lockstep(sc, osc, ds_t.cpu().numpy(), dt_t.cpu().numpy(), hist, pick)
+    ids = np.sort(rng.choice(N, 1024, replace=False))
+    tr = oracle.trace(osc, ray_ids=ids, eps_edge_rel=EPS_FREE)
+    _check_free_running(sc, hist, ids, tr)
+
+
+def test_deterministic():
+    sc = scenes.shoebox(n_rays=20_000, n_bounces=20)
+    tree = _tree(sc)
+    a = rt.rt_trace(tree, **rt.scene_args(sc))
+    b = rt.rt_trace(tree, **rt.scene_args(sc))
+    assert torch.equal(a.hist, b.hist)
+    assert a.n == b.n
+    for x, y in ((a.pos, b.pos), (a.energy, b.energy), (a.count, b.count)):
+        assert torch.equal(x, y)
+    ha = rt.rt_rir(a, sc.fs).download()
+    hb = rt.rt_rir(b, sc.fs).download()
+    assert np.array_equal(ha, hb)
+
+
+@pytest.mark.parametrize("tail", [-1, 1, 5000])
+def test_tail_mode_matches_per_bounce_launches(tail):
+    """Finishing the last bounces in one launch changes nothing per ray."""
+    sc = scenes.theatre(n_rays=200_000, n_bounces=30)
+    tree = _tree(sc)
+    a = rt.rt_trace(tree, tail_rays=-1, **rt.scene_args(sc))
+    b = rt.rt_trace(tree, tail_rays=tail, **rt.scene_args(sc))
+    assert torch.equal(a.hist, b.hist)
+    assert torch.equal(a.ray_energy, b.ray_energy) and torch.equal(a.ray_length, b.ray_length)
+    assert a.queries == b.queries and a.n == b.n and a.n_records == b.n_records
+    assert torch.equal(a.energy, b.energy) and torch.equal(a.count, b.count)
+
+
+def test_shards_add_up():
+    sc = scenes.shoebox(n_rays=30_000, n_bounces=20)
+    tree = _tree(sc)
+    full = rt.rt_trace(tree, **rt.scene_args(sc))
+    Hf = rt.rt_rir(full, sc.fs, duration=0.4).download().astype(np.float64)
+    Hs = 0
+    for b0, cnt in ((0, 10_000), (10_000, 12_345), (22_345, 7_655)):
+        part = rt.rt_trace(tree, ray_begin=b0, ray_count=cnt, **rt.scene_args(sc))
+        Hs = Hs + rt.rt_rir(part, sc.fs, duration=0.4).download().astype(np.float64)
+    assert np.linalg.norm(Hs - Hf) / np.linalg.norm(Hf) < 1e-6
+
+
+def test_device_and_host_mesh_agree():
+    sc = scenes.lroom(h=0.5, n_rays=20_000, n_bounces=20)
+    t_host, a = _trace(sc)
+    dev = [torch.as_tensor(x).cuda() for x in (sc.vertices, sc.tris, sc.material_id, sc.surface_id)]
+    t_dev = rt.rt_build_tree(*dev)
+    b = rt.rt_trace(t_dev, **rt.scene_args(sc))
+    assert torch.equal(a.hist, b.hist)
+    assert t_host.info() == t_dev.info()
+
+
+def test_record_capacity_retry():
+    # a receiver that fills most of the room: far more crossings than the first buffer
+    sc = scenes.shoebox(receiver=(5.0, 3.5, 1.5), radius=1.4, n_rays=200_000, n_bounces=40)
+    tree, isrc = _trace(sc)
+    assert isrc.n_records > 2 * sc.n_rays
+    assert int(isrc.count.sum()) == isrc.n_records
+    assert isrc.hash_collisions == 0
+
+
+def test_errors_are_reported():
+    sc = scenes.shoebox(n_rays=100, n_bounces=4)
+    tree = _tree(sc)
+    args = rt.scene_args(sc)
+    for bad in (dict(n_rays=0), dict(n_bounces=0), dict(c=0.0), dict(ray_begin=100),
+                dict(band_absorption=np.full((1, 8), 1.5)), dict(rcv_source=[3])):
+        kw = dict(args)
+        kw.update(bad)
+        with pytest.raises(rt.RtError) as e:
+            rt.rt_trace(tree, **kw)
+        assert e.value.status == rt.RT_ERR_INVALID_ARG, bad
+    tris = sc.tris.copy()
+    tris[0, 2] = tris[0, 1]
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_build_tree(sc.vertices, tris, sc.material_id, sc.surface_id)
+    assert e.value.status == rt.RT_ERR_DEGENERATE_MESH
+    tris = sc.tris.copy()
+    tris[3, 0] = 10_000
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_build_tree(sc.vertices, tris, sc.material_id, sc.surface_id)
+    assert e.value.status == rt.RT_ERR_INVALID_ARG
+    v = sc.vertices.copy()
+    v[0, 0] = np.nan
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_build_tree(v, sc.tris, sc.material_id, sc.surface_id)
+    assert e.value.status == rt.RT_ERR_INVALID_ARG
+    mixed = sc.material_id.copy()
+    mixed[1] = 1
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_build_tree(sc.vertices, sc.tris, mixed, sc.surface_id)
+    assert e.value.status == rt.RT_ERR_INVALID_ARG
+
+
+def test_node_visit_cap_is_reported():
+    sc = scenes.lroom(h=0.5, n_rays=1000, n_bounces=5)
+    tree = _tree(sc)
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_trace(tree, max_node_visits=2, **rt.scene_args(sc))
+    assert e.value.status == rt.RT_ERR_STEP_LIMIT
+    rt.rt_trace(tree, **rt.scene_args(sc))   # the default cap passes
+
+
+def test_allocation_failure_is_reported():
+    sc = scenes.shoebox(n_rays=100, n_bounces=4)
+    rt.rt_set_allocator(lambda nbytes, stream, ctx: None, lambda p, s, c: None)
+    try:
+        with pytest.raises(rt.RtError) as e:
+            _tree(sc)
+        assert e.value.status == rt.RT_ERR_OOM
+    finally:
+        rt.rt_set_allocator(None, None)
+    _trace(sc)   # default allocator works again
+
+
+def test_surface_grouping_when_ids_missing():
+    sc = scenes.shoebox(n_rays=5000, n_bounces=10)
+    t_ids = rt.rt_build_tree(sc.vertices, sc.tris, sc.material_id, None)
+    assert t_ids.info()["n_surfaces"] == 6
+    a = rt.rt_trace(t_ids, **rt.scene_args(sc))
+    b = rt.rt_trace(_tree(sc), **rt.scene_args(sc))
+    assert torch.equal(a.hist, b.hist) and a.n == b.n
