@@ -177,6 +177,29 @@ rt_status rt_response_get(const rt_response* rir, rt_response_view* out);
 rt_status rt_response_download(const rt_response* rir, float* dst, void* stream);
 void rt_response_free(rt_response* rir);
 
+/* rt_rir_static -- the histogram step of rt_rir without any device
+ * allocation, for callers that cannot allocate while they run (a real-time
+ * auralisation loop re-binning image sources for a moving listener under an
+ * audio deadline; an application that reserves its GPU memory up front).
+ * The paper has no counterpart: this is a deployment variant of rt_rir.
+ *   time, rcv, energy: device arrays of n image sources (e.g. the time /
+ *     rcv / energy fields of an rt_is_view): arrival time (s), receiver
+ *     index, [n][8] band energy;
+ *   hist: device output [n_rcv][8][n_bins], zero-filled and then summed by
+ *     this call exactly as rt_rir does (same bins, same FP64 order);
+ *   image sources with a receiver outside [0, n_rcv) or a bin outside
+ *     [0, n_bins) are dropped.
+ * Its sort scratch is one static device array of RT_RIR_STATIC_SCRATCH_BYTES
+ * that every GPU loading the library holds until exit; all calls share it,
+ * so calls whose GPU work overlaps race (serialise them).  The first call on
+ * a device looks up the array's address; make it before any stream capture.
+ * Errors: RT_ERR_INVALID_ARG (n > RT_RIR_STATIC_MAX_SOURCES, bad sizes or
+ * null arrays), RT_ERR_CUDA. */
+#define RT_RIR_STATIC_MAX_SOURCES 524288
+#define RT_RIR_STATIC_SCRATCH_BYTES 12910592
+rt_status rt_rir_static(const double* time, const int32_t* rcv, const double* energy, int64_t n, int32_t n_rcv,
+                        double fs, int64_t n_bins, float* hist, void* stream);
+
 /* Message of the last error on this thread ("" if none). */
 const char* rt_last_error(void);
 int32_t rt_api_version(void);

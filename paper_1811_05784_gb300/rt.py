@@ -26,7 +26,8 @@ STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_DEGENERATE_MESH"
 RT_MEM_HOST, RT_MEM_DEVICE = 0, 1
 
 EXPORTED = ["rt_build_tree", "rt_tree_free", "rt_tree_info", "rt_trace", "rt_image_sources_view",
-            "rt_image_sources_free", "rt_rir", "rt_response_get", "rt_response_download", "rt_response_free",
+            "rt_image_sources_free", "rt_rir", "rt_rir_static", "rt_response_get", "rt_response_download",
+            "rt_response_free",
             "rt_last_error", "rt_api_version", "rt_launch_count", "rt_set_allocator"]
 
 
@@ -104,6 +105,8 @@ def lib():
             L.rt_image_sources_free.argtypes = [P]
             L.rt_rir.restype = st
             L.rt_rir.argtypes = [P, C.c_double, C.c_double, P, C.POINTER(P)]
+            L.rt_rir_static.restype = st
+            L.rt_rir_static.argtypes = [P, P, P, C.c_int64, C.c_int32, C.c_double, C.c_int64, P, P]
             L.rt_response_get.restype = st
             L.rt_response_get.argtypes = [P, C.POINTER(rt_response_view)]
             L.rt_response_download.restype = st
@@ -291,7 +294,9 @@ def rt_trace(tree: Tree, sources, rcv_center, rcv_radius, rcv_source, band_absor
                           P(debug_cost.data_ptr()) if debug_cost is not None else None)
     out = P()
     _check(lib().rt_trace(tree._h, C.byref(S), C.byref(R), pal, len(al), C.byref(prm), C.byref(out)))
-    return ImageSources(out)
+    res = ImageSources(out)
+    res.n_rcv = len(rc)
+    return res
 
 
 class Response:
@@ -326,6 +331,28 @@ def rt_rir(image_sources: ImageSources, fs, duration=0.0, stream=None) -> Respon
     out = P()
     _check(lib().rt_rir(image_sources._h, float(fs), float(duration), _stream_ptr(stream), C.byref(out)))
     return Response(out)
+
+
+RT_RIR_STATIC_MAX_SOURCES = 524288
+
+
+def rt_rir_static(image_sources: ImageSources, fs, duration, out=None, stream=None):
+    """Histograms of image sources without any device allocation inside the
+    library (static scratch; see roomrays.h).  `out` is a CUDA float32 tensor
+    [n_rcv, 8, ceil(duration * fs)], allocated here by torch if not given."""
+    import torch
+    n_bins = int(np.ceil(duration * fs))
+    n_rcv = max(image_sources_n_rcv(image_sources), 1)
+    if out is None:
+        out = torch.empty((n_rcv, N_BANDS, n_bins), dtype=torch.float32, device="cuda")
+    v = image_sources.view
+    _check(lib().rt_rir_static(P(v.time), P(v.rcv), P(v.energy), int(v.n), int(n_rcv), float(fs), int(n_bins),
+                               P(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def image_sources_n_rcv(image_sources: ImageSources) -> int:
+    return image_sources.n_rcv
 
 
 _alloc_keep = []
