@@ -207,6 +207,12 @@ int32_t rt_api_version(void);
  * accounting; monotonic, thread-safe). */
 int64_t rt_launch_count(void);
 
+/* Measurement utility (no counterpart in the paper): L2 read bandwidth of
+ * the current device in GB/s, from streaming a 32 MiB L2-resident buffer 16
+ * times with L1-bypassing 128-bit loads (best of 5 timed launches after one
+ * warm-up).  Used as the roofline denominator of the traversal kernel. */
+rt_status rt_measure_l2_bandwidth(double* read_gbs, void* stream);
+
 /* Optional device allocator (e.g. a framework's caching allocator).  Both
  * NULL restores cudaMallocAsync / cudaFreeAsync on the call's stream.  An
  * allocator that returns NULL makes the call fail with RT_ERR_OOM. */

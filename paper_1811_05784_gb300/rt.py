@@ -28,7 +28,7 @@ RT_MEM_HOST, RT_MEM_DEVICE = 0, 1
 EXPORTED = ["rt_build_tree", "rt_tree_free", "rt_tree_info", "rt_trace", "rt_image_sources_view",
             "rt_image_sources_free", "rt_rir", "rt_rir_static", "rt_response_get", "rt_response_download",
             "rt_response_free",
-            "rt_last_error", "rt_api_version", "rt_launch_count", "rt_set_allocator"]
+            "rt_last_error", "rt_api_version", "rt_launch_count", "rt_measure_l2_bandwidth", "rt_set_allocator"]
 
 
 class RtError(RuntimeError):
@@ -115,6 +115,8 @@ def lib():
             L.rt_last_error.restype = C.c_char_p
             L.rt_api_version.restype = C.c_int32
             L.rt_launch_count.restype = C.c_int64
+            L.rt_measure_l2_bandwidth.restype = st
+            L.rt_measure_l2_bandwidth.argtypes = [C.POINTER(C.c_double), P]
             L.rt_set_allocator.restype = st
             L.rt_set_allocator.argtypes = [ALLOC_FN, FREE_FN, P]
             _lib = L
@@ -132,6 +134,13 @@ def rt_api_version() -> int:
 def rt_launch_count() -> int:
     """Kernel launches made by libroomrays in this process."""
     return int(lib().rt_launch_count())
+
+
+def rt_measure_l2_bandwidth(stream=None) -> float:
+    """L2 read bandwidth (GB/s) measured by the library's probe kernel."""
+    v = C.c_double()
+    _check(lib().rt_measure_l2_bandwidth(C.byref(v), _stream_ptr(stream)))
+    return v.value
 
 
 def _check(status):

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     src = open(os.path.join(ROOT, "include", "roomrays.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = set(re.findall(r"\b(rt_[a-z_]+)\s*\(", src))
+    names = set(re.findall(r"\b(rt_[a-z0-9_]+)\s*\(", src))
     return sorted(n for n in names if not n.endswith("_fn"))
 
 
