@@ -53,7 +53,7 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--tail-rays", type=int, default=None, help="override the autotuned tail threshold")
     ap.add_argument("--cpu-sample-rays", type=int, default=200_000)
@@ -230,30 +230,22 @@ def run_native(args):
     St = torch.as_tensor(sc.surface_id, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
+    ws_trace = rt.Workspace()
+    tail = rt.RT_TAIL_AUTOTUNE if args.tail_rays is None else args.tail_rays
+
     def step(tail):
         tree = rt.rt_build_tree(V, T, Mt, St, stream=stream)
-        isrc = rt.rt_trace(tree, tail_rays=tail, stream=stream, **kw)
+        isrc = rt.rt_trace(tree, tail_rays=tail, stream=stream, workspace=ws_trace, **kw)
         resp = rt.rt_rir(isrc, sc.fs, duration=DURATION, stream=stream)
         return tree, isrc, resp
 
-    # autotune the tail threshold (one launch finishes the trace below it)
+    # warm-up; with the default the library's online autotuner tries its block
+    # sizes and tail thresholds on these calls and keeps the fastest
     with torch.cuda.stream(stream):
-        cand = [args.tail_rays] if args.tail_rays is not None else [-1, 0, 262_144, N_RAYS]
-        best_tail, best_ms = cand[0], math.inf
-        for tail in cand:
-            times = []
-            for _ in range(2):
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                step(tail)
-                torch.cuda.synchronize()
-                times.append(time.perf_counter() - t0)
-            if min(times) < best_ms:
-                best_ms, best_tail = min(times), tail
-        tail = best_tail
-        for _ in range(args.warmup):
-            step(tail)
+        for _ in range(max(args.warmup, 1)):
+            _, isrc_w, _ = step(tail)
         torch.cuda.synchronize()
+        chosen = {"block_size": isrc_w.block_size, "tail_rays": int(isrc_w.tail_rays)}
 
         # -- timed region (device-resident inputs) --------------------------
         if ws > 1:
@@ -292,7 +284,7 @@ def run_native(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             tree = rt.rt_build_tree(*host, stream=stream)
-            isrc = rt.rt_trace(tree, tail_rays=tail, stream=stream, **kw)
+            isrc = rt.rt_trace(tree, tail_rays=tail, stream=stream, workspace=ws_trace, **kw)
             resp = rt.rt_rir(isrc, sc.fs, duration=DURATION, stream=stream)
             resp.download(out, stream=stream)
             dt = time.perf_counter() - t0
@@ -304,7 +296,9 @@ def run_native(args):
         B = sc.n_bounces
         cost = torch.zeros((B, N_RAYS, 2), dtype=torch.int32, device=dev)
         tree = rt.rt_build_tree(V, T, Mt, St, stream=stream)
-        isrc = rt.rt_trace(tree, tail_rays=tail, stream=stream, debug_cost=cost, **kw)
+        fixed_tail = chosen["tail_rays"] if chosen["tail_rays"] > 0 else -1
+        isrc = rt.rt_trace(tree, tail_rays=fixed_tail, block_size=chosen["block_size"], stream=stream,
+                           debug_cost=cost, **kw)
         torch.cuda.synchronize()
         c = cost.double().sum((0, 1)).cpu().numpy()
         n_q = isrc.queries
@@ -333,7 +327,8 @@ def run_native(args):
         "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(ws), "rays_per_gpu": N_RAYS, "n_bounces": N_BOUNCES,
-                   "queries_per_step_per_gpu": int(statistics.median(queries)), "tail_rays": tail,
+                   "queries_per_step_per_gpu": int(statistics.median(queries)),
+                   "bounce_kernel": chosen, "cuda_graph": ws_trace.graph_launches > 0,
                    "l2": "flushed (256 MB write) before every timed step", "parallelism": f"ray shards x{ws}"},
         "e2e": {"value": e2e_q_all / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
@@ -341,7 +336,7 @@ def run_native(args):
                      "achieved": l2_bytes / bounce_s / 1e9, "peak": l2_peak, "unit": "GB/s",
                      "frac": l2_bytes / bounce_s / 1e9 / l2_peak,
                      "peak_source": "measured in this run: rt_measure_l2_bandwidth (32 MiB L2-resident, ld.global.cg)",
-                     "traffic": profiled_traffic(tail), "algorithmic_bytes": l2_bytes,
+                     "traffic": profiled_traffic(chosen["tail_rays"]), "algorithmic_bytes": l2_bytes,
                      "hbm": {"achieved": hbm_bytes / bounce_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
                              "frac": hbm_bytes / bounce_s / 1e9 / hbm_peak, "peak_source": hbm_src},
                      "ms_per_launch_set": bounce_s * 1e3,

@@ -60,6 +60,7 @@ typedef enum { RT_MEM_HOST = 0, RT_MEM_DEVICE = 1 } rt_memory;
 typedef struct rt_tree rt_tree;                   /* immutable after build */
 typedef struct rt_image_sources rt_image_sources; /* device-resident results of rt_trace */
 typedef struct rt_response rt_response;           /* device-resident histograms */
+typedef struct rt_workspace rt_workspace;         /* reusable trace scratch + CUDA graph */
 
 /* Mesh of flat triangles (Sec. 2.1).  `memory` says where the four arrays
  * live.  surface_id groups coplanar triangles of one material; image sources
@@ -103,13 +104,32 @@ typedef struct {
                                 the call with RT_ERR_STEP_LIMIT instead of looping on */
     int32_t tail_rays;     /* once a bounce starts with at most this many live rays, one
                               launch finishes all their remaining bounces (0 = the number
-                              of resident threads, < 0 = never: one launch per bounce) */
+                              of resident threads, -1 = never: one launch per bounce,
+                              RT_TAIL_AUTOTUNE = the library times its candidate block
+                              sizes and thresholds on the first calls of each workload
+                              class and keeps the fastest; results do not depend on it) */
     void* stream;          /* cudaStream_t */
     /* optional device outputs for parity checks (NULL = off) */
     float* debug_t;        /* [n_bounces][n_traced] hit distance, +inf on escape */
     float* debug_state;    /* [n_bounces][n_traced][6] origin and direction before each query */
     int32_t* debug_cost;   /* [n_bounces][n_traced][2] nodes visited, triangles tested per query */
+    rt_workspace* workspace; /* NULL, or scratch reused across calls on one stream; on a
+                                non-default stream the bounce loop then runs as one CUDA
+                                graph launch (captured on the first call, parameters
+                                updated on later ones) */
 } rt_trace_params;
+
+#define RT_TAIL_AUTOTUNE (-2)
+
+/* One room of a batched trace: its tree, sources, receivers (source_of
+ * indexes this room's sources) and absorption table. */
+typedef struct {
+    const rt_tree* tree;
+    rt_sources sources;
+    rt_receivers receivers;
+    const float* band_absorption; /* [n_materials][8] */
+    int32_t n_materials;
+} rt_room;
 
 /* Borrowed device views of rt_trace's results.  Traced ray q belongs to
  * source q / ray_count and has Fibonacci index ray_begin + q % ray_count. */
@@ -136,6 +156,8 @@ typedef struct {
     const float* rec_length;   /* [n_records] path length at the closest point */
     int64_t queries;           /* nearest-element queries resolved (hits + escapes) */
     int64_t hash_collisions;   /* equal keys with different sequences (expected 0) */
+    int32_t block_size;        /* bounce-kernel configuration used */
+    int64_t tail_rays;
     float ms_rays;             /* device time of ray generation (CUDA events) */
     float ms_bounces;          /* device time of all bounce launches */
     float ms_image_sources;    /* device time of dedup + FP64 reconstruction */
@@ -165,6 +187,14 @@ rt_status rt_tree_info(const rt_tree* tree, int64_t* n_nodes, int64_t* n_tris, i
 rt_status rt_trace(const rt_tree* tree, const rt_sources* src, const rt_receivers* rcv,
                    const float* band_absorption, int32_t n_materials, const rt_trace_params* params,
                    rt_image_sources** out);
+/* Many rooms of uneven size in one persistent launch (config: batched rooms).
+ * Every source of every room sends params->n_rays rays; sources and receivers
+ * are numbered room after room (receiver k of room r has global index
+ * sum_{r'<r} n_receivers(r') + k), and so are traced rays (ray q belongs to
+ * global source q / ray_count).  Each ray meets only its own room's tree.
+ * Errors as rt_trace. */
+rt_status rt_trace_batch(const rt_room* rooms, int32_t n_rooms, const rt_trace_params* params,
+                         rt_image_sources** out);
 rt_status rt_image_sources_view(const rt_image_sources* is, rt_is_view* out);
 void rt_image_sources_free(rt_image_sources* is);
 
@@ -212,6 +242,13 @@ int64_t rt_launch_count(void);
  * times with L1-bypassing 128-bit loads (best of 5 timed launches after one
  * warm-up).  Used as the roofline denominator of the traversal kernel. */
 rt_status rt_measure_l2_bandwidth(double* read_gbs, void* stream);
+
+/* Workspace: queues and counters kept between traces on one stream, and the
+ * CUDA graph of the bounce loop.  Free it after its last trace finished. */
+rt_status rt_workspace_create(rt_workspace** out);
+void rt_workspace_free(rt_workspace* ws);
+/* Number of graph launches the workspace has made (0 if graphs were not used). */
+int64_t rt_workspace_graph_launches(const rt_workspace* ws);
 
 /* Optional device allocator (e.g. a framework's caching allocator).  Both
  * NULL restores cudaMallocAsync / cudaFreeAsync on the call's stream.  An

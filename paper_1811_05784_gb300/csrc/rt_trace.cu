@@ -36,7 +36,11 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 
 namespace rr {
 
@@ -52,13 +56,24 @@ struct Queue {
     uint4* m;    // traced ray index, last surface id, sequence hash lo, hi
 };
 
-struct BounceArgs {
-    const float4* __restrict__ nodes;
-    const float4* __restrict__ tris;
+// Per-room device tables: the tree of the room and where its materials start
+// in the concatenated absorption table.  A single-room trace has one entry.
+struct RoomDev {
+    const float4* nodes;
+    const float4* tris;
+    const float4* tri_nrm;
+    const int32_t* mat_of_surf;
+    const int32_t* surf_of;
+    const Plane* planes;
     int64_t n_nodes, n_tris;
-    const float4* __restrict__ tri_nrm;
-    const int32_t* __restrict__ mat_of_surf;
-    const float* __restrict__ refl;      // [n_mat][8] 1 - alpha
+    int32_t mat_base;
+    int32_t pad;
+};
+
+struct BounceArgs {
+    const RoomDev* __restrict__ rooms;
+    const int32_t* __restrict__ room_of_src;  // [S] room of each source
+    const float* __restrict__ refl;      // [sum of n_mat][8] 1 - alpha
     const float4* __restrict__ rcv;      // [R] centre, r^2 (sorted by source)
     const int32_t* __restrict__ rcv_id;  // [R] original receiver index
     const int32_t* __restrict__ rcv_beg; // [S+1] receiver range per source
@@ -262,7 +277,6 @@ __device__ __forceinline__ void tri_test(const RayPre& r, const float4* __restri
 
 // traversal stack in shared memory: STACK_SMEM entries per thread, laid out
 // [entry][thread] so that lanes at the same depth hit different banks
-static constexpr int BOUNCE_THREADS = 128;
 static constexpr int STACK_SMEM = 48;
 
 // Nearest hit, while-while traversal with postponed leaves (Aila & Laine
@@ -270,9 +284,10 @@ static constexpr int STACK_SMEM = 48;
 // until every lane of the warp holds a leaf, then all lanes test triangles
 // together.  Child references: >= 0 internal node, < 0 leaf
 // ~(first_triangle << 3 | count).
-__device__ __forceinline__ void nearest_hit(const BounceArgs& a, const RayPre& r, int exclude, float& best_t,
-                                            int& best_id, unsigned int& err, int& n_nodes, int& n_tests,
-                                            int* __restrict__ stack) {
+template <int BT>
+__device__ __forceinline__ void nearest_hit(const BounceArgs& a, const RoomDev& rm, const RayPre& r, int exclude,
+                                            float& best_t, int& best_id, unsigned int& err, int& n_nodes,
+                                            int& n_tests, int* __restrict__ stack) {
     const int SENTINEL = 0x7FFFFFFF;
     int sp = 0;
     int node = 0;
@@ -288,13 +303,13 @@ __device__ __forceinline__ void nearest_hit(const BounceArgs& a, const RayPre& r
                 leaf = 0;
                 break;
             }
-            if ((int64_t)node >= a.n_nodes) {  // never read outside the node array
+            if ((int64_t)node >= rm.n_nodes) {  // never read outside the node array
                 err |= ST_BOUNDS;
                 node = SENTINEL;
                 leaf = 0;
                 break;
             }
-            const float4* np = a.nodes + 4 * (int64_t)node;
+            const float4* np = rm.nodes + 4 * (int64_t)node;
             const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
             n_nodes++;
             const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
@@ -302,7 +317,7 @@ __device__ __forceinline__ void nearest_hit(const BounceArgs& a, const RayPre& r
             const float t1 = slab(r, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, best_t);
             const bool h0 = t0 < INFINITY, h1 = t1 < INFINITY;
             if (!h0 && !h1) {
-                node = sp > 0 ? stack[--sp * BOUNCE_THREADS] : SENTINEL;
+                node = sp > 0 ? stack[--sp * BT] : SENTINEL;
             } else {
                 const bool swap = h1 && (!h0 || t1 < t0);  // nearest child first
                 node = swap ? r1 : r0;
@@ -313,29 +328,29 @@ __device__ __forceinline__ void nearest_hit(const BounceArgs& a, const RayPre& r
                         leaf = 0;
                         break;
                     }
-                    stack[sp++ * BOUNCE_THREADS] = swap ? r0 : r1;
+                    stack[sp++ * BT] = swap ? r0 : r1;
                 }
             }
             if (node < 0 && leaf == 0) {  // postpone the leaf, keep descending
                 leaf = node;
-                node = sp > 0 ? stack[--sp * BOUNCE_THREADS] : SENTINEL;
+                node = sp > 0 ? stack[--sp * BT] : SENTINEL;
             }
             if (__all_sync(__activemask(), leaf != 0)) break;
         }
         while (leaf != 0) {
             const int code = ~leaf;
             const int first = code >> 3, cnt = code & 7;
-            if ((int64_t)first + cnt > a.n_tris) {
+            if ((int64_t)first + cnt > rm.n_tris) {
                 err |= ST_BOUNDS;
                 node = SENTINEL;
                 break;
             }
-            for (int k = 0; k < cnt; k++) tri_test(r, a.tris + 3 * (int64_t)(first + k), exclude, best_t, best_id);
+            for (int k = 0; k < cnt; k++) tri_test(r, rm.tris + 3 * (int64_t)(first + k), exclude, best_t, best_id);
             n_tests += cnt;
             leaf = 0;
             if (node < 0) {  // a leaf popped from the stack
                 leaf = node;
-                node = sp > 0 ? stack[--sp * BOUNCE_THREADS] : SENTINEL;
+                node = sp > 0 ? stack[--sp * BT] : SENTINEL;
             }
         }
     }
@@ -357,16 +372,19 @@ __device__ __forceinline__ void load_ray(const Queue& q, unsigned int slot, RayS
 
 // One bounce of the ray in s (bounce index bb).  Every lane of the warp calls
 // it; lanes without a ray pass active = false.  Returns true if the ray goes on.
+template <int BT>
 __device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool active, int bb, RayState& s,
                                          int* __restrict__ stack) {
     const int q = (int)s.m.x;
+    const int src = active ? (int)(q / a.per_src) : 0;
+    const RoomDev& rm = a.rooms[active ? a.room_of_src[src] : 0];
     float best_t = INFINITY;
     int hit = -1;
     unsigned int err = 0;
     float4 o4 = s.o, d4 = s.d;
     RayPre rp = ray_pre(make_float3(o4.x, o4.y, o4.z), make_float3(d4.x, d4.y, d4.z));
     int n_nodes = 0, n_tests = 0;
-    if (active) nearest_hit(a, rp, (int)s.m.y, best_t, hit, err, n_nodes, n_tests, stack);
+    if (active) nearest_hit<BT>(a, rm, rp, (int)s.m.y, best_t, hit, err, n_nodes, n_tests, stack);
     if (err) atomicOr(a.status, err);
     const unsigned int amask = __ballot_sync(0xffffffffu, active);
     if (lane == 0 && amask) atomicAdd(a.n_queries, (unsigned long long)__popc(amask));
@@ -374,7 +392,6 @@ __device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool act
     // -- measurement spheres of this ray's source (eq. 22) -----------------
     // each sphere test is evaluated once; crossings of one receiver slot are
     // appended with one atomic per warp
-    const int src = active ? (int)(q / a.per_src) : 0;
     const int rb = active ? a.rcv_beg[src] : 0;
     const int nk = active ? a.rcv_beg[src + 1] - rb : 0;
     const int nk_max = __reduce_max_sync(0xffffffffu, (unsigned)nk);
@@ -423,7 +440,7 @@ __device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool act
     }
     if (hit >= 0) {
         // reflect (eq. 15), absorb (eq. 16), path length (Kahan), hash
-        float4 nr = __ldg(a.tri_nrm + hit);
+        float4 nr = __ldg(rm.tri_nrm + hit);
         int surf = __float_as_int(nr.w);
         float dn = d4.x * nr.x + d4.y * nr.y + d4.z * nr.z;
         // next origin: the hit point pulled back along the incoming ray by
@@ -443,7 +460,7 @@ __device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool act
         d4.x = rx * inv;
         d4.y = ry * inv;
         d4.z = rz * inv;
-        const float* rf = a.refl + 8 * a.mat_of_surf[surf];
+        const float* rf = a.refl + 8 * (rm.mat_base + rm.mat_of_surf[surf]);
         s.e0.x *= __ldg(rf + 0);
         s.e0.y *= __ldg(rf + 1);
         s.e0.z *= __ldg(rf + 2);
@@ -478,8 +495,9 @@ __device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool act
 //   wait for their slowest ray.  It writes no survivors, so the later
 //   launches of the same trace find no live rays and return at once.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(BounceArgs a) {
-    __shared__ int s_stack[STACK_SMEM * BOUNCE_THREADS];
+template <int BT>
+__global__ void __launch_bounds__(BT) k_bounce(BounceArgs a) {
+    __shared__ int s_stack[STACK_SMEM * BT];
     int* stack = s_stack + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const unsigned int n_live = a.live[a.b];
@@ -499,7 +517,7 @@ __global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(BounceArgs a) {
             s.e0 = s.e1 = s.o;
             s.m = make_uint4(0, 0xFFFFFFFFu, 0, 0);
             if (active) load_ray(a.in, slot, s);
-            const bool survive = step_ray(a, lane, active, b, s, stack);
+            const bool survive = step_ray<BT>(a, lane, active, b, s, stack);
             const unsigned int mask = __ballot_sync(0xffffffffu, survive);
             if (mask) {
                 unsigned int obase = 0;
@@ -544,7 +562,7 @@ __global__ void __launch_bounds__(BOUNCE_THREADS) k_bounce(BounceArgs a) {
             exhausted = base + __popc(need) >= n_live;
         }
         if (__ballot_sync(0xffffffffu, has) == 0) break;
-        const bool survive = step_ray(a, lane, has, bb, s, stack);
+        const bool survive = step_ray<BT>(a, lane, has, bb, s, stack);
         if (has) {
             if (survive)
                 bb++;
@@ -566,9 +584,10 @@ __global__ void k_dedup_init(const uint64_t* __restrict__ rec_key, int64_t n, ui
 }
 
 __device__ __forceinline__ bool same_beam(int64_t ra, int64_t rb, const int32_t* rec_rcv, const int32_t* rec_ray,
-                                          const int32_t* rec_m, const int32_t* hist, const int32_t* surf_of,
-                                          int64_t n_traced) {
+                                          const int32_t* rec_m, const int32_t* hist, const RoomDev* rooms,
+                                          const int32_t* room_of_rcv, int64_t n_traced) {
     if (rec_rcv[ra] != rec_rcv[rb] || rec_m[ra] != rec_m[rb]) return false;
+    const int32_t* surf_of = rooms[room_of_rcv[rec_rcv[ra]]].surf_of;
     int m = rec_m[ra];
     int64_t qa = rec_ray[ra], qb = rec_ray[rb];
     for (int k = 0; k < m; k++) {
@@ -581,14 +600,14 @@ __device__ __forceinline__ bool same_beam(int64_t ra, int64_t rb, const int32_t*
 __global__ void k_seg_flags(const uint64_t* __restrict__ keys, const uint32_t* __restrict__ vals, int64_t n,
                             const int32_t* __restrict__ rec_rcv, const int32_t* __restrict__ rec_ray,
                             const int32_t* __restrict__ rec_m, const int32_t* __restrict__ hist,
-                            const int32_t* __restrict__ surf_of, int64_t n_traced, uint32_t* __restrict__ flags,
-                            unsigned long long* collisions) {
+                            const RoomDev* __restrict__ rooms, const int32_t* __restrict__ room_of_rcv,
+                            int64_t n_traced, uint32_t* __restrict__ flags, unsigned long long* collisions) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     uint32_t f = 1;
     if (j > 0 && keys[j] == keys[j - 1]) {
         f = 0;
-        if (!same_beam(vals[j - 1], vals[j], rec_rcv, rec_ray, rec_m, hist, surf_of, n_traced)) {
+        if (!same_beam(vals[j - 1], vals[j], rec_rcv, rec_ray, rec_m, hist, rooms, room_of_rcv, n_traced)) {
             f = 1;
             atomicAdd(collisions, 1ull);
         }
@@ -622,10 +641,9 @@ struct ReconArgs {
     const int32_t* rec_ray;
     const int32_t* rec_m;
     const int32_t* hist;
-    const int32_t* surf_of;
-    const int32_t* mat_of_surf;
-    const Plane* planes;
-    const double* alpha64;   // [n_mat][8]
+    const RoomDev* rooms;
+    const int32_t* room_of_rcv;
+    const double* alpha64;   // [sum of n_mat][8]
     const double* beta64;    // [8]
     const double* src64;     // [S][3]
     const double* rcv64;     // [R][3] by original receiver id
@@ -643,6 +661,7 @@ __global__ void k_reconstruct(ReconArgs a) {
     const int32_t rep = a.o_rep[u];  // set by k_seg_min
     const uint32_t r0 = a.vals[lo];
     const int32_t rcv = a.rec_rcv[r0], m = a.rec_m[r0];
+    const RoomDev& rm = a.rooms[a.room_of_rcv[rcv]];
     const int64_t s = rep / a.per_src;
     double x = a.src64[3 * s], y = a.src64[3 * s + 1], z = a.src64[3 * s + 2];
     double prod[RT_N_BANDS];
@@ -654,13 +673,13 @@ __global__ void k_reconstruct(ReconArgs a) {
             atomicOr(a.status, ST_HISTORY);
             break;
         }
-        int sid = a.surf_of[tri];
-        Plane P = a.planes[sid];
+        int sid = rm.surf_of[tri];
+        Plane P = rm.planes[sid];
         double dist = P.x * x + P.y * y + P.z * z - P.w;
         x -= 2.0 * dist * P.x;
         y -= 2.0 * dist * P.y;
         z -= 2.0 * dist * P.z;
-        const double* al = a.alpha64 + 8 * a.mat_of_surf[sid];
+        const double* al = a.alpha64 + 8 * (rm.mat_base + rm.mat_of_surf[sid]);
 #pragma unroll
         for (int f = 0; f < RT_N_BANDS; f++) prod[f] *= (1.0 - al[f]);
     }
@@ -685,19 +704,9 @@ static unsigned grid_of(int64_t n, int threads) { return (unsigned)((n + threads
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
-struct TraceBuffers {
-    Queue q[2];
-    int32_t* hist;
-    float4* ray_e;
-    float* ray_len;
-    int32_t* ray_hits;
-    int32_t *rec_rcv, *rec_ray, *rec_m;
-    float* rec_len;
-    uint64_t* rec_key;
-    unsigned int* counters;  // live[B+1], fetch[B], status, pad
-    unsigned long long* n_rec;
-};
-
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
 static rt_status alloc_queue(Arena& ar, Queue& q, int64_t n) {
     RR_TRY(ar.alloc(&q.o, n));
     RR_TRY(ar.alloc(&q.d, n));
@@ -707,19 +716,362 @@ static rt_status alloc_queue(Arena& ar, Queue& q, int64_t n) {
     return RT_OK;
 }
 
-static rt_status trace_impl(const rt_tree* tree, const rt_sources* src, const rt_receivers* rcv,
-                            const float* alpha, int32_t n_mat, const rt_trace_params* p, rt_image_sources** out) {
-    if (!tree || !src || !rcv || !alpha || !p || !out) {
+// -- bounce-kernel configurations and the online autotuner -------------------
+// A configuration is a block size and a tail threshold (never / resident
+// threads / every ray).  Every configuration gives identical results per ray,
+// so the autotuner times the real calls: the first calls of a workload class
+// each run the next candidate, and once all have run the fastest is kept
+// (optionally persisted in the file named by RT_AUTOTUNE_CACHE).
+struct Config {
+    int block;
+    int tail_mode;  // 0 never, 1 resident threads, 2 every ray
+};
+static const Config CANDIDATES[] = {{128, 2}, {128, 1}, {64, 2}, {256, 2}, {128, 0}, {64, 1}, {256, 1}};
+static constexpr int N_CANDIDATES = sizeof(CANDIDATES) / sizeof(CANDIDATES[0]);
+
+struct TuneState {
+    float ms[N_CANDIDATES];
+    int next = 0;
+    int best = -1;
+};
+static std::mutex g_tune_mu;
+static std::map<std::string, TuneState> g_tune;
+static bool g_tune_loaded = false;
+
+static void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = getenv("RT_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    char key[256];
+    int best;
+    while (fscanf(f, "%255s %d", key, &best) == 2) {
+        if (best >= 0 && best < N_CANDIDATES) {
+            TuneState t;
+            t.next = N_CANDIDATES;
+            t.best = best;
+            for (float& x : t.ms) x = 0.f;
+            g_tune[key] = t;
+        }
+    }
+    fclose(f);
+}
+
+static void tune_save_locked() {
+    const char* path = getenv("RT_AUTOTUNE_CACHE");
+    if (!path) return;
+    FILE* f = fopen(path, "w");
+    if (!f) return;
+    for (auto& kv : g_tune)
+        if (kv.second.best >= 0) fprintf(f, "%s %d\n", kv.first.c_str(), kv.second.best);
+    fclose(f);
+}
+
+static std::string tune_key(int64_t n_tris, int64_t n_traced, int B, int n_rooms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto lg = [](int64_t x) {
+        int k = 0;
+        while ((1ll << k) < x) k++;
+        return k;
+    };
+    char buf[128];
+    snprintf(buf, sizeof buf, "dev%d_rooms%d_tris2^%d_rays2^%d_b%d", dev, n_rooms, lg(n_tris), lg(n_traced), B);
+    return buf;
+}
+
+static int tune_pick(const std::string& key) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    TuneState& t = g_tune[key];
+    if (t.best >= 0) return t.best;
+    return t.next < N_CANDIDATES ? t.next : 0;
+}
+
+static void tune_report(const std::string& key, int cand, float ms) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    TuneState& t = g_tune[key];
+    if (t.best >= 0 || cand != t.next) return;
+    t.ms[cand] = ms;
+    t.next++;
+    if (t.next == N_CANDIDATES) {
+        int b = 0;
+        for (int k = 1; k < N_CANDIDATES; k++)
+            if (t.ms[k] < t.ms[b]) b = k;
+        t.best = b;
+        tune_save_locked();
+    }
+}
+
+template <int BT>
+static int occupancy_grid() {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bounce<BT>, BT, 0);
+    cudaGetLastError();
+    return device_sm_count() * (occ > 0 ? occ : 1);
+}
+
+static void* kernel_of(int block) {
+    switch (block) {
+        case 64: return (void*)k_bounce<64>;
+        case 256: return (void*)k_bounce<256>;
+        default: return (void*)k_bounce<128>;
+    }
+}
+
+static int grid_of_block(int block) {
+    switch (block) {
+        case 64: return occupancy_grid<64>();
+        case 256: return occupancy_grid<256>();
+        default: return occupancy_grid<128>();
+    }
+}
+
+}  // namespace rr
+
+// -- workspace: reusable scratch and the graph of the bounce loop ------------
+struct rt_workspace {
+    cudaStream_t stream = nullptr;
+    std::vector<void*> owned;
+    int64_t cap_rays = 0;
+    int cap_b = 0;
+    rr::Queue q[2]{};
+    unsigned int* counters = nullptr;
+    unsigned long long* n2 = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    std::vector<cudaGraphNode_t> nodes;
+    int g_b = 0, g_grid = 0, g_block = 0;
+    long long graph_launches = 0;
+
+    void release_graph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+        nodes.clear();
+    }
+    void release_buffers() {
+        for (void* p : owned) rr::dev_free(p, stream);
+        owned.clear();
+        cap_rays = 0;
+        cap_b = 0;
+    }
+};
+
+namespace rr {
+
+// Launch the B bounce kernels.  With a workspace on a capturable stream the
+// loop is captured once into a CUDA graph and later replayed with updated
+// kernel parameters (one graph launch per trace).
+static rt_status run_bounces(BounceArgs a, const Queue q[2], int B, int block, int grid, cudaStream_t s,
+                             rt_workspace* ws) {
+    void* kern = kernel_of(block);
+    std::vector<BounceArgs> args((size_t)B, a);
+    for (int b = 0; b < B; b++) {
+        args[b].b = b;
+        args[b].in = q[b & 1];
+        args[b].out = q[(b + 1) & 1];
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool can_graph = ws && s != nullptr && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
+                           cs == cudaStreamCaptureStatusNone;
+    cudaGetLastError();
+    if (!can_graph) {
+        for (int b = 0; b < B; b++) {
+            void* params[] = {&args[b]};
+            RR_CUDA(cudaLaunchKernel(kern, dim3(grid), dim3(block), params, 0, s));
+            note_launch();
+        }
+        return RT_OK;
+    }
+    if (!ws->exec || ws->g_b != B || ws->g_grid != grid || ws->g_block != block) {
+        ws->release_graph();
+        RR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        for (int b = 0; b < B; b++) {
+            void* params[] = {&args[b]};
+            cudaLaunchKernel(kern, dim3(grid), dim3(block), params, 0, s);
+        }
+        cudaGraph_t g = nullptr;
+        RR_CUDA(cudaStreamEndCapture(s, &g));
+        ws->graph = g;
+        RR_CUDA(cudaGraphInstantiate(&ws->exec, g, 0));
+        // the captured launches form a chain: walk it from the root
+        size_t n = 1;
+        cudaGraphNode_t node;
+        RR_CUDA(cudaGraphGetRootNodes(g, &node, &n));
+        ws->nodes.clear();
+        for (int b = 0; b < B; b++) {
+            ws->nodes.push_back(node);
+            size_t nd = 1;
+            cudaGraphNode_t next = nullptr;
+            if (b + 1 < B) {
+                RR_CUDA(cudaGraphNodeGetDependentNodes(node, &next, nullptr, &nd));
+                node = next;
+            }
+        }
+        ws->g_b = B;
+        ws->g_grid = grid;
+        ws->g_block = block;
+    } else {
+        for (int b = 0; b < B; b++) {
+            cudaKernelNodeParams kp{};
+            void* params[] = {&args[b]};
+            kp.func = kern;
+            kp.gridDim = dim3(grid);
+            kp.blockDim = dim3(block);
+            kp.sharedMemBytes = 0;
+            kp.kernelParams = params;
+            kp.extra = nullptr;
+            RR_CUDA(cudaGraphExecKernelNodeSetParams(ws->exec, ws->nodes[b], &kp));
+        }
+    }
+    RR_CUDA(cudaGraphLaunch(ws->exec, s));
+    ws->graph_launches++;
+    for (int b = 0; b < B; b++) note_launch();
+    return RT_OK;
+}
+
+struct HostRoomTables {
+    std::vector<RoomDev> rooms;
+    std::vector<int32_t> room_of_src, room_of_rcv, rcv_id, rcv_beg;
+    std::vector<float4> rcv;
+    std::vector<float> src;
+    std::vector<double> src64, rcv64, alpha64;
+    std::vector<float> refl;
+    int S = 0, R = 0;
+    int64_t total_tris = 0;
+};
+
+static rt_status gather_rooms(const rt_room* rooms, int n_rooms, HostRoomTables& h) {
+    if (!rooms || n_rooms < 1) {
+        set_error("rt_trace: need at least one room");
+        return RT_ERR_INVALID_ARG;
+    }
+    int mat_base = 0;
+    // global source and receiver numbering: room after room
+    std::vector<int> src_base((size_t)n_rooms + 1, 0), rcv_base((size_t)n_rooms + 1, 0);
+    for (int r = 0; r < n_rooms; r++) {
+        const rt_room& rm = rooms[r];
+        if (!rm.tree || rm.sources.n < 1 || !rm.sources.pos || rm.receivers.n < 0 || !rm.band_absorption ||
+            (rm.receivers.n > 0 && (!rm.receivers.center || !rm.receivers.radius || !rm.receivers.source_of))) {
+            set_error("rt_trace: room %d needs a tree, >= 1 source, valid receivers and an absorption table", r);
+            return RT_ERR_INVALID_ARG;
+        }
+        if (rm.n_materials < rm.tree->n_materials) {
+            set_error("rt_trace: room %d: absorption table has %d materials, mesh uses %d", r, rm.n_materials,
+                      rm.tree->n_materials);
+            return RT_ERR_INVALID_ARG;
+        }
+        src_base[r + 1] = src_base[r] + rm.sources.n;
+        rcv_base[r + 1] = rcv_base[r] + rm.receivers.n;
+    }
+    h.S = src_base[n_rooms];
+    h.R = rcv_base[n_rooms];
+    h.room_of_src.resize((size_t)h.S);
+    h.src.resize((size_t)3 * h.S);
+    h.src64.resize((size_t)3 * h.S);
+    h.room_of_rcv.resize((size_t)std::max(h.R, 1), 0);
+    h.rcv64.resize((size_t)3 * std::max(h.R, 1), 0.0);
+    std::vector<int> gsrc((size_t)std::max(h.R, 1), 0);  // global source of each global receiver
+    for (int r = 0; r < n_rooms; r++) {
+        const rt_room& rm = rooms[r];
+        for (int64_t k = 0; k < (int64_t)rm.n_materials * RT_N_BANDS; k++) {
+            float al = rm.band_absorption[k];
+            if (!(al >= 0.0f && al <= 1.0f)) {
+                set_error("rt_trace: room %d: absorption coefficients must lie in [0, 1]", r);
+                return RT_ERR_INVALID_ARG;
+            }
+            h.refl.push_back(1.0f - al);
+            h.alpha64.push_back((double)al);
+        }
+        for (int k = 0; k < rm.sources.n; k++) {
+            const int g = src_base[r] + k;
+            h.room_of_src[g] = r;
+            for (int c = 0; c < 3; c++) {
+                double x = rm.sources.pos[3 * k + c];
+                if (!std::isfinite(x)) {
+                    set_error("rt_trace: room %d: non-finite source position", r);
+                    return RT_ERR_INVALID_ARG;
+                }
+                h.src64[3 * g + c] = x;
+                h.src[3 * g + c] = (float)x;
+            }
+        }
+        for (int k = 0; k < rm.receivers.n; k++) {
+            const int g = rcv_base[r] + k;
+            const int so = rm.receivers.source_of[k];
+            if (so < 0 || so >= rm.sources.n || !(rm.receivers.radius[k] > 0)) {
+                set_error("rt_trace: room %d receiver %d invalid (source index or radius)", r, k);
+                return RT_ERR_INVALID_ARG;
+            }
+            for (int c = 0; c < 3; c++) {
+                double x = rm.receivers.center[3 * k + c];
+                if (!std::isfinite(x)) {
+                    set_error("rt_trace: room %d receiver %d has a non-finite centre", r, k);
+                    return RT_ERR_INVALID_ARG;
+                }
+                h.rcv64[3 * g + c] = x;
+            }
+            h.room_of_rcv[g] = r;
+            gsrc[g] = src_base[r] + so;
+        }
+        RoomDev d{};
+        d.nodes = rm.tree->nodes;
+        d.tris = rm.tree->tris;
+        d.tri_nrm = rm.tree->tri_nrm;
+        d.mat_of_surf = rm.tree->mat_of_surf;
+        d.surf_of = rm.tree->surf_of;
+        d.planes = rm.tree->planes;
+        d.n_nodes = rm.tree->n_nodes;
+        d.n_tris = rm.tree->n_tris;
+        d.mat_base = mat_base;
+        mat_base += rm.n_materials;
+        h.total_tris += rm.tree->n_tris;
+        h.rooms.push_back(d);
+    }
+    // receivers grouped by global source
+    std::vector<int> order((size_t)h.R);
+    for (int k = 0; k < h.R; k++) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return gsrc[a] < gsrc[b]; });
+    h.rcv.resize((size_t)std::max(h.R, 1));
+    h.rcv_id.resize((size_t)std::max(h.R, 1), 0);
+    h.rcv_beg.assign((size_t)h.S + 1, 0);
+    for (int k = 0; k < h.R; k++) {
+        const int o = order[k];
+        const int r = h.room_of_rcv[o];
+        const int local = o - rcv_base[r];
+        const float rad = (float)rooms[r].receivers.radius[local];
+        h.rcv[k] = make_float4((float)h.rcv64[3 * o], (float)h.rcv64[3 * o + 1], (float)h.rcv64[3 * o + 2], rad * rad);
+        h.rcv_id[k] = o;
+        h.rcv_beg[gsrc[o] + 1]++;
+    }
+    for (int k = 0; k < h.S; k++) h.rcv_beg[k + 1] += h.rcv_beg[k];
+    return RT_OK;
+}
+
+template <class T>
+static rt_status upload(Arena& ar, const std::vector<T>& v, T** out, cudaStream_t s) {
+    RR_TRY(ar.alloc(out, std::max<size_t>(v.size(), 1)));
+    if (!v.empty()) RR_CUDA(cudaMemcpyAsync(*out, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
+    return RT_OK;
+}
+
+static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_trace_params* p,
+                                  rt_image_sources** out) {
+    if (!p || !out) {
         set_error("rt_trace: null argument");
         return RT_ERR_INVALID_ARG;
     }
     *out = nullptr;
     cudaStream_t s = (cudaStream_t)p->stream;
+    rt_workspace* ws = p->workspace;
     const int64_t N = p->n_rays;
     const int B = p->n_bounces;
-    if (N < 1 || B < 1 || B > RT_MAX_BOUNCES || !(p->c > 0) || src->n < 1 || !src->pos || rcv->n < 0 ||
-        (rcv->n > 0 && (!rcv->center || !rcv->radius || !rcv->source_of))) {
-        set_error("rt_trace: need n_rays >= 1, 1 <= n_bounces <= %d, c > 0, >= 1 source", RT_MAX_BOUNCES);
+    if (N < 1 || B < 1 || B > RT_MAX_BOUNCES || !(p->c > 0)) {
+        set_error("rt_trace: need n_rays >= 1, 1 <= n_bounces <= %d, c > 0", RT_MAX_BOUNCES);
         return RT_ERR_INVALID_ARG;
     }
     if (p->ray_begin < 0 || p->ray_begin >= N) {
@@ -731,112 +1083,110 @@ static rt_status trace_impl(const rt_tree* tree, const rt_sources* src, const rt
         set_error("rt_trace: ray range exceeds n_rays");
         return RT_ERR_INVALID_ARG;
     }
-    const int S = src->n, R = rcv->n;
+    if (p->max_node_visits < 0) {
+        set_error("rt_trace: max_node_visits must be >= 0");
+        return RT_ERR_INVALID_ARG;
+    }
+    if (p->block_size != 0 && p->block_size != 64 && p->block_size != 128 && p->block_size != 256) {
+        set_error("rt_trace: block_size must be 0, 64, 128 or 256");
+        return RT_ERR_INVALID_ARG;
+    }
+    if (ws && ws->stream != s && !ws->owned.empty()) {
+        set_error("rt_trace: a workspace serves one stream");
+        return RT_ERR_INVALID_ARG;
+    }
+    HostRoomTables h;
+    RR_TRY(gather_rooms(rooms, n_rooms, h));
+    const int S = h.S, R = h.R;
     const int64_t n_traced = per_src * S;
     if (n_traced > (int64_t)INT32_MAX) {
         set_error("rt_trace: %lld rays exceed the 32-bit ray index", (long long)n_traced);
         return RT_ERR_INVALID_ARG;
     }
-    if (n_mat < tree->n_materials) {
-        set_error("rt_trace: absorption table has %d materials, mesh uses %d", n_mat, tree->n_materials);
-        return RT_ERR_INVALID_ARG;
-    }
-    for (int64_t k = 0; k < (int64_t)n_mat * RT_N_BANDS; k++)
-        if (!(alpha[k] >= 0.0f && alpha[k] <= 1.0f)) {
-            set_error("rt_trace: absorption coefficients must lie in [0, 1]");
-            return RT_ERR_INVALID_ARG;
-        }
-    for (int k = 0; k < 3 * S; k++)
-        if (!std::isfinite(src->pos[k])) {
-            set_error("rt_trace: non-finite source position");
-            return RT_ERR_INVALID_ARG;
-        }
-    // receivers grouped by source
-    std::vector<int> order((size_t)R);
-    for (int k = 0; k < R; k++) {
-        order[k] = k;
-        if (rcv->source_of[k] < 0 || rcv->source_of[k] >= S || !(rcv->radius[k] > 0) ||
-            !std::isfinite(rcv->center[3 * k]) || !std::isfinite(rcv->center[3 * k + 1]) ||
-            !std::isfinite(rcv->center[3 * k + 2])) {
-            set_error("rt_trace: receiver %d invalid (source index, radius or centre)", k);
-            return RT_ERR_INVALID_ARG;
-        }
-    }
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int b) { return rcv->source_of[a] < rcv->source_of[b]; });
-    std::vector<float4> h_rcv((size_t)std::max(R, 1));
-    std::vector<int32_t> h_rcv_id((size_t)std::max(R, 1)), h_beg((size_t)S + 1, 0);
-    for (int k = 0; k < R; k++) {
-        int o = order[k];
-        float r = (float)rcv->radius[o];
-        h_rcv[k] = make_float4((float)rcv->center[3 * o], (float)rcv->center[3 * o + 1], (float)rcv->center[3 * o + 2],
-                               r * r);
-        h_rcv_id[k] = o;
-        h_beg[rcv->source_of[o] + 1]++;
-    }
-    for (int k = 0; k < S; k++) h_beg[k + 1] += h_beg[k];
-    std::vector<float> h_src((size_t)3 * S), h_refl((size_t)n_mat * 8);
-    std::vector<double> h_alpha64((size_t)n_mat * 8), h_beta64(8, 0.0);
-    for (int k = 0; k < 3 * S; k++) h_src[k] = (float)src->pos[k];
-    for (int64_t k = 0; k < (int64_t)n_mat * 8; k++) {
-        h_refl[k] = 1.0f - alpha[k];
-        h_alpha64[k] = (double)alpha[k];
-    }
+    std::vector<double> h_beta64(8, 0.0);
     if (p->air_beta)
         for (int f = 0; f < 8; f++) h_beta64[f] = (double)p->air_beta[f];
 
     Arena tmp(s), keep(s);
+    RoomDev* d_rooms;
+    int32_t *d_room_of_src, *d_room_of_rcv, *d_rcv_id, *d_beg;
     float4* d_rcv;
-    int32_t *d_rcv_id, *d_beg;
     float *d_src, *d_refl;
     double *d_alpha64, *d_beta64, *d_src64, *d_rcv64;
-    RR_TRY(tmp.alloc(&d_rcv, std::max(R, 1)));
-    RR_TRY(tmp.alloc(&d_rcv_id, std::max(R, 1)));
-    RR_TRY(tmp.alloc(&d_beg, S + 1));
-    RR_TRY(tmp.alloc(&d_src, 3 * S));
-    RR_TRY(tmp.alloc(&d_refl, (int64_t)n_mat * 8));
-    RR_TRY(tmp.alloc(&d_alpha64, (int64_t)n_mat * 8));
-    RR_TRY(tmp.alloc(&d_beta64, 8));
-    RR_TRY(tmp.alloc(&d_src64, 3 * S));
-    RR_TRY(tmp.alloc(&d_rcv64, 3 * std::max(R, 1)));
-    RR_CUDA(cudaMemcpyAsync(d_rcv, h_rcv.data(), sizeof(float4) * std::max(R, 1), cudaMemcpyHostToDevice, s));
-    RR_CUDA(cudaMemcpyAsync(d_rcv_id, h_rcv_id.data(), sizeof(int32_t) * std::max(R, 1), cudaMemcpyHostToDevice, s));
-    RR_CUDA(cudaMemcpyAsync(d_beg, h_beg.data(), sizeof(int32_t) * (S + 1), cudaMemcpyHostToDevice, s));
-    RR_CUDA(cudaMemcpyAsync(d_src, h_src.data(), sizeof(float) * 3 * S, cudaMemcpyHostToDevice, s));
-    RR_CUDA(cudaMemcpyAsync(d_refl, h_refl.data(), sizeof(float) * n_mat * 8, cudaMemcpyHostToDevice, s));
-    RR_CUDA(cudaMemcpyAsync(d_alpha64, h_alpha64.data(), sizeof(double) * n_mat * 8, cudaMemcpyHostToDevice, s));
-    RR_CUDA(cudaMemcpyAsync(d_beta64, h_beta64.data(), sizeof(double) * 8, cudaMemcpyHostToDevice, s));
-    RR_CUDA(cudaMemcpyAsync(d_src64, src->pos, sizeof(double) * 3 * S, cudaMemcpyHostToDevice, s));
-    if (R > 0) RR_CUDA(cudaMemcpyAsync(d_rcv64, rcv->center, sizeof(double) * 3 * R, cudaMemcpyHostToDevice, s));
+    RR_TRY(upload(tmp, h.rooms, &d_rooms, s));
+    RR_TRY(upload(tmp, h.room_of_src, &d_room_of_src, s));
+    RR_TRY(upload(tmp, h.room_of_rcv, &d_room_of_rcv, s));
+    RR_TRY(upload(tmp, h.rcv, &d_rcv, s));
+    RR_TRY(upload(tmp, h.rcv_id, &d_rcv_id, s));
+    RR_TRY(upload(tmp, h.rcv_beg, &d_beg, s));
+    RR_TRY(upload(tmp, h.src, &d_src, s));
+    RR_TRY(upload(tmp, h.refl, &d_refl, s));
+    RR_TRY(upload(tmp, h.alpha64, &d_alpha64, s));
+    RR_TRY(upload(tmp, h_beta64, &d_beta64, s));
+    RR_TRY(upload(tmp, h.src64, &d_src64, s));
+    RR_TRY(upload(tmp, h.rcv64, &d_rcv64, s));
 
-    // per-ray buffers (queues are scratch; history and final state are kept)
-    TraceBuffers tb{};
-    RR_TRY(alloc_queue(tmp, tb.q[0], n_traced));
-    RR_TRY(alloc_queue(tmp, tb.q[1], n_traced));
-    RR_TRY(keep.alloc(&tb.hist, (int64_t)B * n_traced));
-    RR_TRY(keep.alloc(&tb.ray_e, 2 * n_traced));
-    RR_TRY(keep.alloc(&tb.ray_len, n_traced));
-    RR_TRY(keep.alloc(&tb.ray_hits, n_traced));
+    // scratch: queues and counters (from the workspace when given)
+    Queue q[2];
+    unsigned int* counters;
+    unsigned long long* n2d;
     const int n_counters = 2 * B + 4;
-    RR_TRY(tmp.alloc(&tb.counters, n_counters));
-    RR_TRY(tmp.alloc(&tb.n_rec, 2));  // records, queries
+    if (ws) {
+        if (ws->cap_rays < n_traced || ws->cap_b < B) {
+            ws->release_graph();
+            ws->release_buffers();
+            ws->stream = s;
+            Arena war(s);
+            RR_TRY(alloc_queue(war, ws->q[0], n_traced));
+            RR_TRY(alloc_queue(war, ws->q[1], n_traced));
+            RR_TRY(war.alloc(&ws->counters, n_counters));
+            RR_TRY(war.alloc(&ws->n2, 2));
+            ws->owned = war.release();
+            ws->cap_rays = n_traced;
+            ws->cap_b = B;
+        }
+        q[0] = ws->q[0];
+        q[1] = ws->q[1];
+        counters = ws->counters;
+        n2d = ws->n2;
+    } else {
+        RR_TRY(alloc_queue(tmp, q[0], n_traced));
+        RR_TRY(alloc_queue(tmp, q[1], n_traced));
+        RR_TRY(tmp.alloc(&counters, n_counters));
+        RR_TRY(tmp.alloc(&n2d, 2));
+    }
+    int32_t* hist;
+    float4* ray_e;
+    float* ray_len;
+    int32_t* ray_hits;
+    RR_TRY(keep.alloc(&hist, (int64_t)B * n_traced));
+    RR_TRY(keep.alloc(&ray_e, 2 * n_traced));
+    RR_TRY(keep.alloc(&ray_len, n_traced));
+    RR_TRY(keep.alloc(&ray_hits, n_traced));
 
-    if (p->max_node_visits < 0) {
-        set_error("rt_trace: max_node_visits must be >= 0");
-        return RT_ERR_INVALID_ARG;
-    }
+    // bounce-kernel configuration
     const int a_step_cap = p->max_node_visits > 0 ? p->max_node_visits : DEFAULT_NODE_VISITS;
-    const int block = p->block_size > 0 ? p->block_size : BOUNCE_THREADS;
-    if (block != BOUNCE_THREADS) {
-        set_error("rt_trace: block_size must be 0 or %d in this build", BOUNCE_THREADS);
-        return RT_ERR_INVALID_ARG;
+    const bool autotune = p->tail_rays == RT_TAIL_AUTOTUNE;
+    std::string key;
+    int cand = -1;
+    int block = p->block_size > 0 ? p->block_size : 128;
+    int tail_mode = p->tail_rays < 0 ? 0 : 1;
+    if (autotune) {
+        key = tune_key(h.total_tris, n_traced, B, n_rooms);
+        cand = tune_pick(key);
+        block = CANDIDATES[cand].block;
+        tail_mode = CANDIDATES[cand].tail_mode;
     }
-    int occ = 0;
-    RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bounce, block, 0));
-    const int grid = device_sm_count() * std::max(occ, 1);
-    // below this many live rays one launch finishes the trace (tail mode)
-    const unsigned int tail = p->tail_rays > 0 ? (unsigned int)p->tail_rays
-                            : (p->tail_rays < 0 ? 0u : (unsigned int)grid * (unsigned int)block);
+    const int grid = grid_of_block(block);
+    unsigned int tail = 0;
+    if (autotune) {
+        tail = tail_mode == 0 ? 0u : (tail_mode == 1 ? (unsigned int)grid * (unsigned int)block
+                                                    : (unsigned int)std::min<int64_t>(n_traced, UINT32_MAX));
+    } else if (p->tail_rays > 0) {
+        tail = (unsigned int)p->tail_rays;
+    } else if (p->tail_rays == 0) {
+        tail = (unsigned int)grid * (unsigned int)block;
+    }
 
     unsigned long long cap = (unsigned long long)std::min<int64_t>(
         std::max<int64_t>(1 << 20, 2 * n_traced), std::max<int64_t>(1, n_traced * (int64_t)B * std::max(R, 1)));
@@ -851,17 +1201,20 @@ static rt_status trace_impl(const rt_tree* tree, const rt_sources* src, const rt
     unsigned long long n_rec = 0, n2[2] = {0, 0};
     std::vector<unsigned int> h_cnt((size_t)n_counters);
     Arena rec_arena(s);
+    int32_t *rec_rcv = nullptr, *rec_ray = nullptr, *rec_m = nullptr;
+    float* rec_len = nullptr;
+    uint64_t* rec_key = nullptr;
     for (int attempt = 0; attempt < 2; attempt++) {
-        RR_TRY(rec_arena.alloc(&tb.rec_rcv, (int64_t)cap));
-        RR_TRY(rec_arena.alloc(&tb.rec_ray, (int64_t)cap));
-        RR_TRY(rec_arena.alloc(&tb.rec_m, (int64_t)cap));
-        RR_TRY(rec_arena.alloc(&tb.rec_len, (int64_t)cap));
-        RR_TRY(rec_arena.alloc(&tb.rec_key, (int64_t)cap));
-        RR_CUDA(cudaMemsetAsync(tb.hist, 0xFF, sizeof(int32_t) * (size_t)B * n_traced, s));
-        RR_CUDA(cudaMemsetAsync(tb.counters, 0, sizeof(unsigned int) * n_counters, s));
-        RR_CUDA(cudaMemsetAsync(tb.n_rec, 0, 2 * sizeof(unsigned long long), s));
+        RR_TRY(rec_arena.alloc(&rec_rcv, (int64_t)cap));
+        RR_TRY(rec_arena.alloc(&rec_ray, (int64_t)cap));
+        RR_TRY(rec_arena.alloc(&rec_m, (int64_t)cap));
+        RR_TRY(rec_arena.alloc(&rec_len, (int64_t)cap));
+        RR_TRY(rec_arena.alloc(&rec_key, (int64_t)cap));
+        RR_CUDA(cudaMemsetAsync(hist, 0xFF, sizeof(int32_t) * (size_t)B * n_traced, s));
+        RR_CUDA(cudaMemsetAsync(counters, 0, sizeof(unsigned int) * n_counters, s));
+        RR_CUDA(cudaMemsetAsync(n2d, 0, 2 * sizeof(unsigned long long), s));
         unsigned int n0 = (unsigned int)n_traced;
-        RR_CUDA(cudaMemcpyAsync(tb.counters, &n0, sizeof n0, cudaMemcpyHostToDevice, s));
+        RR_CUDA(cudaMemcpyAsync(counters, &n0, sizeof n0, cudaMemcpyHostToDevice, s));
         RR_CUDA(cudaEventRecord(ev.e[0], s));
         int64_t F = 1, F1 = 1;  // largest Fibonacci number <= sqrt(per_src)
         while (F1 * F1 <= per_src) {
@@ -869,35 +1222,31 @@ static rt_status trace_impl(const rt_tree* tree, const rt_sources* src, const rt
             F = F1;
             F1 = t;
         }
-        RR_LAUNCH(k_gen_rays, grid_of(n_traced, 256), 256, 0, s, tb.q[0], d_src, n_traced, per_src, p->ray_begin, N, F);
+        RR_LAUNCH(k_gen_rays, grid_of(n_traced, 256), 256, 0, s, q[0], d_src, n_traced, per_src, p->ray_begin, N, F);
         RR_CUDA(cudaGetLastError());
         RR_CUDA(cudaEventRecord(ev.e[1], s));
         BounceArgs a{};
-        a.nodes = tree->nodes;
-        a.tris = tree->tris;
-        a.n_nodes = tree->n_nodes;
-        a.n_tris = tree->n_tris;
-        a.tri_nrm = tree->tri_nrm;
-        a.mat_of_surf = tree->mat_of_surf;
+        a.rooms = d_rooms;
+        a.room_of_src = d_room_of_src;
         a.refl = d_refl;
         a.rcv = d_rcv;
         a.rcv_id = d_rcv_id;
         a.rcv_beg = d_beg;
-        a.hist = tb.hist;
-        a.ray_e = tb.ray_e;
-        a.ray_len = tb.ray_len;
-        a.ray_hits = tb.ray_hits;
-        a.rec_rcv = tb.rec_rcv;
-        a.rec_ray = tb.rec_ray;
-        a.rec_m = tb.rec_m;
-        a.rec_len = tb.rec_len;
-        a.rec_key = tb.rec_key;
+        a.hist = hist;
+        a.ray_e = ray_e;
+        a.ray_len = ray_len;
+        a.ray_hits = ray_hits;
+        a.rec_rcv = rec_rcv;
+        a.rec_ray = rec_ray;
+        a.rec_m = rec_m;
+        a.rec_len = rec_len;
+        a.rec_key = rec_key;
         a.rec_cap = cap;
-        a.live = tb.counters;
-        a.fetch = tb.counters + (B + 1);
-        a.status = tb.counters + (2 * B + 1);
-        a.n_rec = tb.n_rec;
-        a.n_queries = tb.n_rec + 1;
+        a.live = counters;
+        a.fetch = counters + (B + 1);
+        a.status = counters + (2 * B + 1);
+        a.n_rec = n2d;
+        a.n_queries = n2d + 1;
         a.tail_threshold = tail;
         a.n_traced = n_traced;
         a.per_src = per_src;
@@ -907,16 +1256,11 @@ static rt_status trace_impl(const rt_tree* tree, const rt_sources* src, const rt
         a.debug_t = p->debug_t;
         a.debug_state = p->debug_state;
         a.debug_cost = p->debug_cost;
-        for (int b = 0; b < B; b++) {
-            a.b = b;
-            a.in = tb.q[b & 1];
-            a.out = tb.q[(b + 1) & 1];
-            RR_LAUNCH(k_bounce, grid, block, 0, s, a);
-        }
+        RR_TRY(run_bounces(a, q, B, block, grid, s, ws));
         RR_CUDA(cudaGetLastError());
         RR_CUDA(cudaEventRecord(ev.e[2], s));
-        RR_CUDA(cudaMemcpyAsync(h_cnt.data(), tb.counters, sizeof(unsigned int) * n_counters, cudaMemcpyDeviceToHost, s));
-        RR_CUDA(cudaMemcpyAsync(n2, tb.n_rec, sizeof n2, cudaMemcpyDeviceToHost, s));
+        RR_CUDA(cudaMemcpyAsync(h_cnt.data(), counters, sizeof(unsigned int) * n_counters, cudaMemcpyDeviceToHost, s));
+        RR_CUDA(cudaMemcpyAsync(n2, n2d, sizeof n2, cudaMemcpyDeviceToHost, s));
         RR_CUDA(cudaStreamSynchronize(s));
         n_rec = n2[0];
         unsigned int st = h_cnt[2 * B + 1];
@@ -942,6 +1286,9 @@ static rt_status trace_impl(const rt_tree* tree, const rt_sources* src, const rt
         cap = n_rec;
     }
     const int64_t queries = (int64_t)n2[1];
+    float ms_bounce = 0.f;
+    cudaEventElapsedTime(&ms_bounce, ev.e[1], ev.e[2]);
+    if (autotune) tune_report(key, cand, ms_bounce);
 
     // -- dedup + reconstruction ---------------------------------------------
     const int64_t nr = (int64_t)n_rec;
@@ -988,27 +1335,26 @@ static rt_status trace_impl(const rt_tree* tree, const rt_sources* src, const rt
         RR_TRY(tmp.alloc((char**)&sort_tmp, sort_temp_bytes(nr)));
         RR_TRY(tmp.alloc((char**)&scan_tmp, scan_temp_bytes(nr)));
         RR_CUDA(cudaMemsetAsync(d_coll, 0, sizeof(unsigned long long), s));
-        RR_LAUNCH(k_dedup_init, grid_of(nr, 256), 256, 0, s, tb.rec_key, nr, keys, vals);
+        RR_LAUNCH(k_dedup_init, grid_of(nr, 256), 256, 0, s, rec_key, nr, keys, vals);
         RR_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, nr, 0, 64, sort_tmp, s));
-        RR_LAUNCH(k_seg_flags, grid_of(nr, 256), 256, 0, s, keys, vals, nr, tb.rec_rcv, tb.rec_ray, tb.rec_m, tb.hist,
-                                                     tree->surf_of, n_traced, flags, d_coll);
+        RR_LAUNCH(k_seg_flags, grid_of(nr, 256), 256, 0, s, keys, vals, nr, rec_rcv, rec_ray, rec_m, hist, d_rooms,
+                  d_room_of_rcv, n_traced, flags, d_coll);
         RR_CUDA(cudaGetLastError());
         RR_TRY(exclusive_scan_u32(flags, segid, nr, nuniq, scan_tmp, s));
         RR_LAUNCH(k_seg_heads, grid_of(nr, 256), 256, 0, s, flags, segid, nr, heads);
         RR_CUDA(cudaMemsetAsync(o_rep, 0x7F, sizeof(int32_t) * nr, s));
-        RR_LAUNCH(k_seg_min, grid_of(nr, 256), 256, 0, s, vals, flags, segid, nr, tb.rec_ray, o_rep);
+        RR_LAUNCH(k_seg_min, grid_of(nr, 256), 256, 0, s, vals, flags, segid, nr, rec_ray, o_rep);
         ReconArgs ra;
         ra.heads = heads;
         ra.vals = vals;
         ra.n_unique_dev = nuniq;
-        ra.status = tb.counters + (2 * B + 1);
-        ra.rec_rcv = tb.rec_rcv;
-        ra.rec_ray = tb.rec_ray;
-        ra.rec_m = tb.rec_m;
-        ra.hist = tb.hist;
-        ra.surf_of = tree->surf_of;
-        ra.mat_of_surf = tree->mat_of_surf;
-        ra.planes = tree->planes;
+        ra.status = counters + (2 * B + 1);
+        ra.rec_rcv = rec_rcv;
+        ra.rec_ray = rec_ray;
+        ra.rec_m = rec_m;
+        ra.hist = hist;
+        ra.rooms = d_rooms;
+        ra.room_of_rcv = d_room_of_rcv;
         ra.alpha64 = d_alpha64;
         ra.beta64 = d_beta64;
         ra.src64 = d_src64;
@@ -1044,19 +1390,21 @@ static rt_status trace_impl(const rt_tree* tree, const rt_sources* src, const rt
     v.energy = o_energy;
     v.n_traced = n_traced;
     v.n_bounces = B;
-    v.hist = tb.hist;
-    v.ray_energy = (const float*)tb.ray_e;
-    v.ray_length = tb.ray_len;
-    v.ray_hits = tb.ray_hits;
+    v.hist = hist;
+    v.ray_energy = (const float*)ray_e;
+    v.ray_length = ray_len;
+    v.ray_hits = ray_hits;
     v.n_records = nr;
-    v.rec_rcv = tb.rec_rcv;
-    v.rec_ray = tb.rec_ray;
-    v.rec_order = tb.rec_m;
-    v.rec_length = tb.rec_len;
+    v.rec_rcv = rec_rcv;
+    v.rec_ray = rec_ray;
+    v.rec_order = rec_m;
+    v.rec_length = rec_len;
     v.queries = queries;
     v.hash_collisions = (int64_t)collisions;
+    v.block_size = block;
+    v.tail_rays = (int64_t)tail;
     cudaEventElapsedTime(&v.ms_rays, ev.e[0], ev.e[1]);
-    cudaEventElapsedTime(&v.ms_bounces, ev.e[1], ev.e[2]);
+    v.ms_bounces = ms_bounce;
     if (nr > 0) cudaEventElapsedTime(&v.ms_image_sources, ev.e[2], ev.e[3]);
     cudaGetLastError();
     is->owned = keep.release();
@@ -1072,7 +1420,42 @@ extern "C" rt_status rt_trace(const rt_tree* tree, const rt_sources* src, const 
                               const float* band_absorption, int32_t n_materials, const rt_trace_params* params,
                               rt_image_sources** out) {
     rr::clear_error();
-    return rr::trace_impl(tree, src, rcv, band_absorption, n_materials, params, out);
+    if (!tree || !src || !rcv || !band_absorption) {
+        rr::set_error("rt_trace: null argument");
+        return RT_ERR_INVALID_ARG;
+    }
+    rt_room room;
+    room.tree = tree;
+    room.sources = *src;
+    room.receivers = *rcv;
+    room.band_absorption = band_absorption;
+    room.n_materials = n_materials;
+    return rr::trace_batch_impl(&room, 1, params, out);
+}
+
+extern "C" rt_status rt_trace_batch(const rt_room* rooms, int32_t n_rooms, const rt_trace_params* params,
+                                    rt_image_sources** out) {
+    rr::clear_error();
+    return rr::trace_batch_impl(rooms, n_rooms, params, out);
+}
+
+extern "C" rt_status rt_workspace_create(rt_workspace** out) {
+    rr::clear_error();
+    if (!out) {
+        rr::set_error("rt_workspace_create: null output");
+        return RT_ERR_INVALID_ARG;
+    }
+    *out = new rt_workspace();
+    return RT_OK;
+}
+
+extern "C" int64_t rt_workspace_graph_launches(const rt_workspace* ws) { return ws ? ws->graph_launches : 0; }
+
+extern "C" void rt_workspace_free(rt_workspace* ws) {
+    if (!ws) return;
+    ws->release_graph();
+    ws->release_buffers();
+    delete ws;
 }
 
 extern "C" rt_status rt_image_sources_view(const rt_image_sources* is, rt_is_view* out) {

@@ -25,7 +25,10 @@ STATUS_NAMES = {0: "RT_OK", 1: "RT_ERR_INVALID_ARG", 2: "RT_ERR_DEGENERATE_MESH"
                 8: "RT_ERR_INTERNAL"}
 RT_MEM_HOST, RT_MEM_DEVICE = 0, 1
 
-EXPORTED = ["rt_build_tree", "rt_tree_free", "rt_tree_info", "rt_trace", "rt_image_sources_view",
+RT_TAIL_AUTOTUNE = -2
+
+EXPORTED = ["rt_build_tree", "rt_tree_free", "rt_tree_info", "rt_trace", "rt_trace_batch", "rt_image_sources_view",
+            "rt_workspace_create", "rt_workspace_free", "rt_workspace_graph_launches",
             "rt_image_sources_free", "rt_rir", "rt_rir_static", "rt_response_get", "rt_response_download",
             "rt_response_free",
             "rt_last_error", "rt_api_version", "rt_launch_count", "rt_measure_l2_bandwidth", "rt_set_allocator"]
@@ -58,7 +61,12 @@ class rt_trace_params(C.Structure):
                 ("n_bounces", C.c_int32), ("max_distance", C.c_double), ("air_beta", P), ("c", C.c_double),
                 ("block_size", C.c_int32), ("max_node_visits", C.c_int32), ("tail_rays", C.c_int32),
                 ("stream", P), ("debug_t", P),
-                ("debug_state", P), ("debug_cost", P)]
+                ("debug_state", P), ("debug_cost", P), ("workspace", P)]
+
+
+class rt_room(C.Structure):
+    _fields_ = [("tree", P), ("sources", rt_sources), ("receivers", rt_receivers), ("band_absorption", P),
+                ("n_materials", C.c_int32)]
 
 
 class rt_is_view(C.Structure):
@@ -66,8 +74,8 @@ class rt_is_view(C.Structure):
                 ("dist", P), ("time", P), ("energy", P), ("n_traced", C.c_int64), ("n_bounces", C.c_int32),
                 ("hist", P), ("ray_energy", P), ("ray_length", P), ("ray_hits", P), ("n_records", C.c_int64),
                 ("rec_rcv", P), ("rec_ray", P), ("rec_order", P), ("rec_length", P), ("queries", C.c_int64),
-                ("hash_collisions", C.c_int64), ("ms_rays", C.c_float), ("ms_bounces", C.c_float),
-                ("ms_image_sources", C.c_float)]
+                ("hash_collisions", C.c_int64), ("block_size", C.c_int32), ("tail_rays", C.c_int64),
+                ("ms_rays", C.c_float), ("ms_bounces", C.c_float), ("ms_image_sources", C.c_float)]
 
 
 class rt_response_view(C.Structure):
@@ -100,6 +108,13 @@ def lib():
             L.rt_trace.restype = st
             L.rt_trace.argtypes = [P, C.POINTER(rt_sources), C.POINTER(rt_receivers), P, C.c_int32,
                                    C.POINTER(rt_trace_params), C.POINTER(P)]
+            L.rt_trace_batch.restype = st
+            L.rt_trace_batch.argtypes = [C.POINTER(rt_room), C.c_int32, C.POINTER(rt_trace_params), C.POINTER(P)]
+            L.rt_workspace_create.restype = st
+            L.rt_workspace_create.argtypes = [C.POINTER(P)]
+            L.rt_workspace_free.argtypes = [P]
+            L.rt_workspace_graph_launches.restype = C.c_int64
+            L.rt_workspace_graph_launches.argtypes = [P]
             L.rt_image_sources_view.restype = st
             L.rt_image_sources_view.argtypes = [P, C.POINTER(rt_is_view)]
             L.rt_image_sources_free.argtypes = [P]
@@ -270,6 +285,7 @@ class ImageSources:
         self.queries = v.queries
         self.hash_collisions = v.hash_collisions
         self.ms_rays, self.ms_bounces, self.ms_image_sources = v.ms_rays, v.ms_bounces, v.ms_image_sources
+        self.block_size, self.tail_rays = v.block_size, v.tail_rays
 
     def free(self):
         if getattr(self, "_h", None):
@@ -283,7 +299,7 @@ class ImageSources:
 def rt_trace(tree: Tree, sources, rcv_center, rcv_radius, rcv_source, band_absorption, n_rays, n_bounces,
              ray_begin=0, ray_count=0, max_distance=0.0, air_beta=None, c=343.2, block_size=0,
              max_node_visits=0, tail_rays=0, stream=None, debug_t=None, debug_state=None,
-             debug_cost=None) -> ImageSources:
+             debug_cost=None, workspace=None) -> ImageSources:
     """Propagate rays and build image sources (host inputs; see roomrays.h)."""
     src, ps = _host(np.asarray(sources, np.float64).reshape(-1, 3), np.float64)
     rc, prc = _host(np.asarray(rcv_center, np.float64).reshape(-1, 3), np.float64)
@@ -300,7 +316,8 @@ def rt_trace(tree: Tree, sources, rcv_center, rcv_radius, rcv_source, band_absor
                           float(c), int(block_size), int(max_node_visits), int(tail_rays), _stream_ptr(stream),
                           P(debug_t.data_ptr()) if debug_t is not None else None,
                           P(debug_state.data_ptr()) if debug_state is not None else None,
-                          P(debug_cost.data_ptr()) if debug_cost is not None else None)
+                          P(debug_cost.data_ptr()) if debug_cost is not None else None,
+                          workspace._h if workspace is not None else None)
     out = P()
     _check(lib().rt_trace(tree._h, C.byref(S), C.byref(R), pal, len(al), C.byref(prm), C.byref(out)))
     res = ImageSources(out)
@@ -340,6 +357,57 @@ def rt_rir(image_sources: ImageSources, fs, duration=0.0, stream=None) -> Respon
     out = P()
     _check(lib().rt_rir(image_sources._h, float(fs), float(duration), _stream_ptr(stream), C.byref(out)))
     return Response(out)
+
+
+class Workspace:
+    """rt_workspace: scratch and the bounce-loop CUDA graph reused across traces."""
+
+    def __init__(self):
+        h = P()
+        _check(lib().rt_workspace_create(C.byref(h)))
+        self._h = h
+
+    @property
+    def graph_launches(self) -> int:
+        return int(lib().rt_workspace_graph_launches(self._h))
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().rt_workspace_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.free()
+
+
+def rt_trace_batch(rooms, n_rays, n_bounces, ray_begin=0, ray_count=0, max_distance=0.0, air_beta=None, c=343.2,
+                   block_size=0, max_node_visits=0, tail_rays=0, stream=None, workspace=None) -> ImageSources:
+    """Trace many rooms in one persistent launch.  `rooms` is a list of dicts
+    with keys tree, sources, rcv_center, rcv_radius, rcv_source,
+    band_absorption.  Receivers are numbered room after room."""
+    keep, arr = [], (rt_room * len(rooms))()
+    n_rcv = 0
+    for k, r in enumerate(rooms):
+        src, ps = _host(np.asarray(r["sources"], np.float64).reshape(-1, 3), np.float64)
+        rc, prc = _host(np.asarray(r["rcv_center"], np.float64).reshape(-1, 3), np.float64)
+        rr, prr = _host(np.asarray(r["rcv_radius"], np.float64).reshape(-1), np.float64)
+        rs, prs = _host(np.asarray(r["rcv_source"], np.int32).reshape(-1), np.int32)
+        al, pal = _host(np.asarray(r["band_absorption"], np.float32).reshape(-1, N_BANDS), np.float32)
+        keep += [src, rc, rr, rs, al]
+        arr[k] = rt_room(r["tree"]._h, rt_sources(ps, len(src)), rt_receivers(prc, prr, prs, len(rc)), pal, len(al))
+        n_rcv += len(rc)
+    if air_beta is not None:
+        be, pbe = _host(np.asarray(air_beta, np.float32).reshape(N_BANDS), np.float32)
+    else:
+        be, pbe = None, None
+    prm = rt_trace_params(int(n_rays), int(ray_begin), int(ray_count), int(n_bounces), float(max_distance), pbe,
+                          float(c), int(block_size), int(max_node_visits), int(tail_rays), _stream_ptr(stream),
+                          None, None, None, workspace._h if workspace is not None else None)
+    out = P()
+    _check(lib().rt_trace_batch(arr, len(rooms), C.byref(prm), C.byref(out)))
+    res = ImageSources(out)
+    res.n_rcv = n_rcv
+    return res
 
 
 RT_RIR_STATIC_MAX_SOURCES = 524288

@@ -1,0 +1,84 @@
+"""Batched rooms in one launch, the workspace's CUDA-graph bounce loop, and
+the online autotuner: none of them may change any ray's result."""
+import numpy as np
+import pytest
+
+import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1811_05784_gb300 import rt  # noqa: E402
+
+
+def _tree(sc):
+    return rt.rt_build_tree(sc.vertices, sc.tris, sc.material_id, sc.surface_id)
+
+
+def _is_table(sc_list, isrc, rcv_base):
+    """{(room, local receiver, surface sequence): (count, energy)} from an output."""
+    hist = isrc.hist.cpu().numpy()
+    rep, order, rcv = (x.cpu().numpy() for x in (isrc.rep_ray, isrc.order, isrc.rcv))
+    cnt, en = isrc.count.cpu().numpy(), isrc.energy.cpu().numpy()
+    out = {}
+    for k in range(isrc.n):
+        room = int(np.searchsorted(rcv_base, rcv[k], side="right") - 1)
+        sc = sc_list[room]
+        seq = tuple(int(sc.surface_id[hist[j, rep[k]]]) for j in range(order[k]))
+        out[(room, int(rcv[k] - rcv_base[room]), seq)] = (int(cnt[k]), en[k])
+    return out
+
+
+def test_batch_matches_single_rooms():
+    N, B = 20_000, 20
+    scs = [scenes.shoebox(n_rays=N, n_bounces=B), scenes.lroom(h=0.5, n_rays=N, n_bounces=B),
+           scenes.icosphere(level=2, n_rays=N, n_bounces=B)]
+    trees = [_tree(sc) for sc in scs]
+    rooms = [dict(tree=t, sources=sc.sources, rcv_center=sc.rcv_center, rcv_radius=sc.rcv_radius,
+                  rcv_source=sc.rcv_source, band_absorption=sc.alpha) for t, sc in zip(trees, scs)]
+    batch = rt.rt_trace_batch(rooms, N, B, tail_rays=rt.RT_TAIL_AUTOTUNE)
+    rcv_base = np.cumsum([0] + [len(sc.rcv_center) for sc in scs])
+    hb = batch.hist.cpu().numpy()
+    eb = batch.ray_energy.cpu().numpy()
+    table_b = _is_table(scs, batch, rcv_base)
+    off = 0
+    for r, (sc, t) in enumerate(zip(scs, trees)):
+        single = rt.rt_trace(t, **rt.scene_args(sc))
+        n = single.n_traced
+        assert np.array_equal(hb[:, off:off + n], single.hist.cpu().numpy())
+        assert np.array_equal(eb[off:off + n], single.ray_energy.cpu().numpy())
+        ts = _is_table([sc], single, np.array([0, len(sc.rcv_center)]))
+        for (room0, lr, seq), (c, e) in ts.items():
+            cb, ebx = table_b[(r, lr, seq)]
+            assert cb == c and np.array_equal(ebx, e)
+        assert sum(1 for key in table_b if key[0] == r) == len(ts)
+        off += n
+    assert off == batch.n_traced
+
+
+def test_workspace_graph_replays_give_identical_results():
+    sc = scenes.theatre(n_rays=100_000)
+    tree = _tree(sc)
+    ref = rt.rt_trace(tree, **rt.scene_args(sc))
+    stream = torch.cuda.Stream()
+    ws = rt.Workspace()
+    for k in range(3):
+        got = rt.rt_trace(tree, stream=stream, workspace=ws, **rt.scene_args(sc))
+        torch.cuda.synchronize()
+        assert torch.equal(got.hist, ref.hist) and torch.equal(got.energy, ref.energy)
+        assert got.n == ref.n and got.queries == ref.queries
+    assert ws.graph_launches == 3
+    ws.free()
+
+
+def test_autotuner_candidates_agree():
+    sc = scenes.theatre(n_rays=50_000)
+    tree = _tree(sc)
+    ref = rt.rt_trace(tree, tail_rays=-1, block_size=128, **rt.scene_args(sc))
+    seen = set()
+    for k in range(9):
+        got = rt.rt_trace(tree, tail_rays=rt.RT_TAIL_AUTOTUNE, **rt.scene_args(sc))
+        seen.add((got.block_size, got.tail_rays))
+        assert torch.equal(got.hist, ref.hist) and torch.equal(got.ray_energy, ref.ray_energy)
+        assert torch.equal(got.count, ref.count)
+    assert len(seen) >= 5          # the candidates were tried, then one kept
