@@ -68,6 +68,20 @@ def dist_env():
     return ws, rank, local
 
 
+def shard(rank: int, world: int, n_per_rank: int = N_RAYS):
+    """Weak scaling: rank r traces rays [r n, (r+1) n) of a world x n-ray job."""
+    return dict(ray_begin=rank * n_per_rank, ray_count=n_per_rank), n_per_rank * world
+
+
+def reduce_over_ranks(dist, torch, device, seconds, e2e_seconds, queries, e2e_queries):
+    """Max of the timed regions and sum of the work over ranks (all-reduce)."""
+    t = torch.tensor([seconds, e2e_seconds], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    q = torch.tensor([float(queries), float(e2e_queries)], device=device, dtype=torch.float64)
+    dist.all_reduce(q, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(t[1]), float(q[0]), float(q[1])
+
+
 def workload(world: int):
     sc = scenes.theatre(n_rays=N_RAYS * world, n_bounces=N_BOUNCES)
     return sc
@@ -222,7 +236,8 @@ def run_native(args):
     stream = torch.cuda.Stream()
     sc = workload(ws)
     kw = rt.scene_args(sc)
-    kw.update(ray_begin=rank * N_RAYS, ray_count=N_RAYS)
+    rng_kw, _ = shard(rank, ws)
+    kw.update(rng_kw)
     # resident inputs
     V = torch.as_tensor(sc.vertices, device=dev)
     T = torch.as_tensor(sc.tris, device=dev)
@@ -312,12 +327,8 @@ def run_native(args):
     # max over ranks
     t_max = t_total
     if ws > 1:
-        tt = torch.tensor([t_total, sum(e2e_ms) / 1e3], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        qq = torch.tensor([q_total, e2e_q], device=dev, dtype=torch.float64)
-        dist.all_reduce(qq, op=dist.ReduceOp.SUM)
-        t_max, e2e_t = float(tt[0]), float(tt[1])
-        q_all, e2e_q_all = float(qq[0]), float(qq[1])
+        t_max, e2e_t, q_all, e2e_q_all = reduce_over_ranks(dist, torch, dev, t_total, sum(e2e_ms) / 1e3,
+                                                           q_total, e2e_q)
     else:
         e2e_t, q_all, e2e_q_all = sum(e2e_ms) / 1e3, q_total, e2e_q
     value = q_all / t_max
