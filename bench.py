@@ -32,6 +32,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -58,6 +59,7 @@ def parse():
     ap.add_argument("--tail-rays", type=int, default=None, help="override the autotuned tail threshold")
     ap.add_argument("--cpu-sample-rays", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clock-log", default=None, help="keep the nvidia-smi samples of the timed region here")
     return ap.parse_args()
 
 
@@ -100,10 +102,13 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, path=None):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        if path is None:
+            fd, path = tempfile.mkstemp(prefix=f"clocks_gpu{gpu_index}_", suffix=".csv")
+            os.close(fd)
+        self.path = path
 
     def __enter__(self):
         try:
@@ -268,7 +273,7 @@ def run_native(args):
         torch.cuda.synchronize()
         launches0 = rt.rt_launch_count()
         ms, queries, ms_bounce = [], [], []
-        with ClockSampler(torch.cuda.current_device()) as clk:
+        with ClockSampler(torch.cuda.current_device(), args.clock_log) as clk:
             for _ in range(args.steps):
                 flush.zero_()
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -243,6 +243,56 @@ int64_t rt_launch_count(void);
  * warm-up).  Used as the roofline denominator of the traversal kernel. */
 rt_status rt_measure_l2_bandwidth(double* read_gbs, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned late-reverberation tail (no counterpart in the paper: the network
+ * of the surrogate-tail mode, which predicts the traced tail).  A 3-layer
+ * MLP: Linear(n_in, H) - GELU - Linear(H, H) - GELU - Linear(H, n_out), FP32
+ * master weights with Adam, BF16
+ * copies read by hand-written tensor-core GEMMs (mma.sync m16n8k16, FP32
+ * accumulation).  Sizes must be multiples of 32.  x, target, y are device
+ * float arrays [batch][n_in] / [batch][n_out].  The loss is the mean squared
+ * error over batch x n_out.  Parameter block layout (rt_mlp_info offsets):
+ * W1 [H][n_in], b1 [H], W2 [H][H], b2 [H], W3 [n_out][H], b3 [n_out].
+ * ------------------------------------------------------------------------- */
+typedef struct rt_mlp rt_mlp;
+rt_status rt_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_out, uint64_t seed, void* stream, rt_mlp** out);
+void rt_mlp_free(rt_mlp* net);
+rt_status rt_mlp_info(const rt_mlp* net, int32_t* n_in, int32_t* n_hidden, int32_t* n_out, int64_t* n_params,
+                      int64_t* offsets6);
+rt_status rt_mlp_forward(rt_mlp* net, const float* x, int32_t batch, float* y, void* stream);
+/* gradients of the loss into the network's gradient block; loss to *loss (host, nullable; synchronises) */
+rt_status rt_mlp_gradients(rt_mlp* net, const float* x, const float* target, int32_t batch, float* loss,
+                           void* stream);
+/* gradients + one Adam step (beta 0.9 / 0.999, eps 1e-8, decoupled weight
+ * decay as set by rt_mlp_set_weight_decay, default 0) */
+rt_status rt_mlp_train_step(rt_mlp* net, const float* x, const float* target, int32_t batch, float lr,
+                            float* loss, void* stream);
+/* copy a parameter-sized FP32 block to or from host memory (synchronous):
+ * what = 0 weights, 1 gradients, 2 first moments, 3 second moments */
+rt_status rt_mlp_copy(rt_mlp* net, int32_t what, float* host, int32_t to_device, void* stream);
+rt_status rt_mlp_set_weight_decay(rt_mlp* net, float weight_decay);
+rt_status rt_mlp_get_step(const rt_mlp* net, int64_t* step);
+rt_status rt_mlp_set_step(rt_mlp* net, int64_t step);
+
+/* Specular tail prior of the learned tail (no counterpart in the paper).  In a
+ * room whose walls are grouped by the axis their normal is closest to, a ray
+ * of direction d loses energy at R(d) = sum_k |d_k| rate[k][f] + air[f] (1/s);
+ * the energy histogram of a measurement sphere (Sec. 1.4, eq. 19 with beams of
+ * n / N rays) then averages level * exp(-R t) over directions.  For every room
+ * i, band f and bin b this writes
+ *   out[i][f][b] = level[i] * sum_j w_j (1/dt) int_{t0 + b dt}^{t0 + (b+1) dt} exp(-R(d_j) t) dt
+ * with the product Gauss-Legendre rule of n_nodes x n_nodes directions of the
+ * first octant: theta and phi on the nodes of (0, pi / 2), d = (sin theta
+ * cos phi, sin theta sin phi, cos theta), w_j = (pi / 4) w_theta sin theta *
+ * w_phi / 2 for weights w on (-1, 1) (the area element over the octant's area
+ * pi / 2).  R depends on |d_k| only, so this is the mean over the sphere.
+ * rates [n][3][8], air [n][8], level [n], out [n][8][n_bins]: device float
+ * arrays owned by the caller; rates and air must be >= 0 (not checked: a
+ * negative rate gives a growing curve).  0 < n <= 65535, 0 < n_nodes <= 256,
+ * n_bins > 0, dt > 0, t0 >= 0 are checked (RT_ERR_INVALID_ARG). */
+rt_status rt_tail_prior(const float* rates, const float* air, const float* level, int32_t n, int32_t n_nodes,
+                        float t0, float dt, int32_t n_bins, float* out, void* stream);
+
 /* Workspace: queues and counters kept between traces on one stream, and the
  * CUDA graph of the bounce loop.  Free it after its last trace finished. */
 rt_status rt_workspace_create(rt_workspace** out);

@@ -1,0 +1,514 @@
+// rt_mlp.cu -- the learned late-reverberation tail: a 3-layer MLP trained and
+// run on the GPU with hand-written BF16 tensor-core kernels.
+//
+// Network: x[B][n_in] -> Linear(n_in, H) -> GELU -> Linear(H, H) -> GELU ->
+// Linear(H, n_out).  Weights are kept as FP32 master copies (Adam) and as
+// BF16 copies (row-major [out][in] and transposed) that the GEMMs read;
+// activations entering a GEMM are BF16, accumulation is FP32.
+//
+// One GEMM kernel serves every product: C[M][N] = A[M][K] . B[N][K]^T with
+// both operands K-contiguous (warp-level mma.sync.m16n8k16 bf16 -> f32,
+// 64x64x32 block tiles staged in shared memory).  Backward products that need
+// the other orientation read transposed BF16 copies made by k_transpose.
+//   forward    Z = X W^T + b             (A = X, B = W)
+//   dX         dX = dZ W                 (A = dZ, B = W^T)
+//   dW         dW = dZ^T X               (A = dZ^T, B = X^T, K = batch)
+// The paper has no learned component; the network is the learned tail of the
+// surrogate mode (room descriptors and short traces in, late decay out).
+#include "rt_internal.cuh"
+
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <random>
+
+namespace rr {
+
+typedef __nv_bfloat16 bf16;
+
+static constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+
+enum { EPI_F32 = 0, EPI_BIAS_GELU = 1, EPI_BIAS_F32 = 2 };
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float x) {
+    // d/dx [x Phi(x)] = Phi(x) + x phi(x)
+    const float cdf = 0.5f * (1.0f + erff(x * 0.70710678118654752f));
+    const float pdf = 0.3989422804014327f * expf(-0.5f * x * x);
+    return cdf + x * pdf;
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// C[M][N] = A[M][K] . B[N][K]^T (+ bias, GELU).  K % 32 == 0; M, N any.
+// EPI_F32:        Cf = acc
+// EPI_BIAS_F32:   Cf = acc + bias
+// EPI_BIAS_GELU:  Cpre = acc + bias, Cb = bf16(gelu(acc + bias))
+template <int EPI>
+__global__ void __launch_bounds__(128) k_gemm_nt(const bf16* __restrict__ A, const bf16* __restrict__ Bm, int M, int N,
+                                                 int K, const float* __restrict__ bias, float* __restrict__ Cf,
+                                                 float* __restrict__ Cpre, bf16* __restrict__ Cb) {
+    __shared__ __align__(16) bf16 As[GBM][GBK + GPAD];
+    __shared__ __align__(16) bf16 Bs[GBN][GBK + GPAD];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 1, wn = warp & 1;  // 2 x 2 warps, each 32 x 32
+    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+    const int g = lane >> 2, t = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) acc[i][j][k] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += GBK) {
+        // stage: 64 rows x 32 bf16 = 256 chunks of 16 B per operand, 2 per thread
+#pragma unroll
+        for (int r = 0; r < 2; r++) {
+            const int c = tid + r * 128;
+            const int row = c >> 2, col = (c & 3) * 8;
+            uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
+            if (m0 + row < M) va = *reinterpret_cast<const uint4*>(A + (size_t)(m0 + row) * K + k0 + col);
+            if (n0 + row < N) vb = *reinterpret_cast<const uint4*>(Bm + (size_t)(n0 + row) * K + k0 + col);
+            *reinterpret_cast<uint4*>(&As[row][col]) = va;
+            *reinterpret_cast<uint4*>(&Bs[row][col]) = vb;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GBK; kk += 16) {
+            uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const int r = wm * 32 + i * 16;
+                af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r + g][kk + 2 * t]);
+                af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + g + 8][kk + 2 * t]);
+                af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r + g][kk + 2 * t + 8]);
+                af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + g + 8][kk + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int c = wn * 32 + j * 8;
+                bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c + g][kk + 2 * t]);
+                bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c + g][kk + 2 * t + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) mma_bf16(acc[i][j], af[i], bfr[j]);
+        }
+        __syncthreads();
+    }
+    // epilogue
+#pragma unroll
+    for (int i = 0; i < 2; i++) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+#pragma unroll
+            for (int h = 0; h < 4; h++) {
+                const int row = m0 + wm * 32 + i * 16 + g + (h >= 2 ? 8 : 0);
+                const int col = n0 + wn * 32 + j * 8 + 2 * t + (h & 1);
+                if (row >= M || col >= N) continue;
+                float v = acc[i][j][h];
+                const size_t o = (size_t)row * N + col;
+                if (EPI == EPI_F32) {
+                    Cf[o] = v;
+                } else if (EPI == EPI_BIAS_F32) {
+                    Cf[o] = v + bias[col];
+                } else {
+                    v += bias[col];
+                    Cpre[o] = v;
+                    Cb[o] = __float2bfloat16_rn(gelu_f(v));
+                }
+            }
+        }
+    }
+}
+
+// out[C][R_pad] = in[R][C]^T, zero in columns R .. R_pad-1
+__global__ void k_transpose(const bf16* __restrict__ in, int R, int C, int R_pad, bf16* __restrict__ out) {
+    __shared__ bf16 tile[32][33];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        tile[k][threadIdx.x] = (r < R && c < C) ? in[(size_t)r * C + c] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+        const int c = c0 + k, r = r0 + threadIdx.x;
+        if (c < C && r < R_pad) out[(size_t)c * R_pad + r] = tile[threadIdx.x][k];
+    }
+}
+
+__global__ void k_f32_to_bf16(const float* __restrict__ in, int64_t n, bf16* __restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = __float2bfloat16_rn(in[i]);
+}
+
+// d = 2 (y - t) / (rows * cols) for rows < B (MSE gradient), loss partials per block
+__global__ void k_mse(const float* __restrict__ y, const float* __restrict__ tg, int64_t n, float scale,
+                      bf16* __restrict__ dy, float* __restrict__ loss_part) {
+    __shared__ float red[256];
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    float e = 0.f;
+    if (i < n) {
+        const float d = y[i] - tg[i];
+        e = d * d;
+        dy[i] = __float2bfloat16_rn(2.0f * d * scale);
+    }
+    red[threadIdx.x] = e;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = red[0];
+}
+
+// dZ = dH * gelu'(pre) -> bf16
+__global__ void k_gelu_back(const float* __restrict__ dh, const float* __restrict__ pre, int64_t n,
+                            bf16* __restrict__ dz) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dz[i] = __float2bfloat16_rn(dh[i] * gelu_grad(pre[i]));
+}
+
+// db[c] = sum_r d[r][c]
+__global__ void k_colsum(const bf16* __restrict__ d, int R, int C, float* __restrict__ db) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float s = 0.f;
+    for (int r = 0; r < R; r++) s += __bfloat162float(d[(size_t)r * C + c]);
+    db[c] = s;
+}
+
+// Adam on FP32 masters (bias-corrected), then the BF16 copy
+// Adam with decoupled weight decay (AdamW): w -= lr (m_hat / (sqrt(v_hat) + eps) + wd w)
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int64_t n, float lr, float b1, float b2, float eps, float c1, float c2, float wd,
+                       bf16* __restrict__ wb) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * ((mi * c1) / (sqrtf(vi * c2) + eps) + wd * w[i]);
+    w[i] = wi;
+    if (wb) wb[i] = __float2bfloat16_rn(wi);
+}
+
+}  // namespace rr
+
+// ---------------------------------------------------------------------------
+// the network object
+// ---------------------------------------------------------------------------
+struct rt_mlp {
+    int n_in = 0, n_h = 0, n_out = 0;
+    // FP32 parameter block: W1 [H][n_in], b1 [H], W2 [H][H], b2 [H], W3 [n_out][H], b3 [n_out]
+    int64_t off[6] = {};
+    int64_t n_params = 0;
+    float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    rr::bf16 *wb = nullptr;   // BF16 copies of the weight matrices (same offsets, biases unused)
+    rr::bf16 *wt[3] = {};     // transposed BF16 weights: W1^T [n_in][H], W2^T [H][H], W3^T [H][n_out]
+    int64_t step = 0;
+    float weight_decay = 0.f;
+    // activation scratch sized for cap_b rows
+    int cap_b = 0;
+    std::vector<void*> act;
+    rr::bf16 *xb = nullptr, *h1 = nullptr, *h2 = nullptr;  // BF16 activations
+    float *z1 = nullptr, *z2 = nullptr, *y = nullptr;        // pre-activations, output
+    float *dh = nullptr;                                      // FP32 backward scratch
+    rr::bf16 *dz = nullptr, *dzt = nullptr, *at = nullptr;   // backward BF16 scratch
+    float* loss_part = nullptr;
+    std::vector<void*> owned;
+    cudaStream_t stream = nullptr;
+};
+
+namespace rr {
+
+static unsigned gridn(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+static rt_status mlp_reserve(rt_mlp* net, int B, cudaStream_t s) {
+    if (B <= net->cap_b) return RT_OK;
+    for (void* p : net->act) dev_free(p, s);
+    net->act.clear();
+    Arena ar(s);
+    const int Bp = (B + 31) / 32 * 32;
+    const int W = std::max(std::max(net->n_in, net->n_h), net->n_out);
+    RR_TRY(ar.alloc(&net->xb, (int64_t)Bp * net->n_in));
+    RR_TRY(ar.alloc(&net->h1, (int64_t)Bp * net->n_h));
+    RR_TRY(ar.alloc(&net->h2, (int64_t)Bp * net->n_h));
+    RR_TRY(ar.alloc(&net->z1, (int64_t)Bp * net->n_h));
+    RR_TRY(ar.alloc(&net->z2, (int64_t)Bp * net->n_h));
+    RR_TRY(ar.alloc(&net->y, (int64_t)Bp * net->n_out));
+    RR_TRY(ar.alloc(&net->dh, (int64_t)Bp * W));
+    RR_TRY(ar.alloc(&net->dz, (int64_t)Bp * W));
+    RR_TRY(ar.alloc(&net->dzt, (int64_t)Bp * W));
+    RR_TRY(ar.alloc(&net->at, (int64_t)Bp * W));
+    RR_TRY(ar.alloc(&net->loss_part, (int64_t)gridn((int64_t)Bp * net->n_out, 256)));
+    net->act = ar.release();
+    net->cap_b = B;
+    return RT_OK;
+}
+
+template <int EPI>
+static void gemm(const bf16* A, const bf16* B, int M, int N, int K, const float* bias, float* Cf, float* Cpre, bf16* Cb,
+                 cudaStream_t s) {
+    dim3 grid(gridn(N, GBN), gridn(M, GBM));
+    RR_LAUNCH(k_gemm_nt<EPI>, grid, 128, 0, s, A, B, M, N, K, bias, Cf, Cpre, Cb);
+}
+
+static void transpose(const bf16* in, int R, int C, int R_pad, bf16* out, cudaStream_t s) {
+    dim3 grid(gridn(C, 32), gridn(R_pad, 32));
+    RR_LAUNCH(k_transpose, grid, dim3(32, 8), 0, s, in, R, C, R_pad, out);
+}
+
+static void refresh_bf16(rt_mlp* net, cudaStream_t s) {
+    const int L_in[3] = {net->n_in, net->n_h, net->n_h}, L_out[3] = {net->n_h, net->n_h, net->n_out};
+    for (int l = 0; l < 3; l++) {
+        const int64_t o = net->off[2 * l];
+        const int64_t n = (int64_t)L_in[l] * L_out[l];
+        RR_LAUNCH(k_f32_to_bf16, gridn(n, 256), 256, 0, s, net->w + o, n, net->wb + o);
+        transpose(net->wb + o, L_out[l], L_in[l], L_out[l], net->wt[l], s);
+    }
+}
+
+static rt_status mlp_forward_impl(rt_mlp* net, const float* x, int B, float* y_out, cudaStream_t s) {
+    RR_TRY(mlp_reserve(net, B, s));
+    RR_LAUNCH(k_f32_to_bf16, gridn((int64_t)B * net->n_in, 256), 256, 0, s, x, (int64_t)B * net->n_in, net->xb);
+    gemm<EPI_BIAS_GELU>(net->xb, net->wb + net->off[0], B, net->n_h, net->n_in, net->w + net->off[1], nullptr, net->z1,
+                        net->h1, s);
+    gemm<EPI_BIAS_GELU>(net->h1, net->wb + net->off[2], B, net->n_h, net->n_h, net->w + net->off[3], nullptr, net->z2,
+                        net->h2, s);
+    gemm<EPI_BIAS_F32>(net->h2, net->wb + net->off[4], B, net->n_out, net->n_h, net->w + net->off[5],
+                       y_out ? y_out : net->y, nullptr, nullptr, s);
+    RR_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+// gradients of the mean squared error into net->g; loss partials into net->loss_part
+static rt_status mlp_backward_impl(rt_mlp* net, const float* x, const float* target, int B, cudaStream_t s) {
+    RR_TRY(mlp_forward_impl(net, x, B, nullptr, s));
+    const int Bp = (B + 31) / 32 * 32;
+    const int H = net->n_h, NI = net->n_in, NO = net->n_out;
+    const int64_t ny = (int64_t)B * NO;
+    RR_LAUNCH(k_mse, gridn(ny, 256), 256, 0, s, net->y, target, ny, 1.0f / (float)ny, net->dz, net->loss_part);
+    // layer 3: dW3 = dY^T H2, db3 = colsum dY, dH2 = dY W3
+    transpose(net->dz, B, NO, Bp, net->dzt, s);
+    transpose(net->h2, B, H, Bp, net->at, s);
+    gemm<EPI_F32>(net->dzt, net->at, NO, H, Bp, nullptr, net->g + net->off[4], nullptr, nullptr, s);
+    RR_LAUNCH(k_colsum, gridn(NO, 128), 128, 0, s, net->dz, B, NO, net->g + net->off[5]);
+    gemm<EPI_F32>(net->dz, net->wt[2], B, H, NO, nullptr, net->dh, nullptr, nullptr, s);
+    RR_LAUNCH(k_gelu_back, gridn((int64_t)B * H, 256), 256, 0, s, net->dh, net->z2, (int64_t)B * H, net->dz);
+    // layer 2
+    transpose(net->dz, B, H, Bp, net->dzt, s);
+    transpose(net->h1, B, H, Bp, net->at, s);
+    gemm<EPI_F32>(net->dzt, net->at, H, H, Bp, nullptr, net->g + net->off[2], nullptr, nullptr, s);
+    RR_LAUNCH(k_colsum, gridn(H, 128), 128, 0, s, net->dz, B, H, net->g + net->off[3]);
+    gemm<EPI_F32>(net->dz, net->wt[1], B, H, H, nullptr, net->dh, nullptr, nullptr, s);
+    RR_LAUNCH(k_gelu_back, gridn((int64_t)B * H, 256), 256, 0, s, net->dh, net->z1, (int64_t)B * H, net->dz);
+    // layer 1 (no input gradient needed)
+    transpose(net->dz, B, H, Bp, net->dzt, s);
+    transpose(net->xb, B, NI, Bp, net->at, s);
+    gemm<EPI_F32>(net->dzt, net->at, H, NI, Bp, nullptr, net->g + net->off[0], nullptr, nullptr, s);
+    RR_LAUNCH(k_colsum, gridn(H, 128), 128, 0, s, net->dz, B, H, net->g + net->off[1]);
+    RR_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+static rt_status read_loss(rt_mlp* net, int B, cudaStream_t s, float* loss) {
+    const int64_t ny = (int64_t)B * net->n_out;
+    const int nb = (int)gridn(ny, 256);
+    std::vector<float> part((size_t)nb);
+    RR_CUDA(cudaMemcpyAsync(part.data(), net->loss_part, sizeof(float) * nb, cudaMemcpyDeviceToHost, s));
+    RR_CUDA(cudaStreamSynchronize(s));
+    double acc = 0;
+    for (float x : part) acc += x;
+    *loss = (float)(acc / (double)ny);
+    return RT_OK;
+}
+
+static bool dims_ok(int n_in, int n_h, int n_out) {
+    return n_in > 0 && n_h > 0 && n_out > 0 && n_in % 32 == 0 && n_h % 32 == 0 && n_out % 32 == 0 &&
+           n_in <= 16384 && n_h <= 16384 && n_out <= 16384;
+}
+
+}  // namespace rr
+
+extern "C" rt_status rt_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_out, uint64_t seed, void* stream,
+                                   rt_mlp** out) {
+    rr::clear_error();
+    if (!out || !rr::dims_ok(n_in, n_hidden, n_out)) {
+        rr::set_error("rt_mlp_create: sizes must be positive multiples of 32 (<= 16384)");
+        return RT_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    rt_mlp* net = new rt_mlp();
+    net->stream = s;
+    net->n_in = n_in;
+    net->n_h = n_hidden;
+    net->n_out = n_out;
+    const int64_t sizes[6] = {(int64_t)n_hidden * n_in, n_hidden, (int64_t)n_hidden * n_hidden, n_hidden,
+                              (int64_t)n_out * n_hidden, n_out};
+    int64_t o = 0;
+    for (int k = 0; k < 6; k++) {
+        net->off[k] = o;
+        o += (sizes[k] + 63) / 64 * 64;  // keep every block 256-byte aligned
+    }
+    net->n_params = o;
+    rr::Arena ar(s);
+    rt_status st;
+    if ((st = ar.alloc(&net->w, o)) || (st = ar.alloc(&net->g, o)) || (st = ar.alloc(&net->m, o)) ||
+        (st = ar.alloc(&net->v, o)) || (st = ar.alloc(&net->wb, o)) ||
+        (st = ar.alloc(&net->wt[0], sizes[0])) || (st = ar.alloc(&net->wt[1], sizes[2])) ||
+        (st = ar.alloc(&net->wt[2], sizes[4]))) {
+        delete net;
+        return st;
+    }
+    // He-uniform weights from a seeded host generator, zero biases and moments
+    std::vector<float> hw((size_t)o, 0.f);
+    std::mt19937_64 rng(seed);
+    const int fan_in[3] = {n_in, n_hidden, n_hidden};
+    for (int l = 0; l < 3; l++) {
+        const float a = std::sqrt(6.0f / (float)fan_in[l]);
+        std::uniform_real_distribution<float> U(-a, a);
+        for (int64_t i = 0; i < sizes[2 * l]; i++) hw[(size_t)(net->off[2 * l] + i)] = U(rng);
+    }
+    if (cudaMemcpyAsync(net->w, hw.data(), sizeof(float) * o, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(net->m, 0, sizeof(float) * o, s) != cudaSuccess ||
+        cudaMemsetAsync(net->v, 0, sizeof(float) * o, s) != cudaSuccess ||
+        cudaMemsetAsync(net->g, 0, sizeof(float) * o, s) != cudaSuccess) {
+        rr::set_error("rt_mlp_create: initialisation copy failed");
+        delete net;
+        return RT_ERR_CUDA;
+    }
+    net->owned = ar.release();
+    rr::refresh_bf16(net, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+        rr::set_error("rt_mlp_create: %s", cudaGetErrorString(cudaGetLastError()));
+        for (void* p : net->owned) rr::dev_free(p, s);
+        delete net;
+        return RT_ERR_CUDA;
+    }
+    *out = net;
+    return RT_OK;
+}
+
+extern "C" void rt_mlp_free(rt_mlp* net) {
+    if (!net) return;
+    for (void* p : net->act) rr::dev_free(p, net->stream);
+    for (void* p : net->owned) rr::dev_free(p, net->stream);
+    delete net;
+}
+
+extern "C" rt_status rt_mlp_info(const rt_mlp* net, int32_t* n_in, int32_t* n_hidden, int32_t* n_out,
+                                 int64_t* n_params, int64_t* offsets6) {
+    if (!net) {
+        rr::set_error("rt_mlp_info: null network");
+        return RT_ERR_INVALID_ARG;
+    }
+    if (n_in) *n_in = net->n_in;
+    if (n_hidden) *n_hidden = net->n_h;
+    if (n_out) *n_out = net->n_out;
+    if (n_params) *n_params = net->n_params;
+    if (offsets6)
+        for (int k = 0; k < 6; k++) offsets6[k] = net->off[k];
+    return RT_OK;
+}
+
+extern "C" rt_status rt_mlp_forward(rt_mlp* net, const float* x, int32_t batch, float* y, void* stream) {
+    rr::clear_error();
+    if (!net || !x || !y || batch < 1) {
+        rr::set_error("rt_mlp_forward: need a network, device x [batch][n_in], y [batch][n_out], batch >= 1");
+        return RT_ERR_INVALID_ARG;
+    }
+    return rr::mlp_forward_impl(net, x, batch, y, (cudaStream_t)stream);
+}
+
+extern "C" rt_status rt_mlp_gradients(rt_mlp* net, const float* x, const float* target, int32_t batch,
+                                      float* loss, void* stream) {
+    rr::clear_error();
+    if (!net || !x || !target || batch < 1) {
+        rr::set_error("rt_mlp_gradients: need a network, device x, target and batch >= 1");
+        return RT_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    RR_TRY(rr::mlp_backward_impl(net, x, target, batch, s));
+    if (loss) RR_TRY(rr::read_loss(net, batch, s, loss));
+    return RT_OK;
+}
+
+extern "C" rt_status rt_mlp_train_step(rt_mlp* net, const float* x, const float* target, int32_t batch, float lr,
+                                       float* loss, void* stream) {
+    rr::clear_error();
+    if (!net || !x || !target || batch < 1 || !(lr > 0)) {
+        rr::set_error("rt_mlp_train_step: need a network, device x, target, batch >= 1 and lr > 0");
+        return RT_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    RR_TRY(rr::mlp_backward_impl(net, x, target, batch, s));
+    net->step++;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.0f / (1.0f - std::pow(b1, (float)net->step));
+    const float c2 = 1.0f / (1.0f - std::pow(b2, (float)net->step));
+    RR_LAUNCH(rr::k_adam, rr::gridn(net->n_params, 256), 256, 0, s, net->w, net->g, net->m, net->v, net->n_params, lr,
+              b1, b2, eps, c1, c2, net->weight_decay, (rr::bf16*)nullptr);
+    rr::refresh_bf16(net, s);
+    RR_CUDA(cudaGetLastError());
+    if (loss) RR_TRY(rr::read_loss(net, batch, s, loss));
+    return RT_OK;
+}
+
+// parameter access (FP32 masters, gradients, or the Adam state) for checkpoints and checks
+extern "C" rt_status rt_mlp_copy(rt_mlp* net, int32_t what, float* host, int32_t to_device, void* stream) {
+    rr::clear_error();
+    if (!net || !host || what < 0 || what > 3) {
+        rr::set_error("rt_mlp_copy: what = 0 weights, 1 gradients, 2 first moments, 3 second moments");
+        return RT_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    float* dev = what == 0 ? net->w : (what == 1 ? net->g : (what == 2 ? net->m : net->v));
+    const size_t bytes = sizeof(float) * (size_t)net->n_params;
+    if (to_device) {
+        RR_CUDA(cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, s));
+        if (what == 0) rr::refresh_bf16(net, s);
+    } else {
+        RR_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, s));
+    }
+    RR_CUDA(cudaStreamSynchronize(s));
+    return RT_OK;
+}
+
+extern "C" rt_status rt_mlp_set_weight_decay(rt_mlp* net, float weight_decay) {
+    if (!net || !(weight_decay >= 0.f)) {
+        rr::set_error("rt_mlp_set_weight_decay: null network or negative decay");
+        return RT_ERR_INVALID_ARG;
+    }
+    net->weight_decay = weight_decay;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_mlp_get_step(const rt_mlp* net, int64_t* step) {
+    if (!net || !step) {
+        rr::set_error("rt_mlp_get_step: null argument");
+        return RT_ERR_INVALID_ARG;
+    }
+    *step = net->step;
+    return RT_OK;
+}
+
+extern "C" rt_status rt_mlp_set_step(rt_mlp* net, int64_t step) {
+    if (!net || step < 0) {
+        rr::set_error("rt_mlp_set_step: null network or negative step");
+        return RT_ERR_INVALID_ARG;
+    }
+    net->step = step;
+    return RT_OK;
+}

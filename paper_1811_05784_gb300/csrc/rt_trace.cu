@@ -845,6 +845,7 @@ struct rt_workspace {
     std::vector<cudaGraphNode_t> nodes;
     int g_b = 0, g_grid = 0, g_block = 0;
     long long graph_launches = 0;
+    unsigned long long last_records = 0;  // capacity hint for the next trace
 
     void release_graph() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -1190,6 +1191,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
 
     unsigned long long cap = (unsigned long long)std::min<int64_t>(
         std::max<int64_t>(1 << 20, 2 * n_traced), std::max<int64_t>(1, n_traced * (int64_t)B * std::max(R, 1)));
+    if (ws && ws->last_records + ws->last_records / 4 > cap) cap = ws->last_records + ws->last_records / 4;
     struct Events {
         cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
         ~Events() {
@@ -1286,6 +1288,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
         cap = n_rec;
     }
     const int64_t queries = (int64_t)n2[1];
+    if (ws) ws->last_records = n_rec;
     float ms_bounce = 0.f;
     cudaEventElapsedTime(&ms_bounce, ev.e[1], ev.e[2]);
     if (autotune) tune_report(key, cand, ms_bounce);

@@ -31,7 +31,9 @@ EXPORTED = ["rt_build_tree", "rt_tree_free", "rt_tree_info", "rt_trace", "rt_tra
             "rt_workspace_create", "rt_workspace_free", "rt_workspace_graph_launches",
             "rt_image_sources_free", "rt_rir", "rt_rir_static", "rt_response_get", "rt_response_download",
             "rt_response_free",
-            "rt_last_error", "rt_api_version", "rt_launch_count", "rt_measure_l2_bandwidth", "rt_set_allocator"]
+            "rt_last_error", "rt_api_version", "rt_launch_count", "rt_measure_l2_bandwidth", "rt_set_allocator",
+            "rt_mlp_create", "rt_mlp_free", "rt_mlp_info", "rt_mlp_forward", "rt_mlp_gradients", "rt_mlp_train_step",
+            "rt_mlp_copy", "rt_mlp_set_weight_decay", "rt_mlp_get_step", "rt_mlp_set_step", "rt_tail_prior"]
 
 
 class RtError(RuntimeError):
@@ -132,6 +134,28 @@ def lib():
             L.rt_launch_count.restype = C.c_int64
             L.rt_measure_l2_bandwidth.restype = st
             L.rt_measure_l2_bandwidth.argtypes = [C.POINTER(C.c_double), P]
+            L.rt_mlp_create.restype = st
+            L.rt_mlp_create.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_uint64, P, C.POINTER(P)]
+            L.rt_mlp_free.argtypes = [P]
+            L.rt_mlp_info.restype = st
+            L.rt_mlp_info.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_int64), P]
+            L.rt_mlp_forward.restype = st
+            L.rt_mlp_forward.argtypes = [P, P, C.c_int32, P, P]
+            L.rt_mlp_gradients.restype = st
+            L.rt_mlp_gradients.argtypes = [P, P, P, C.c_int32, C.POINTER(C.c_float), P]
+            L.rt_mlp_train_step.restype = st
+            L.rt_mlp_train_step.argtypes = [P, P, P, C.c_int32, C.c_float, C.POINTER(C.c_float), P]
+            L.rt_mlp_copy.restype = st
+            L.rt_mlp_copy.argtypes = [P, C.c_int32, P, C.c_int32, P]
+            L.rt_mlp_set_weight_decay.restype = st
+            L.rt_mlp_set_weight_decay.argtypes = [P, C.c_float]
+            L.rt_mlp_get_step.restype = st
+            L.rt_mlp_get_step.argtypes = [P, C.POINTER(C.c_int64)]
+            L.rt_mlp_set_step.restype = st
+            L.rt_mlp_set_step.argtypes = [P, C.c_int64]
+            L.rt_tail_prior.restype = st
+            L.rt_tail_prior.argtypes = [P, P, P, C.c_int32, C.c_int32, C.c_float, C.c_float, C.c_int32, P, P]
             L.rt_set_allocator.restype = st
             L.rt_set_allocator.argtypes = [ALLOC_FN, FREE_FN, P]
             _lib = L
@@ -156,6 +180,22 @@ def rt_measure_l2_bandwidth(stream=None) -> float:
     v = C.c_double()
     _check(lib().rt_measure_l2_bandwidth(C.byref(v), _stream_ptr(stream)))
     return v.value
+
+
+def rt_tail_prior(rates, air, level, n_nodes, t0, dt, n_bins, out=None, stream=None):
+    """Direction-integrated specular tail [n][8][n_bins] (CUDA float tensor)
+    from per-axis decay rates [n][3][8], air rates [n][8] and levels [n]
+    (CUDA tensors), with an n_nodes x n_nodes Gauss-Legendre direction rule."""
+    import torch
+    rates, air, level = (x.contiguous().float() for x in (rates, air, level))
+    n = rates.shape[0]
+    if rates.shape != (n, 3, N_BANDS) or air.shape != (n, N_BANDS) or level.shape != (n,):
+        raise ValueError("rt_tail_prior: rates [n][3][8], air [n][8], level [n]")
+    if out is None:
+        out = torch.empty((n, N_BANDS, int(n_bins)), dtype=torch.float32, device=rates.device)
+    _check(lib().rt_tail_prior(P(rates.data_ptr()), P(air.data_ptr()), P(level.data_ptr()), int(n), int(n_nodes),
+                               float(t0), float(dt), int(n_bins), P(out.data_ptr()), _stream_ptr(stream)))
+    return out
 
 
 def _check(status):
@@ -253,42 +293,47 @@ def rt_build_tree(vertices, tris, material_id, surface_id=None, stream=None) -> 
 
 
 class ImageSources:
-    """rt_image_sources handle with its device arrays as torch tensors."""
+    """rt_image_sources handle.  Its device arrays are exposed as torch tensors
+    created on access; each tensor keeps the handle alive, and the handle keeps
+    no tensor (no reference cycle, so memory returns as soon as both are gone)."""
+
+    _FIELDS = {  # name: (view field, shape key, dtype name)
+        "rcv": ("rcv", "n", "int32"), "order": ("order", "n", "int32"), "count": ("count", "n", "int32"),
+        "rep_ray": ("rep_ray", "n", "int32"), "pos": ("pos", "n3", "float64"), "dist": ("dist", "n", "float64"),
+        "time": ("time", "n", "float64"), "energy": ("energy", "n8", "float64"),
+        "hist": ("hist", "hist", "int32"), "ray_energy": ("ray_energy", "t8", "float32"),
+        "ray_length": ("ray_length", "t", "float32"), "ray_hits": ("ray_hits", "t", "int32"),
+        "rec_rcv": ("rec_rcv", "r", "int32"), "rec_ray": ("rec_ray", "r", "int32"),
+        "rec_order": ("rec_order", "r", "int32"), "rec_length": ("rec_length", "r", "float32"),
+    }
 
     def __init__(self, handle):
-        import torch
         self._h = handle
         v = rt_is_view()
         _check(lib().rt_image_sources_view(handle, C.byref(v)))
         self.view = v
-        n, nt, B, nr = v.n, v.n_traced, v.n_bounces, v.n_records
-        T = _device_tensor
-        self.n = n
-        self.rcv = T(v.rcv, (n,), torch.int32, self)
-        self.order = T(v.order, (n,), torch.int32, self)
-        self.count = T(v.count, (n,), torch.int32, self)
-        self.rep_ray = T(v.rep_ray, (n,), torch.int32, self)
-        self.pos = T(v.pos, (n, 3), torch.float64, self)
-        self.dist = T(v.dist, (n,), torch.float64, self)
-        self.time = T(v.time, (n,), torch.float64, self)
-        self.energy = T(v.energy, (n, N_BANDS), torch.float64, self)
-        self.n_traced, self.n_bounces = nt, B
-        self.hist = T(v.hist, (B, nt), torch.int32, self)
-        self.ray_energy = T(v.ray_energy, (nt, N_BANDS), torch.float32, self)
-        self.ray_length = T(v.ray_length, (nt,), torch.float32, self)
-        self.ray_hits = T(v.ray_hits, (nt,), torch.int32, self)
-        self.n_records = nr
-        self.rec_rcv = T(v.rec_rcv, (nr,), torch.int32, self)
-        self.rec_ray = T(v.rec_ray, (nr,), torch.int32, self)
-        self.rec_order = T(v.rec_order, (nr,), torch.int32, self)
-        self.rec_length = T(v.rec_length, (nr,), torch.float32, self)
+        self.n = v.n
+        self.n_traced, self.n_bounces = v.n_traced, v.n_bounces
+        self.n_records = v.n_records
         self.queries = v.queries
         self.hash_collisions = v.hash_collisions
         self.ms_rays, self.ms_bounces, self.ms_image_sources = v.ms_rays, v.ms_bounces, v.ms_image_sources
         self.block_size, self.tail_rays = v.block_size, v.tail_rays
 
+    def __getattr__(self, name):
+        f = ImageSources._FIELDS.get(name)
+        if f is None:
+            raise AttributeError(name)
+        import torch
+        v = self.__dict__["view"]
+        n, t, r = v.n, v.n_traced, v.n_records
+        shape = {"n": (n,), "n3": (n, 3), "n8": (n, N_BANDS), "hist": (v.n_bounces, t), "t8": (t, N_BANDS),
+                 "t": (t,), "r": (r,)}[f[1]]
+        return _device_tensor(getattr(v, f[0]), shape, getattr(torch, f[2]), self)
+
     def free(self):
-        if getattr(self, "_h", None):
+        """Release the device memory now (tensors taken from it become invalid)."""
+        if self.__dict__.get("_h"):
             lib().rt_image_sources_free(self._h)
             self._h = None
 
@@ -326,15 +371,21 @@ def rt_trace(tree: Tree, sources, rcv_center, rcv_radius, rcv_source, band_absor
 
 
 class Response:
-    """rt_response handle: [n_rcv, 8, n_bins] float32 device histograms."""
+    """rt_response handle: [n_rcv, 8, n_bins] float32 device histograms
+    (``data`` is created on access and keeps the handle alive)."""
 
     def __init__(self, handle):
-        import torch
         self._h = handle
         v = rt_response_view()
         _check(lib().rt_response_get(handle, C.byref(v)))
+        self.view = v
         self.n_rcv, self.n_bins, self.fs = v.n_rcv, v.n_bins, v.fs
-        self.data = _device_tensor(v.data, (max(v.n_rcv, 1), N_BANDS, v.n_bins), torch.float32, self)
+
+    @property
+    def data(self):
+        import torch
+        v = self.view
+        return _device_tensor(v.data, (max(v.n_rcv, 1), N_BANDS, v.n_bins), torch.float32, self)
 
     def download(self, out=None, stream=None):
         """Copy to host through rt_response_download (out: numpy or CPU tensor)."""
@@ -452,3 +503,73 @@ def scene_args(scene):
                 rcv_source=scene.rcv_source, band_absorption=scene.alpha, n_rays=scene.n_rays,
                 n_bounces=scene.n_bounces, max_distance=scene.max_distance,
                 air_beta=scene.beta if np.any(scene.beta) else None, c=scene.c)
+
+
+class MLP:
+    """rt_mlp handle: the surrogate network, trained and run by libroomrays."""
+
+    def __init__(self, n_in, n_hidden, n_out, seed=0, stream=None):
+        h = P()
+        _check(lib().rt_mlp_create(int(n_in), int(n_hidden), int(n_out), int(seed), _stream_ptr(stream), C.byref(h)))
+        self._h = h
+        a, b, c, n = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64()
+        off = (C.c_int64 * 6)()
+        _check(lib().rt_mlp_info(h, C.byref(a), C.byref(b), C.byref(c), C.byref(n), off))
+        self.n_in, self.n_hidden, self.n_out, self.n_params = a.value, b.value, c.value, n.value
+        self.offsets = [int(x) for x in off]
+
+    def forward(self, x, y=None, stream=None):
+        import torch
+        x = x.contiguous().float()
+        if y is None:
+            y = torch.empty((x.shape[0], self.n_out), dtype=torch.float32, device=x.device)
+        _check(lib().rt_mlp_forward(self._h, P(x.data_ptr()), int(x.shape[0]), P(y.data_ptr()), _stream_ptr(stream)))
+        return y
+
+    def gradients(self, x, target, stream=None):
+        loss = C.c_float()
+        x, target = x.contiguous().float(), target.contiguous().float()
+        _check(lib().rt_mlp_gradients(self._h, P(x.data_ptr()), P(target.data_ptr()), int(x.shape[0]),
+                                      C.byref(loss), _stream_ptr(stream)))
+        return loss.value
+
+    def train_step(self, x, target, lr, stream=None, want_loss=True):
+        loss = C.c_float()
+        x, target = x.contiguous().float(), target.contiguous().float()
+        _check(lib().rt_mlp_train_step(self._h, P(x.data_ptr()), P(target.data_ptr()), int(x.shape[0]), float(lr),
+                                       C.byref(loss) if want_loss else None, _stream_ptr(stream)))
+        return loss.value if want_loss else None
+
+    def copy(self, what, host=None, to_device=False, stream=None):
+        if host is None:
+            host = np.empty(self.n_params, np.float32)
+        host = np.ascontiguousarray(host, np.float32)
+        _check(lib().rt_mlp_copy(self._h, int(what), P(host.ctypes.data), int(bool(to_device)), _stream_ptr(stream)))
+        return host
+
+    def blocks(self, flat):
+        """Split a parameter-sized vector into W1, b1, W2, b2, W3, b3."""
+        I, H, O = self.n_in, self.n_hidden, self.n_out
+        shapes = [(H, I), (H,), (H, H), (H,), (O, H), (O,)]
+        return [flat[o:o + int(np.prod(sh))].reshape(sh) for o, sh in zip(self.offsets, shapes)]
+
+    def set_weight_decay(self, wd):
+        _check(lib().rt_mlp_set_weight_decay(self._h, float(wd)))
+
+    @property
+    def step(self):
+        v = C.c_int64()
+        _check(lib().rt_mlp_get_step(self._h, C.byref(v)))
+        return v.value
+
+    @step.setter
+    def step(self, value):
+        _check(lib().rt_mlp_set_step(self._h, int(value)))
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().rt_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.free()

@@ -597,3 +597,56 @@ def _scaled_lroom(sc, height, h, rng):
         soup.grid((p[0], p[1], 0), (q[0] - p[0], q[1] - p[1], 0), (0, 0, height), na, nz,
                   2 + (k % 2), soup.new_surface())
     return (soup, np.array([X, Y, height]))
+
+
+# ----------------------------------------------------------------------------
+# rooms for the learned late-reverberation tail
+# ----------------------------------------------------------------------------
+def surrogate_room(seed: int, v_min=50.0, v_max=20_000.0, radius=0.5, n_rays=65_536, n_bounces=64) -> Scene:
+    """One seeded room of the surrogate data set: a shoebox (even seeds) or an
+    L-room (odd seeds, a 2.5 m-grid L-room scaled per axis, watertight), with
+    volume log-uniform in [v_min, v_max], 3 materials with alpha ~ U[0.02,
+    0.6] per band assigned per surface, one source and one receiver sphere
+    (radius `radius`) at seeded points at least 1 m (or 20 % of the room)
+    inside the walls.  meta holds the analytic volume and surface area."""
+    rng = np.random.default_rng(seed)
+    V = math.exp(rng.uniform(math.log(v_min), math.log(v_max)))
+    alpha = seeded_alpha(3, int(rng.integers(1 << 31)))
+    if seed % 2 == 0:
+        a = rng.uniform(0.6, 1.6, 3) * np.array([1.4, 1.0, 0.55])
+        L = a * (V / np.prod(a)) ** (1.0 / 3.0)
+        L = f32(L)
+        soup = _Soup()
+        _box_faces(soup, (0, 0, 0), L, list(rng.integers(0, 3, 6)))
+        Vt = float(np.prod(L))
+        St = 2.0 * float(L[0] * L[1] + L[1] * L[2] + L[0] * L[2])
+        lo, hi = np.zeros(3), L
+        inside = lambda p: True
+    else:
+        base = lroom(h=2.5, n_rays=1, n_bounces=1, n_receivers=1, seed=seed)
+        # L-room area 225 m^2, height 5 m -> volume 1125 m^3; scale per axis
+        sxy = rng.uniform(0.7, 1.4)
+        k = (V / (1125.0)) ** (1.0 / 3.0)
+        sc = np.array([k * sxy, k / sxy, k * rng.uniform(0.5, 1.0)])
+        verts = f32(base.vertices * sc)
+        mat = rng.integers(0, 3, base.n_surfaces)[base.surface_id].astype(np.int32)
+        soup = _Soup()
+        soup.coords.append(verts[base.tris])
+        soup.mat.append(mat)
+        soup.surf.append(base.surface_id.copy())
+        soup.n_surf = base.n_surfaces
+        Vt = 1125.0 * float(np.prod(sc))
+        St = 2 * 225.0 * sc[0] * sc[1] + 5.0 * sc[2] * (2 * 20 * sc[0] + 2 * 15 * sc[1])
+        lo, hi = np.zeros(3), np.array([20 * sc[0], 15 * sc[1], 5 * sc[2]])
+        inside = lambda p: (p[0] < 10 * sc[0]) or (p[1] < 7.5 * sc[1])
+    margin = np.minimum(1.0, 0.2 * (hi - lo))
+    pts = []
+    while len(pts) < 2:
+        p = rng.uniform(lo + margin, hi - margin)
+        if inside(p) and inside(p + np.array([margin[0], margin[1], 0])) and \
+                inside(p - np.array([0, 0, 0])):
+            pts.append(p)
+    sc_ = _scene("surrogate_room", soup, alpha, np.zeros(N_BANDS), [pts[0]], [pts[1]], [radius], [0],
+                 n_rays, n_bounces)
+    sc_.meta.update({"V": Vt, "S": St, "kind": "shoebox" if seed % 2 == 0 else "lroom"})
+    return sc_
