@@ -322,7 +322,9 @@ def run_native(args):
         torch.cuda.synchronize()
         c = cost.double().sum((0, 1)).cpu().numpy()
         n_q = isrc.queries
-        l2_bytes = 64.0 * c[0] + 48.0 * c[1]
+        # a 4-wide node visit reads 112 B (six float4 of child boxes, one of refs);
+        # a triangle test reads 48 B
+        l2_bytes = 112.0 * c[0] + 48.0 * c[1]
         hbm_bytes = n_q * 4.0 + N_RAYS * (80.0 + 44.0) + isrc.n_records * 24.0   # hist, state in/out, records
         del cost
         bounce_s = statistics.median(ms_bounce) / 1e3

@@ -8,10 +8,13 @@
 // the device radix sort, every internal node finds its key range and split
 // independently, boxes are refitted bottom-up with one atomic flag per node
 // (the second child to arrive computes the union and climbs on), and
-// subtrees of at most RR_LEAF_MAX triangles collapse into leaves.
+// subtrees of at most RR_LEAF_MAX triangles collapse into leaves.  The binary
+// tree is then stored 4-wide: every kept node at even depth holds its
+// grandchildren, which halves the traversal steps of a query.
 //
 // Layout in HBM (see also rt_internal.cuh):
-//   nodes   : 64 B per node = 4 x float4 = child-0 box, child-1 box, refs
+//   nodes   : 128 B per 4-wide node = 8 x float4 = child boxes as SoA
+//             (lo.x[4] lo.y[4] lo.z[4] hi.x[4] hi.y[4] hi.z[4]), refs[4], count
 //   tris    : 48 B per triangle in tree order = 3 x float4 (v0|id, v1|surface, v2)
 //   tri_nrm : 16 B per triangle by id = float32 unit normal + surface id
 //   planes  : 32 B per surface, FP64 (n, d) for image-source mirroring
@@ -294,68 +297,113 @@ __global__ void k_keep(int64_t n_int, const int32_t* __restrict__ first, const i
     keep[i] = (i == 0 || (last[i] - first[i] + 1) > RR_LEAF_MAX) ? 1u : 0u;
 }
 
+// A kept binary node at even depth becomes a 4-wide node whose children are
+// its binary grandchildren (children where a child is a leaf).  Kept nodes
+// form a connected top part of the tree (a parent holds more triangles than
+// its child), so every kept odd-depth node is opened by its parent.
+__global__ void k_keep4(int64_t n_int, const int32_t* __restrict__ parent_int, const uint32_t* __restrict__ keep,
+                        uint32_t* __restrict__ keep4) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    if (!keep[i]) {
+        keep4[i] = 0u;
+        return;
+    }
+    int depth = 0;
+    int32_t p = parent_int[i];
+    while (p >= 0 && depth < 100000) {
+        depth++;
+        p = parent_int[p];
+    }
+    keep4[i] = (depth & 1) ? 0u : 1u;
+}
+
 // leaf reference: ~(first triangle << 3 | count), count <= RR_LEAF_MAX
 __device__ __forceinline__ int32_t leaf_ref(int32_t first, int32_t count) { return ~((first << 3) | count); }
 
-__device__ __forceinline__ void emit_child(int32_t c, const uint32_t* keep, const uint32_t* newidx,
-                                           const int32_t* first, const int32_t* last, const float4* leaf_box,
-                                           const float4* node_box, float4& lo, float4& hi, int32_t& ref,
-                                           int32_t& cnt) {
+struct WideChild {
+    float4 lo, hi;
+    int32_t ref;
+};
+
+// binary child c as a wide child: a single-triangle leaf (c < 0), a leaf of
+// a non-kept subtree, or a kept node's 4-wide index
+__device__ __forceinline__ WideChild wide_child(int32_t c, const uint32_t* keep, const uint32_t* newidx,
+                                                const int32_t* first, const int32_t* last, const float4* leaf_box,
+                                                const float4* node_box) {
+    WideChild w;
     if (c < 0) {
-        lo = leaf_box[2 * (int64_t)(~c)];
-        hi = leaf_box[2 * (int64_t)(~c) + 1];
-        cnt = 1;
-        ref = leaf_ref(~c, cnt);
+        w.lo = leaf_box[2 * (int64_t)(~c)];
+        w.hi = leaf_box[2 * (int64_t)(~c) + 1];
+        w.ref = leaf_ref(~c, 1);
     } else {
-        lo = node_box[2 * (int64_t)c];
-        hi = node_box[2 * (int64_t)c + 1];
-        if (keep[c]) {
-            ref = (int32_t)newidx[c];
-            cnt = 0;
-        } else {
-            cnt = last[c] - first[c] + 1;
-            ref = leaf_ref(first[c], cnt);
-        }
+        w.lo = node_box[2 * (int64_t)c];
+        w.hi = node_box[2 * (int64_t)c + 1];
+        w.ref = keep[c] ? (int32_t)newidx[c] : leaf_ref(first[c], last[c] - first[c] + 1);
     }
+    return w;
 }
 
-__global__ void k_emit_nodes(int64_t n_int, const int32_t* __restrict__ left, const int32_t* __restrict__ right,
-                             const int32_t* __restrict__ first, const int32_t* __restrict__ last,
-                             const uint32_t* __restrict__ keep, const uint32_t* __restrict__ newidx,
-                             const float4* __restrict__ leaf_box, const float4* __restrict__ node_box,
-                             float4* __restrict__ nodes) {
+// 4-wide node layout (128 B): float4 0..5 = lo.x[4], lo.y[4], lo.z[4],
+// hi.x[4], hi.y[4], hi.z[4]; float4 6 = child refs; float4 7 = child count.
+// An empty slot has lo = hi = +inf, which every ray misses (entry at +inf or
+// an empty interval) and ref = leaf_ref(0, 0).
+__device__ __forceinline__ void store_wide(float4* n, const WideChild* c, int nc) {
+    float v[6][4];
+    int32_t r[4];
+    for (int k = 0; k < 4; k++) {
+        const bool ok = k < nc;
+        v[0][k] = ok ? c[k].lo.x : INFINITY;
+        v[1][k] = ok ? c[k].lo.y : INFINITY;
+        v[2][k] = ok ? c[k].lo.z : INFINITY;
+        v[3][k] = ok ? c[k].hi.x : INFINITY;
+        v[4][k] = ok ? c[k].hi.y : INFINITY;
+        v[5][k] = ok ? c[k].hi.z : INFINITY;
+        r[k] = ok ? c[k].ref : leaf_ref(0, 0);
+    }
+    for (int j = 0; j < 6; j++) n[j] = make_float4(v[j][0], v[j][1], v[j][2], v[j][3]);
+    n[6] = make_float4(__int_as_float(r[0]), __int_as_float(r[1]), __int_as_float(r[2]), __int_as_float(r[3]));
+    n[7] = make_float4(__int_as_float(nc), 0.f, 0.f, 0.f);
+}
+
+__global__ void k_emit_wide(int64_t n_int, const int32_t* __restrict__ left, const int32_t* __restrict__ right,
+                            const int32_t* __restrict__ first, const int32_t* __restrict__ last,
+                            const uint32_t* __restrict__ keep, const uint32_t* __restrict__ keep4,
+                            const uint32_t* __restrict__ newidx, const float4* __restrict__ leaf_box,
+                            const float4* __restrict__ node_box, float4* __restrict__ nodes) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_int || !keep[i]) return;
-    float4 l0, h0, l1, h1;
-    int32_t r0, r1, c0, c1;
+    if (i >= n_int || !keep4[i]) return;
+    WideChild c[4];
+    int nc = 0;
     if (i == 0 && (last[0] - first[0] + 1) <= RR_LEAF_MAX) {
         // the whole mesh fits one leaf
-        l0 = node_box[0];
-        h0 = node_box[1];
-        c0 = last[0] - first[0] + 1;
-        r0 = leaf_ref(0, c0);
-        l1 = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-        h1 = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
-        c1 = 0;
-        r1 = leaf_ref(0, 0);  // empty
+        c[0].lo = node_box[0];
+        c[0].hi = node_box[1];
+        c[0].ref = leaf_ref(0, last[0] - first[0] + 1);
+        nc = 1;
     } else {
-        emit_child(left[i], keep, newidx, first, last, leaf_box, node_box, l0, h0, r0, c0);
-        emit_child(right[i], keep, newidx, first, last, leaf_box, node_box, l1, h1, r1, c1);
+        const int32_t kids[2] = {left[i], right[i]};
+        for (int k = 0; k < 2; k++) {
+            const int32_t b = kids[k];
+            if (b >= 0 && keep[b]) {  // a kept odd-depth node: open it
+                c[nc++] = wide_child(left[b], keep, newidx, first, last, leaf_box, node_box);
+                c[nc++] = wide_child(right[b], keep, newidx, first, last, leaf_box, node_box);
+            } else {
+                c[nc++] = wide_child(b, keep, newidx, first, last, leaf_box, node_box);
+            }
+        }
     }
-    float4* n = nodes + 4 * (int64_t)newidx[i];
-    n[0] = make_float4(l0.x, l0.y, l0.z, h0.x);
-    n[1] = make_float4(h0.y, h0.z, l1.x, l1.y);
-    n[2] = make_float4(l1.z, h1.x, h1.y, h1.z);
-    n[3] = make_float4(__int_as_float(r0), __int_as_float(r1), __int_as_float(c0), __int_as_float(c1));
+    store_wide(nodes + 8 * (int64_t)newidx[i], c, nc);
 }
 
-// single-triangle mesh: one node holding one leaf
+// single-triangle mesh: one 4-wide node holding one leaf
 __global__ void k_single(const float4* __restrict__ tv, float4* __restrict__ nodes, float4* __restrict__ tris) {
     Box b = tri_box(tv, 0);
-    nodes[0] = make_float4(b.lo[0], b.lo[1], b.lo[2], b.hi[0]);
-    nodes[1] = make_float4(b.hi[1], b.hi[2], INFINITY, INFINITY);
-    nodes[2] = make_float4(INFINITY, -INFINITY, -INFINITY, -INFINITY);
-    nodes[3] = make_float4(__int_as_float(~1), __int_as_float(~0), __int_as_float(1), __int_as_float(0));
+    WideChild c;
+    c.lo = make_float4(b.lo[0], b.lo[1], b.lo[2], 0.f);
+    c.hi = make_float4(b.hi[0], b.hi[1], b.hi[2], 0.f);
+    c.ref = leaf_ref(0, 1);
+    store_wide(nodes, &c, 1);
     tris[0] = tv[0];
     tris[1] = tv[1];
     tris[2] = tv[2];
@@ -535,7 +583,7 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out) 
     float4* nodes;
     int64_t n_nodes = 1;
     if (M == 1) {
-        RR_TRY(keep_arena.alloc(&nodes, 4));
+        RR_TRY(keep_arena.alloc(&nodes, 8));
         RR_LAUNCH(k_single, 1, 1, 0, s, tv, nodes, tris);
         RR_CUDA(cudaGetLastError());
         hm.depth = 1;
@@ -544,7 +592,7 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out) 
         int32_t *left, *right, *first, *last, *pint, *pleaf;
         float4 *leaf_box, *node_box;
         unsigned int* flags;
-        uint32_t *keep, *newidx, *total;
+        uint32_t *keep, *keep4, *newidx, *total;
         RR_TRY(tmp.alloc(&left, NI));
         RR_TRY(tmp.alloc(&right, NI));
         RR_TRY(tmp.alloc(&first, NI));
@@ -555,6 +603,7 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out) 
         RR_TRY(tmp.alloc(&node_box, 2 * NI));
         RR_TRY(tmp.alloc(&flags, NI));
         RR_TRY(tmp.alloc(&keep, NI));
+        RR_TRY(tmp.alloc(&keep4, NI));
         RR_TRY(tmp.alloc(&newidx, NI));
         RR_TRY(tmp.alloc(&total, 1));
         void* scan_tmp;
@@ -566,15 +615,16 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out) 
         RR_LAUNCH(k_refit, grid_of(M, 256), 256, 0, s, M, left, right, pint, pleaf, leaf_box, node_box, flags);
         RR_LAUNCH(k_depth, grid_of(M, 256), 256, 0, s, M, pint, pleaf, meta);
         RR_LAUNCH(k_keep, grid_of(NI, 256), 256, 0, s, NI, first, last, keep);
+        RR_LAUNCH(k_keep4, grid_of(NI, 256), 256, 0, s, NI, pint, keep, keep4);
         RR_CUDA(cudaGetLastError());
-        RR_TRY(exclusive_scan_u32(keep, newidx, NI, total, scan_tmp, s));
+        RR_TRY(exclusive_scan_u32(keep4, newidx, NI, total, scan_tmp, s));
         uint32_t nn = 0;
         RR_CUDA(cudaMemcpyAsync(&nn, total, sizeof nn, cudaMemcpyDeviceToHost, s));
         RR_CUDA(cudaStreamSynchronize(s));
         n_nodes = nn;
-        RR_TRY(keep_arena.alloc(&nodes, 4 * n_nodes));
-        RR_LAUNCH(k_emit_nodes, grid_of(NI, 256), 256, 0, s, NI, left, right, first, last, keep, newidx, leaf_box,
-                                                      node_box, nodes);
+        RR_TRY(keep_arena.alloc(&nodes, 8 * n_nodes));
+        RR_LAUNCH(k_emit_wide, grid_of(NI, 256), 256, 0, s, NI, left, right, first, last, keep, keep4, newidx,
+                  leaf_box, node_box, nodes);
         RR_LAUNCH(k_reorder, grid_of(M, 256), 256, 0, s, tv, vals, M, tris);
         RR_CUDA(cudaGetLastError());
     }

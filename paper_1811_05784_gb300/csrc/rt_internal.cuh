@@ -120,7 +120,7 @@ struct rt_tree {
     int32_t n_materials = 0;      // max material id + 1
     double diameter = 1.0;
     // device arrays
-    float4* nodes = nullptr;      // [n_nodes][4]: two child boxes + refs (64 B / node)
+    float4* nodes = nullptr;      // [n_nodes][8]: four child boxes (SoA) + refs + count (128 B / node)
     float4* tris = nullptr;       // [n_tris][3] tree order: v0 (w = id), v1 (w = surface id), v2
     float4* tri_nrm = nullptr;    // [n_tris] by id: unit normal (float32 of FP64), w = surface id bits
     int32_t* surf_of = nullptr;   // [n_tris] by id

@@ -276,14 +276,30 @@ __device__ __forceinline__ void tri_test(const RayPre& r, const float4* __restri
 }
 
 // traversal stack in shared memory: STACK_SMEM entries per thread, laid out
-// [entry][thread] so that lanes at the same depth hit different banks
-static constexpr int STACK_SMEM = 48;
+// [entry][thread] so that lanes at the same depth hit different banks.  A
+// 4-wide node pushes at most 3 entries, so a tree of binary depth D needs at
+// most 3 ceil(D / 2) <= 64 entries for D <= 42; deeper trees can overflow,
+// which the kernel reports (ST_STACK) instead of writing past the stack.
+static constexpr int STACK_SMEM = 64;
 
-// Nearest hit, while-while traversal with postponed leaves (Aila & Laine
-// 2009): a lane that meets a leaf keeps it aside and goes on descending
-// until every lane of the warp holds a leaf, then all lanes test triangles
-// together.  Child references: >= 0 internal node, < 0 leaf
-// ~(first_triangle << 3 | count).
+// compare-exchange of (t, ref) pairs, nearer first
+__device__ __forceinline__ void cswap(float& ta, int& ra, float& tb, int& rb) {
+    const bool sw = tb < ta;
+    const float t = sw ? tb : ta;
+    const int r = sw ? rb : ra;
+    tb = sw ? ta : tb;
+    rb = sw ? ra : rb;
+    ta = t;
+    ra = r;
+}
+
+// Nearest hit over the 4-wide tree, while-while traversal with postponed
+// leaves (Aila & Laine 2009): a lane that meets a leaf keeps it aside and
+// goes on descending until every lane of the warp holds a leaf, then all
+// lanes test triangles together.  At a node the four child boxes are slab-
+// tested, sorted by entry distance (a 5-exchange network; misses sort last),
+// the nearest is visited next and the other hits are pushed far-to-near.
+// Child references: >= 0 internal node, < 0 leaf ~(first_triangle << 3 | count).
 template <int BT>
 __device__ __forceinline__ void nearest_hit(const BounceArgs& a, const RoomDev& rm, const RayPre& r, int exclude,
                                             float& best_t, int& best_id, unsigned int& err, int& n_nodes,
@@ -309,27 +325,35 @@ __device__ __forceinline__ void nearest_hit(const BounceArgs& a, const RoomDev& 
                 leaf = 0;
                 break;
             }
-            const float4* np = rm.nodes + 4 * (int64_t)node;
-            const float4 n0 = __ldg(np), n1 = __ldg(np + 1), n2 = __ldg(np + 2), n3 = __ldg(np + 3);
+            const float4* np = rm.nodes + 8 * (int64_t)node;
+            const float4 lx = __ldg(np), ly = __ldg(np + 1), lz = __ldg(np + 2);
+            const float4 hx = __ldg(np + 3), hy = __ldg(np + 4), hz = __ldg(np + 5);
+            const int4 ref = __ldg(reinterpret_cast<const int4*>(np + 6));
             n_nodes++;
-            const int r0 = __float_as_int(n3.x), r1 = __float_as_int(n3.y);
-            const float t0 = slab(r, n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, best_t);
-            const float t1 = slab(r, n1.z, n1.w, n2.x, n2.y, n2.z, n2.w, best_t);
-            const bool h0 = t0 < INFINITY, h1 = t1 < INFINITY;
-            if (!h0 && !h1) {
+            float t0 = slab(r, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x, best_t);
+            float t1 = slab(r, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, best_t);
+            float t2 = slab(r, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z, best_t);
+            float t3 = slab(r, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w, best_t);
+            int r0 = ref.x, r1 = ref.y, r2 = ref.z, r3 = ref.w;
+            cswap(t0, r0, t1, r1);
+            cswap(t2, r2, t3, r3);
+            cswap(t0, r0, t2, r2);
+            cswap(t1, r1, t3, r3);
+            cswap(t1, r1, t2, r2);
+            if (!(t0 < INFINITY)) {
                 node = sp > 0 ? stack[--sp * BT] : SENTINEL;
             } else {
-                const bool swap = h1 && (!h0 || t1 < t0);  // nearest child first
-                node = swap ? r1 : r0;
-                if (h0 && h1) {
-                    if (sp >= STACK_SMEM) {
-                        err |= ST_STACK;
-                        node = SENTINEL;
-                        leaf = 0;
-                        break;
-                    }
-                    stack[sp++ * BT] = swap ? r0 : r1;
+                node = r0;
+                const int push = (t1 < INFINITY) + (t2 < INFINITY) + (t3 < INFINITY);
+                if (sp + push > STACK_SMEM) {
+                    err |= ST_STACK;
+                    node = SENTINEL;
+                    leaf = 0;
+                    break;
                 }
+                if (t3 < INFINITY) stack[sp++ * BT] = r3;
+                if (t2 < INFINITY) stack[sp++ * BT] = r2;
+                if (t1 < INFINITY) stack[sp++ * BT] = r1;
             }
             if (node < 0 && leaf == 0) {  // postpone the leaf, keep descending
                 leaf = node;
@@ -497,7 +521,7 @@ __device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool act
 // ---------------------------------------------------------------------------
 template <int BT>
 __global__ void __launch_bounds__(BT) k_bounce(BounceArgs a) {
-    __shared__ int s_stack[STACK_SMEM * BT];
+    extern __shared__ int s_stack[];  // STACK_SMEM * BT entries (stack_bytes)
     int* stack = s_stack + threadIdx.x;
     const int lane = threadIdx.x & 31;
     const unsigned int n_live = a.live[a.b];
@@ -805,13 +829,8 @@ static void tune_report(const std::string& key, int cand, float ms) {
     }
 }
 
-template <int BT>
-static int occupancy_grid() {
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bounce<BT>, BT, 0);
-    cudaGetLastError();
-    return device_sm_count() * (occ > 0 ? occ : 1);
-}
+// dynamic shared memory of a bounce launch: the traversal stacks
+static size_t stack_bytes(int block) { return sizeof(int) * (size_t)STACK_SMEM * (size_t)block; }
 
 static void* kernel_of(int block) {
     switch (block) {
@@ -819,6 +838,23 @@ static void* kernel_of(int block) {
         case 256: return (void*)k_bounce<256>;
         default: return (void*)k_bounce<128>;
     }
+}
+
+// allow the stacks above the 48 KB default (the 256-thread block needs 64 KB);
+// a function attribute of the current device, set before any launch or capture
+static rt_status allow_stack_smem(int block) {
+    RR_CUDA(cudaFuncSetAttribute(kernel_of(block), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)stack_bytes(block)));
+    return RT_OK;
+}
+
+template <int BT>
+static int occupancy_grid() {
+    int occ = 0;
+    if (allow_stack_smem(BT) == RT_OK)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bounce<BT>, BT, stack_bytes(BT));
+    cudaGetLastError();
+    return device_sm_count() * (occ > 0 ? occ : 1);
 }
 
 static int grid_of_block(int block) {
@@ -870,6 +906,8 @@ namespace rr {
 static rt_status run_bounces(BounceArgs a, const Queue q[2], int B, int block, int grid, cudaStream_t s,
                              rt_workspace* ws) {
     void* kern = kernel_of(block);
+    const size_t smem = stack_bytes(block);
+    RR_TRY(allow_stack_smem(block));
     std::vector<BounceArgs> args((size_t)B, a);
     for (int b = 0; b < B; b++) {
         args[b].b = b;
@@ -883,7 +921,7 @@ static rt_status run_bounces(BounceArgs a, const Queue q[2], int B, int block, i
     if (!can_graph) {
         for (int b = 0; b < B; b++) {
             void* params[] = {&args[b]};
-            RR_CUDA(cudaLaunchKernel(kern, dim3(grid), dim3(block), params, 0, s));
+            RR_CUDA(cudaLaunchKernel(kern, dim3(grid), dim3(block), params, smem, s));
             note_launch();
         }
         return RT_OK;
@@ -893,7 +931,7 @@ static rt_status run_bounces(BounceArgs a, const Queue q[2], int B, int block, i
         RR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         for (int b = 0; b < B; b++) {
             void* params[] = {&args[b]};
-            cudaLaunchKernel(kern, dim3(grid), dim3(block), params, 0, s);
+            cudaLaunchKernel(kern, dim3(grid), dim3(block), params, smem, s);
         }
         cudaGraph_t g = nullptr;
         RR_CUDA(cudaStreamEndCapture(s, &g));
@@ -923,7 +961,7 @@ static rt_status run_bounces(BounceArgs a, const Queue q[2], int B, int block, i
             kp.func = kern;
             kp.gridDim = dim3(grid);
             kp.blockDim = dim3(block);
-            kp.sharedMemBytes = 0;
+            kp.sharedMemBytes = (unsigned int)smem;
             kp.kernelParams = params;
             kp.extra = nullptr;
             RR_CUDA(cudaGraphExecKernelNodeSetParams(ws->exec, ws->nodes[b], &kp));
@@ -1267,7 +1305,8 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
         n_rec = n2[0];
         unsigned int st = h_cnt[2 * B + 1];
         if (st & ST_STACK) {
-            set_error("rt_trace: traversal stack overflow (tree deeper than %d)", STACK_SMEM);
+            set_error("rt_trace: traversal stack overflow (more than %d entries; a tree of binary depth <= 42 "
+                      "always fits)", STACK_SMEM);
             return RT_ERR_STACK;
         }
         if (st & ST_BOUNDS) {
