@@ -44,57 +44,78 @@ __device__ __forceinline__ float ord2f(unsigned int o) {
     return __uint_as_float(b);
 }
 
-// pass 1: validate, convert to float32, per-triangle normal, bounds, id ranges
+// pass 1: validate, convert to float32, per-triangle normal, bounds, id ranges.
+// Bounds and id ranges are reduced within each warp first (one atomic per
+// warp and quantity instead of one per triangle).
 __global__ void k_tri_prep(const double* __restrict__ V, int64_t nV, const int32_t* __restrict__ T, int64_t M,
                            const int32_t* __restrict__ mat, const int32_t* __restrict__ surf,
                            float4* __restrict__ tv, float4* __restrict__ nrm, BuildMeta* meta) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= M) return;
-    int32_t ia = T[3 * t], ib = T[3 * t + 1], ic = T[3 * t + 2];
-    if (ia < 0 || ib < 0 || ic < 0 || ia >= nV || ib >= nV || ic >= nV) {
-        atomicAdd(&meta->bad_index, 1u);
-        ia = ib = ic = 0;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = t < M;
+    unsigned int cmin[3] = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu}, cmax[3] = {0u, 0u, 0u};
+    int smax = INT_MIN, smin = INT_MAX, mmax = INT_MIN, mmin = INT_MAX;
+    if (in) {
+        int32_t ia = T[3 * t], ib = T[3 * t + 1], ic = T[3 * t + 2];
+        if (ia < 0 || ib < 0 || ic < 0 || ia >= nV || ib >= nV || ic >= nV) {
+            atomicAdd(&meta->bad_index, 1u);
+            ia = ib = ic = 0;
+        }
+        double a[3], b[3], c[3];
+        for (int k = 0; k < 3; k++) {
+            a[k] = V[3 * (int64_t)ia + k];
+            b[k] = V[3 * (int64_t)ib + k];
+            c[k] = V[3 * (int64_t)ic + k];
+        }
+        bool finite = true;
+        for (int k = 0; k < 3; k++) finite = finite && isfinite(a[k]) && isfinite(b[k]) && isfinite(c[k]);
+        if (!finite) {
+            atomicAdd(&meta->non_finite, 1u);
+            for (int k = 0; k < 3; k++) a[k] = b[k] = c[k] = 0.0;
+        }
+        double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                       e1[0] * e2[1] - e1[1] * e2[0]};
+        double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(len > 0.0)) {
+            atomicAdd(&meta->degenerate, 1u);
+            len = 1.0;
+        }
+        const int32_t s = surf[t], m = mat[t];
+        nrm[t] = make_float4((float)(n[0] / len), (float)(n[1] / len), (float)(n[2] / len), __int_as_float(s));
+        float4 fa = make_float4((float)a[0], (float)a[1], (float)a[2], __int_as_float((int)t));
+        float4 fb = make_float4((float)b[0], (float)b[1], (float)b[2], __int_as_float(s));
+        float4 fc = make_float4((float)c[0], (float)c[1], (float)c[2], 0.f);
+        tv[3 * t] = fa;
+        tv[3 * t + 1] = fb;
+        tv[3 * t + 2] = fc;
+        const float cx = (fa.x + fb.x + fc.x) * (1.0f / 3.0f), cy = (fa.y + fb.y + fc.y) * (1.0f / 3.0f),
+                    cz = (fa.z + fb.z + fc.z) * (1.0f / 3.0f);
+        cmin[0] = cmax[0] = f2ord(cx);
+        cmin[1] = cmax[1] = f2ord(cy);
+        cmin[2] = cmax[2] = f2ord(cz);
+        smax = smin = s;
+        mmax = mmin = m;
     }
-    double a[3], b[3], c[3];
+    const unsigned int full = 0xffffffffu;
     for (int k = 0; k < 3; k++) {
-        a[k] = V[3 * (int64_t)ia + k];
-        b[k] = V[3 * (int64_t)ib + k];
-        c[k] = V[3 * (int64_t)ic + k];
+        cmin[k] = __reduce_min_sync(full, cmin[k]);
+        cmax[k] = __reduce_max_sync(full, cmax[k]);
     }
-    bool finite = true;
-    for (int k = 0; k < 3; k++) finite = finite && isfinite(a[k]) && isfinite(b[k]) && isfinite(c[k]);
-    if (!finite) {
-        atomicAdd(&meta->non_finite, 1u);
-        for (int k = 0; k < 3; k++) a[k] = b[k] = c[k] = 0.0;
+    smax = __reduce_max_sync(full, smax);
+    smin = __reduce_min_sync(full, smin);
+    mmax = __reduce_max_sync(full, mmax);
+    mmin = __reduce_min_sync(full, mmin);
+    if ((threadIdx.x & 31) == 0 && (int64_t)blockIdx.x * blockDim.x + threadIdx.x < M) {
+        for (int k = 0; k < 3; k++) {
+            atomicMin(&meta->cmin[k], cmin[k]);
+            atomicMax(&meta->cmax[k], cmax[k]);
+        }
+        atomicMax(&meta->max_surf, smax);
+        atomicMin(&meta->min_surf, smin);
+        atomicMax(&meta->max_mat, mmax);
+        atomicMin(&meta->min_mat, mmin);
     }
-    double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-    double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
-    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-    double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-    if (!(len > 0.0)) {
-        atomicAdd(&meta->degenerate, 1u);
-        len = 1.0;
-    }
-    int32_t s = surf[t], m = mat[t];
-    nrm[t] = make_float4((float)(n[0] / len), (float)(n[1] / len), (float)(n[2] / len), __int_as_float(s));
-    float4 fa = make_float4((float)a[0], (float)a[1], (float)a[2], __int_as_float((int)t));
-    float4 fb = make_float4((float)b[0], (float)b[1], (float)b[2], __int_as_float(s));
-    float4 fc = make_float4((float)c[0], (float)c[1], (float)c[2], 0.f);
-    tv[3 * t] = fa;
-    tv[3 * t + 1] = fb;
-    tv[3 * t + 2] = fc;
-    float cx = (fa.x + fb.x + fc.x) * (1.0f / 3.0f), cy = (fa.y + fb.y + fc.y) * (1.0f / 3.0f),
-          cz = (fa.z + fb.z + fc.z) * (1.0f / 3.0f);
-    atomicMin(&meta->cmin[0], f2ord(cx));
-    atomicMin(&meta->cmin[1], f2ord(cy));
-    atomicMin(&meta->cmin[2], f2ord(cz));
-    atomicMax(&meta->cmax[0], f2ord(cx));
-    atomicMax(&meta->cmax[1], f2ord(cy));
-    atomicMax(&meta->cmax[2], f2ord(cz));
-    atomicMax(&meta->max_surf, s);
-    atomicMin(&meta->min_surf, s);
-    atomicMax(&meta->max_mat, m);
-    atomicMin(&meta->min_mat, m);
 }
 
 // lowest triangle id per surface
@@ -526,8 +547,76 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out) 
     RR_TRY(keep_arena.alloc(&tri_nrm, M));
     RR_LAUNCH(k_tri_prep, grid_of(M, 256), 256, 0, s, dV, nV, dT, M, dmat, dsurf, tv, tri_nrm, meta);
     RR_CUDA(cudaGetLastError());
+    // Everything up to the 4-wide nodes depends only on M, so it is queued
+    // before the first synchronisation; invalid input (reported below) was
+    // made harmless by k_tri_prep (indices clamped, coordinates zeroed).
+
+    // Morton codes, sort
+    uint64_t *keys, *keys_alt;
+    uint32_t *vals, *vals_alt;
+    RR_TRY(tmp.alloc(&keys, M));
+    RR_TRY(tmp.alloc(&keys_alt, M));
+    RR_TRY(tmp.alloc(&vals, M));
+    RR_TRY(tmp.alloc(&vals_alt, M));
+    void* sort_tmp;
+    RR_TRY(tmp.alloc((char**)&sort_tmp, sort_temp_bytes(M)));
+    RR_LAUNCH(k_morton, grid_of(M, 256), 256, 0, s, tv, M, meta, keys, vals);
+    RR_CUDA(cudaGetLastError());
+    RR_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, M, 0, 64, sort_tmp, s));
+
+    float4* tris;
+    RR_TRY(keep_arena.alloc(&tris, 3 * M));
+    float4* nodes;
+    uint32_t* total = nullptr;
+    if (M == 1) {
+        RR_TRY(keep_arena.alloc(&nodes, 8));
+        RR_LAUNCH(k_single, 1, 1, 0, s, tv, nodes, tris);
+        RR_CUDA(cudaGetLastError());
+    } else {
+        const int64_t NI = M - 1;
+        int32_t *left, *right, *first, *last, *pint, *pleaf;
+        float4 *leaf_box, *node_box;
+        unsigned int* flags;
+        uint32_t *keep, *keep4, *newidx;
+        RR_TRY(tmp.alloc(&left, NI));
+        RR_TRY(tmp.alloc(&right, NI));
+        RR_TRY(tmp.alloc(&first, NI));
+        RR_TRY(tmp.alloc(&last, NI));
+        RR_TRY(tmp.alloc(&pint, NI));
+        RR_TRY(tmp.alloc(&pleaf, M));
+        RR_TRY(tmp.alloc(&leaf_box, 2 * M));
+        RR_TRY(tmp.alloc(&node_box, 2 * NI));
+        RR_TRY(tmp.alloc(&flags, NI));
+        RR_TRY(tmp.alloc(&keep, NI));
+        RR_TRY(tmp.alloc(&keep4, NI));
+        RR_TRY(tmp.alloc(&newidx, NI));
+        RR_TRY(tmp.alloc(&total, 1));
+        void* scan_tmp;
+        RR_TRY(tmp.alloc((char**)&scan_tmp, scan_temp_bytes(NI)));
+        RR_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned int) * NI, s));
+        RR_CUDA(cudaMemsetAsync(pint, 0xFF, sizeof(int32_t) * NI, s));  // root keeps -1
+        RR_LAUNCH(k_karras, grid_of(NI, 256), 256, 0, s, keys, M, left, right, first, last, pint, pleaf);
+        RR_LAUNCH(k_leaf_boxes, grid_of(M, 256), 256, 0, s, tv, vals, M, leaf_box);
+        RR_LAUNCH(k_refit, grid_of(M, 256), 256, 0, s, M, left, right, pint, pleaf, leaf_box, node_box, flags);
+        RR_LAUNCH(k_depth, grid_of(M, 256), 256, 0, s, M, pint, pleaf, meta);
+        RR_LAUNCH(k_keep, grid_of(NI, 256), 256, 0, s, NI, first, last, keep);
+        RR_LAUNCH(k_keep4, grid_of(NI, 256), 256, 0, s, NI, pint, keep, keep4);
+        RR_CUDA(cudaGetLastError());
+        RR_TRY(exclusive_scan_u32(keep4, newidx, NI, total, scan_tmp, s));
+        // at most NI 4-wide nodes (one per kept binary node): allocate that
+        // instead of reading the count back first
+        RR_TRY(keep_arena.alloc(&nodes, 8 * NI));
+        RR_LAUNCH(k_emit_wide, grid_of(NI, 256), 256, 0, s, NI, left, right, first, last, keep, keep4, newidx,
+                  leaf_box, node_box, nodes);
+        RR_LAUNCH(k_reorder, grid_of(M, 256), 256, 0, s, tv, vals, M, tris);
+        RR_CUDA(cudaGetLastError());
+    }
+    uint32_t nn = 1;
+    if (total) RR_CUDA(cudaMemcpyAsync(&nn, total, sizeof nn, cudaMemcpyDeviceToHost, s));
     RR_CUDA(cudaMemcpyAsync(&hm, meta, sizeof hm, cudaMemcpyDeviceToHost, s));
     RR_CUDA(cudaStreamSynchronize(s));
+    const int64_t n_nodes = nn;
+    if (M == 1) hm.depth = 1;
     if (hm.bad_index) {
         set_error("rt_build_tree: %u triangles index vertices out of range", hm.bad_index);
         return RT_ERR_INVALID_ARG;
@@ -564,74 +653,11 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out) 
         RR_CUDA(cudaGetLastError());
         // init is a pageable host buffer: the copy completes before returning
     }
-
-    // Morton codes, sort
-    uint64_t *keys, *keys_alt;
-    uint32_t *vals, *vals_alt;
-    RR_TRY(tmp.alloc(&keys, M));
-    RR_TRY(tmp.alloc(&keys_alt, M));
-    RR_TRY(tmp.alloc(&vals, M));
-    RR_TRY(tmp.alloc(&vals_alt, M));
-    void* sort_tmp;
-    RR_TRY(tmp.alloc((char**)&sort_tmp, sort_temp_bytes(M)));
-    RR_LAUNCH(k_morton, grid_of(M, 256), 256, 0, s, tv, M, meta, keys, vals);
-    RR_CUDA(cudaGetLastError());
-    RR_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, M, 0, 64, sort_tmp, s));
-
-    float4* tris;
-    RR_TRY(keep_arena.alloc(&tris, 3 * M));
-    float4* nodes;
-    int64_t n_nodes = 1;
-    if (M == 1) {
-        RR_TRY(keep_arena.alloc(&nodes, 8));
-        RR_LAUNCH(k_single, 1, 1, 0, s, tv, nodes, tris);
-        RR_CUDA(cudaGetLastError());
-        hm.depth = 1;
-    } else {
-        const int64_t NI = M - 1;
-        int32_t *left, *right, *first, *last, *pint, *pleaf;
-        float4 *leaf_box, *node_box;
-        unsigned int* flags;
-        uint32_t *keep, *keep4, *newidx, *total;
-        RR_TRY(tmp.alloc(&left, NI));
-        RR_TRY(tmp.alloc(&right, NI));
-        RR_TRY(tmp.alloc(&first, NI));
-        RR_TRY(tmp.alloc(&last, NI));
-        RR_TRY(tmp.alloc(&pint, NI));
-        RR_TRY(tmp.alloc(&pleaf, M));
-        RR_TRY(tmp.alloc(&leaf_box, 2 * M));
-        RR_TRY(tmp.alloc(&node_box, 2 * NI));
-        RR_TRY(tmp.alloc(&flags, NI));
-        RR_TRY(tmp.alloc(&keep, NI));
-        RR_TRY(tmp.alloc(&keep4, NI));
-        RR_TRY(tmp.alloc(&newidx, NI));
-        RR_TRY(tmp.alloc(&total, 1));
-        void* scan_tmp;
-        RR_TRY(tmp.alloc((char**)&scan_tmp, scan_temp_bytes(NI)));
-        RR_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned int) * NI, s));
-        RR_CUDA(cudaMemsetAsync(pint, 0xFF, sizeof(int32_t) * NI, s));  // root keeps -1
-        RR_LAUNCH(k_karras, grid_of(NI, 256), 256, 0, s, keys, M, left, right, first, last, pint, pleaf);
-        RR_LAUNCH(k_leaf_boxes, grid_of(M, 256), 256, 0, s, tv, vals, M, leaf_box);
-        RR_LAUNCH(k_refit, grid_of(M, 256), 256, 0, s, M, left, right, pint, pleaf, leaf_box, node_box, flags);
-        RR_LAUNCH(k_depth, grid_of(M, 256), 256, 0, s, M, pint, pleaf, meta);
-        RR_LAUNCH(k_keep, grid_of(NI, 256), 256, 0, s, NI, first, last, keep);
-        RR_LAUNCH(k_keep4, grid_of(NI, 256), 256, 0, s, NI, pint, keep, keep4);
-        RR_CUDA(cudaGetLastError());
-        RR_TRY(exclusive_scan_u32(keep4, newidx, NI, total, scan_tmp, s));
-        uint32_t nn = 0;
-        RR_CUDA(cudaMemcpyAsync(&nn, total, sizeof nn, cudaMemcpyDeviceToHost, s));
-        RR_CUDA(cudaStreamSynchronize(s));
-        n_nodes = nn;
-        RR_TRY(keep_arena.alloc(&nodes, 8 * n_nodes));
-        RR_LAUNCH(k_emit_wide, grid_of(NI, 256), 256, 0, s, NI, left, right, first, last, keep, keep4, newidx,
-                  leaf_box, node_box, nodes);
-        RR_LAUNCH(k_reorder, grid_of(M, 256), 256, 0, s, tv, vals, M, tris);
-        RR_CUDA(cudaGetLastError());
-    }
-    RR_CUDA(cudaMemcpyAsync(&hm, meta, sizeof hm, cudaMemcpyDeviceToHost, s));
+    unsigned int mixed = 0;
+    RR_CUDA(cudaMemcpyAsync(&mixed, &meta->mixed_material, sizeof mixed, cudaMemcpyDeviceToHost, s));
     RR_CUDA(cudaStreamSynchronize(s));
-    if (hm.mixed_material) {
-        set_error("rt_build_tree: %u triangles differ in material from their surface", hm.mixed_material);
+    if (mixed) {
+        set_error("rt_build_tree: %u triangles differ in material from their surface", mixed);
         return RT_ERR_INVALID_ARG;
     }
     tree->depth = hm.depth;

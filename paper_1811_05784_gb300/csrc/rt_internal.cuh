@@ -147,4 +147,4 @@ struct rt_response {
 // Node reference encoding shared by the build and the traversal.
 //   ref >= 0 : internal node index
 //   ref <  0 : leaf, first triangle (tree order) = ~ref, count in the node's cnt field
-#define RR_LEAF_MAX 4
+#define RR_LEAF_MAX 2
