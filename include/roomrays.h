@@ -247,11 +247,13 @@ rt_status rt_measure_l2_bandwidth(double* read_gbs, void* stream);
  * Learned late-reverberation tail (no counterpart in the paper: the network
  * of the surrogate-tail mode, which predicts the traced tail).  A 3-layer
  * MLP: Linear(n_in, H) - GELU - Linear(H, H) - GELU - Linear(H, n_out), FP32
- * master weights with Adam, BF16
- * copies read by hand-written tensor-core GEMMs (mma.sync m16n8k16, FP32
- * accumulation).  Sizes must be multiples of 32.  x, target, y are device
- * float arrays [batch][n_in] / [batch][n_out].  The loss is the mean squared
- * error over batch x n_out.  Parameter block layout (rt_mlp_info offsets):
+ * master weights with Adam, BF16 copies read by hand-written tensor-core
+ * GEMMs (tcgen05.mma from swizzled shared-memory tiles into an FP32
+ * accumulator in tensor memory).  Sizes must be multiples of 32.  x, target,
+ * y are device float arrays [batch][n_in] / [batch][n_out].  The loss is the
+ * mean squared error over batch x n_out.  Calls that synchronise (a loss
+ * requested, rt_mlp_copy) return RT_ERR_CUDA if a GEMM timed out waiting for
+ * its tensor-core operations.  Parameter block layout (rt_mlp_info offsets):
  * W1 [H][n_in], b1 [H], W2 [H][H], b2 [H], W3 [n_out][H], b3 [n_out].
  * ------------------------------------------------------------------------- */
 typedef struct rt_mlp rt_mlp;

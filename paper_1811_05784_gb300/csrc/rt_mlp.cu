@@ -2,20 +2,22 @@
 // run on the GPU with hand-written BF16 tensor-core kernels.
 //
 // Network: x[B][n_in] -> Linear(n_in, H) -> GELU -> Linear(H, H) -> GELU ->
-// Linear(H, n_out).  Weights are kept as FP32 master copies (Adam) and as
+// Linear(H, n_out).  Weights are kept as FP32 master copies (AdamW) and as
 // BF16 copies (row-major [out][in] and transposed) that the GEMMs read;
 // activations entering a GEMM are BF16, accumulation is FP32.
 //
-// One GEMM kernel serves every product: C[M][N] = A[M][K] . B[N][K]^T with
-// both operands K-contiguous (warp-level mma.sync.m16n8k16 bf16 -> f32,
-// 64x64x32 block tiles staged in shared memory).  Backward products that need
-// the other orientation read transposed BF16 copies made by k_transpose.
+// Every product runs on the 5th-generation tensor cores (rt_tc_gemm.cuh:
+// tcgen05.mma from swizzled shared-memory tiles into a TMEM accumulator):
+// C[M][N] = A[M][K] . B[N][K]^T with both operands K-contiguous.  Backward
+// products that need the other orientation read transposed BF16 copies made
+// by k_transpose.
 //   forward    Z = X W^T + b             (A = X, B = W)
 //   dX         dX = dZ W                 (A = dZ, B = W^T)
 //   dW         dW = dZ^T X               (A = dZ^T, B = X^T, K = batch)
 // The paper has no learned component; the network is the learned tail of the
 // surrogate mode (room descriptors and short traces in, late decay out).
 #include "rt_internal.cuh"
+#include "rt_tc_gemm.cuh"
 
 #include <cuda_bf16.h>
 
@@ -26,108 +28,15 @@ namespace rr {
 
 typedef __nv_bfloat16 bf16;
 
-static constexpr int GBM = 64, GBN = 64, GBK = 32, GPAD = 8;
+using tc::EPI_BIAS_F32;
+using tc::EPI_BIAS_GELU;
+using tc::EPI_F32;
 
-enum { EPI_F32 = 0, EPI_BIAS_GELU = 1, EPI_BIAS_F32 = 2 };
-
-__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float x) {
     // d/dx [x Phi(x)] = Phi(x) + x phi(x)
     const float cdf = 0.5f * (1.0f + erff(x * 0.70710678118654752f));
     const float pdf = 0.3989422804014327f * expf(-0.5f * x * x);
     return cdf + x * pdf;
-}
-
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// C[M][N] = A[M][K] . B[N][K]^T (+ bias, GELU).  K % 32 == 0; M, N any.
-// EPI_F32:        Cf = acc
-// EPI_BIAS_F32:   Cf = acc + bias
-// EPI_BIAS_GELU:  Cpre = acc + bias, Cb = bf16(gelu(acc + bias))
-template <int EPI>
-__global__ void __launch_bounds__(128) k_gemm_nt(const bf16* __restrict__ A, const bf16* __restrict__ Bm, int M, int N,
-                                                 int K, const float* __restrict__ bias, float* __restrict__ Cf,
-                                                 float* __restrict__ Cpre, bf16* __restrict__ Cb) {
-    __shared__ __align__(16) bf16 As[GBM][GBK + GPAD];
-    __shared__ __align__(16) bf16 Bs[GBN][GBK + GPAD];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp >> 1, wn = warp & 1;  // 2 x 2 warps, each 32 x 32
-    const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-    const int g = lane >> 2, t = lane & 3;
-    float acc[2][4][4];
-#pragma unroll
-    for (int i = 0; i < 2; i++)
-#pragma unroll
-        for (int j = 0; j < 4; j++)
-#pragma unroll
-            for (int k = 0; k < 4; k++) acc[i][j][k] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += GBK) {
-        // stage: 64 rows x 32 bf16 = 256 chunks of 16 B per operand, 2 per thread
-#pragma unroll
-        for (int r = 0; r < 2; r++) {
-            const int c = tid + r * 128;
-            const int row = c >> 2, col = (c & 3) * 8;
-            uint4 va = make_uint4(0, 0, 0, 0), vb = make_uint4(0, 0, 0, 0);
-            if (m0 + row < M) va = *reinterpret_cast<const uint4*>(A + (size_t)(m0 + row) * K + k0 + col);
-            if (n0 + row < N) vb = *reinterpret_cast<const uint4*>(Bm + (size_t)(n0 + row) * K + k0 + col);
-            *reinterpret_cast<uint4*>(&As[row][col]) = va;
-            *reinterpret_cast<uint4*>(&Bs[row][col]) = vb;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GBK; kk += 16) {
-            uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-            for (int i = 0; i < 2; i++) {
-                const int r = wm * 32 + i * 16;
-                af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r + g][kk + 2 * t]);
-                af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + g + 8][kk + 2 * t]);
-                af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r + g][kk + 2 * t + 8]);
-                af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + g + 8][kk + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const int c = wn * 32 + j * 8;
-                bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c + g][kk + 2 * t]);
-                bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c + g][kk + 2 * t + 8]);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; i++)
-#pragma unroll
-                for (int j = 0; j < 4; j++) mma_bf16(acc[i][j], af[i], bfr[j]);
-        }
-        __syncthreads();
-    }
-    // epilogue
-#pragma unroll
-    for (int i = 0; i < 2; i++) {
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-#pragma unroll
-            for (int h = 0; h < 4; h++) {
-                const int row = m0 + wm * 32 + i * 16 + g + (h >= 2 ? 8 : 0);
-                const int col = n0 + wn * 32 + j * 8 + 2 * t + (h & 1);
-                if (row >= M || col >= N) continue;
-                float v = acc[i][j][h];
-                const size_t o = (size_t)row * N + col;
-                if (EPI == EPI_F32) {
-                    Cf[o] = v;
-                } else if (EPI == EPI_BIAS_F32) {
-                    Cf[o] = v + bias[col];
-                } else {
-                    v += bias[col];
-                    Cpre[o] = v;
-                    Cb[o] = __float2bfloat16_rn(gelu_f(v));
-                }
-            }
-        }
-    }
 }
 
 // out[C][R_pad] = in[R][C]^T, zero in columns R .. R_pad-1
@@ -226,6 +135,7 @@ struct rt_mlp {
     float *dh = nullptr;                                      // FP32 backward scratch
     rr::bf16 *dz = nullptr, *dzt = nullptr, *at = nullptr;   // backward BF16 scratch
     float* loss_part = nullptr;
+    unsigned int* tc_status = nullptr;   // bit 0: a tensor-core GEMM gave up waiting for its MMAs
     std::vector<void*> owned;
     cudaStream_t stream = nullptr;
 };
@@ -257,11 +167,14 @@ static rt_status mlp_reserve(rt_mlp* net, int B, cudaStream_t s) {
     return RT_OK;
 }
 
+// K % 32 == 0 for every product here (layer sizes and the padded batch), so
+// rows are 16-byte aligned as the tile copies need
 template <int EPI>
 static void gemm(const bf16* A, const bf16* B, int M, int N, int K, const float* bias, float* Cf, float* Cpre, bf16* Cb,
-                 cudaStream_t s) {
-    dim3 grid(gridn(N, GBN), gridn(M, GBM));
-    RR_LAUNCH(k_gemm_nt<EPI>, grid, 128, 0, s, A, B, M, N, K, bias, Cf, Cpre, Cb);
+                 unsigned int* status, cudaStream_t s) {
+    dim3 grid(gridn(N, tc::BN), gridn(M, tc::BM));
+    cudaFuncSetAttribute(tc::k_gemm_tc<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    RR_LAUNCH(tc::k_gemm_tc<EPI>, grid, 128, tc::SMEM_BYTES, s, A, B, M, N, K, bias, Cf, Cpre, Cb, status);
 }
 
 static void transpose(const bf16* in, int R, int C, int R_pad, bf16* out, cudaStream_t s) {
@@ -283,11 +196,11 @@ static rt_status mlp_forward_impl(rt_mlp* net, const float* x, int B, float* y_o
     RR_TRY(mlp_reserve(net, B, s));
     RR_LAUNCH(k_f32_to_bf16, gridn((int64_t)B * net->n_in, 256), 256, 0, s, x, (int64_t)B * net->n_in, net->xb);
     gemm<EPI_BIAS_GELU>(net->xb, net->wb + net->off[0], B, net->n_h, net->n_in, net->w + net->off[1], nullptr, net->z1,
-                        net->h1, s);
+                        net->h1, net->tc_status, s);
     gemm<EPI_BIAS_GELU>(net->h1, net->wb + net->off[2], B, net->n_h, net->n_h, net->w + net->off[3], nullptr, net->z2,
-                        net->h2, s);
+                        net->h2, net->tc_status, s);
     gemm<EPI_BIAS_F32>(net->h2, net->wb + net->off[4], B, net->n_out, net->n_h, net->w + net->off[5],
-                       y_out ? y_out : net->y, nullptr, nullptr, s);
+                       y_out ? y_out : net->y, nullptr, nullptr, net->tc_status, s);
     RR_CUDA(cudaGetLastError());
     return RT_OK;
 }
@@ -302,23 +215,33 @@ static rt_status mlp_backward_impl(rt_mlp* net, const float* x, const float* tar
     // layer 3: dW3 = dY^T H2, db3 = colsum dY, dH2 = dY W3
     transpose(net->dz, B, NO, Bp, net->dzt, s);
     transpose(net->h2, B, H, Bp, net->at, s);
-    gemm<EPI_F32>(net->dzt, net->at, NO, H, Bp, nullptr, net->g + net->off[4], nullptr, nullptr, s);
+    gemm<EPI_F32>(net->dzt, net->at, NO, H, Bp, nullptr, net->g + net->off[4], nullptr, nullptr, net->tc_status, s);
     RR_LAUNCH(k_colsum, gridn(NO, 128), 128, 0, s, net->dz, B, NO, net->g + net->off[5]);
-    gemm<EPI_F32>(net->dz, net->wt[2], B, H, NO, nullptr, net->dh, nullptr, nullptr, s);
+    gemm<EPI_F32>(net->dz, net->wt[2], B, H, NO, nullptr, net->dh, nullptr, nullptr, net->tc_status, s);
     RR_LAUNCH(k_gelu_back, gridn((int64_t)B * H, 256), 256, 0, s, net->dh, net->z2, (int64_t)B * H, net->dz);
     // layer 2
     transpose(net->dz, B, H, Bp, net->dzt, s);
     transpose(net->h1, B, H, Bp, net->at, s);
-    gemm<EPI_F32>(net->dzt, net->at, H, H, Bp, nullptr, net->g + net->off[2], nullptr, nullptr, s);
+    gemm<EPI_F32>(net->dzt, net->at, H, H, Bp, nullptr, net->g + net->off[2], nullptr, nullptr, net->tc_status, s);
     RR_LAUNCH(k_colsum, gridn(H, 128), 128, 0, s, net->dz, B, H, net->g + net->off[3]);
-    gemm<EPI_F32>(net->dz, net->wt[1], B, H, H, nullptr, net->dh, nullptr, nullptr, s);
+    gemm<EPI_F32>(net->dz, net->wt[1], B, H, H, nullptr, net->dh, nullptr, nullptr, net->tc_status, s);
     RR_LAUNCH(k_gelu_back, gridn((int64_t)B * H, 256), 256, 0, s, net->dh, net->z1, (int64_t)B * H, net->dz);
     // layer 1 (no input gradient needed)
     transpose(net->dz, B, H, Bp, net->dzt, s);
     transpose(net->xb, B, NI, Bp, net->at, s);
-    gemm<EPI_F32>(net->dzt, net->at, H, NI, Bp, nullptr, net->g + net->off[0], nullptr, nullptr, s);
+    gemm<EPI_F32>(net->dzt, net->at, H, NI, Bp, nullptr, net->g + net->off[0], nullptr, nullptr, net->tc_status, s);
     RR_LAUNCH(k_colsum, gridn(H, 128), 128, 0, s, net->dz, B, H, net->g + net->off[1]);
     RR_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
+// after a synchronisation: did a tensor-core GEMM give up waiting?
+static rt_status check_tc(rt_mlp* net, unsigned int st) {
+    if (st) {
+        set_error("rt_mlp: a tensor-core GEMM timed out waiting for its MMAs (results discarded)");
+        return RT_ERR_CUDA;
+    }
+    (void)net;
     return RT_OK;
 }
 
@@ -326,8 +249,11 @@ static rt_status read_loss(rt_mlp* net, int B, cudaStream_t s, float* loss) {
     const int64_t ny = (int64_t)B * net->n_out;
     const int nb = (int)gridn(ny, 256);
     std::vector<float> part((size_t)nb);
+    unsigned int st = 0;
     RR_CUDA(cudaMemcpyAsync(part.data(), net->loss_part, sizeof(float) * nb, cudaMemcpyDeviceToHost, s));
+    RR_CUDA(cudaMemcpyAsync(&st, net->tc_status, sizeof st, cudaMemcpyDeviceToHost, s));
     RR_CUDA(cudaStreamSynchronize(s));
+    RR_TRY(check_tc(net, st));
     double acc = 0;
     for (float x : part) acc += x;
     *loss = (float)(acc / (double)ny);
@@ -368,7 +294,7 @@ extern "C" rt_status rt_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_out
     if ((st = ar.alloc(&net->w, o)) || (st = ar.alloc(&net->g, o)) || (st = ar.alloc(&net->m, o)) ||
         (st = ar.alloc(&net->v, o)) || (st = ar.alloc(&net->wb, o)) ||
         (st = ar.alloc(&net->wt[0], sizes[0])) || (st = ar.alloc(&net->wt[1], sizes[2])) ||
-        (st = ar.alloc(&net->wt[2], sizes[4]))) {
+        (st = ar.alloc(&net->wt[2], sizes[4])) || (st = ar.alloc(&net->tc_status, 1))) {
         delete net;
         return st;
     }
@@ -384,7 +310,8 @@ extern "C" rt_status rt_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_out
     if (cudaMemcpyAsync(net->w, hw.data(), sizeof(float) * o, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(net->m, 0, sizeof(float) * o, s) != cudaSuccess ||
         cudaMemsetAsync(net->v, 0, sizeof(float) * o, s) != cudaSuccess ||
-        cudaMemsetAsync(net->g, 0, sizeof(float) * o, s) != cudaSuccess) {
+        cudaMemsetAsync(net->g, 0, sizeof(float) * o, s) != cudaSuccess ||
+        cudaMemsetAsync(net->tc_status, 0, sizeof(unsigned int), s) != cudaSuccess) {
         rr::set_error("rt_mlp_create: initialisation copy failed");
         delete net;
         return RT_ERR_CUDA;
@@ -482,8 +409,10 @@ extern "C" rt_status rt_mlp_copy(rt_mlp* net, int32_t what, float* host, int32_t
     } else {
         RR_CUDA(cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, s));
     }
+    unsigned int st = 0;
+    RR_CUDA(cudaMemcpyAsync(&st, net->tc_status, sizeof st, cudaMemcpyDeviceToHost, s));
     RR_CUDA(cudaStreamSynchronize(s));
-    return RT_OK;
+    return rr::check_tc(net, st);
 }
 
 extern "C" rt_status rt_mlp_set_weight_decay(rt_mlp* net, float weight_decay) {
