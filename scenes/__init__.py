@@ -555,15 +555,20 @@ def tetra(level=4, n_rays=None, n_bounces=1) -> Scene:
 
 
 def batched_rooms(n_rooms=64, pairs=16, n_rays=262_144, n_bounces=30, seed=4,
-                  m_min=12, m_max=200_000):
-    """Rooms of uneven size for one batched launch: shoeboxes and L-rooms whose
-    triangle counts are log-uniform on [m_min, m_max] (seeded), each with
-    `pairs` source / receiver pairs (receiver r = 0.5 m)."""
+                  m_min=12, m_max=200_000, radius=0.5):
+    """Rooms of uneven size for one batched launch: shoeboxes (even index) and
+    L-rooms (odd index, once the target size allows a grid) whose triangle
+    counts are log-uniform on [m_min, m_max] (seeded), 4 materials with
+    seeded 8-band absorption, and `pairs` source / receiver pairs each
+    (receiver k of a room listens to source k; r = `radius`), placed at seeded
+    points at least 0.75 m (or 20 % of the extent) inside the walls and 1 m
+    apart.  meta holds the kind and the target size."""
     rng = np.random.default_rng(seed)
-    rooms = []
+    out = []
     for q in range(n_rooms):
         target = math.exp(rng.uniform(math.log(m_min), math.log(m_max)))
         dims = np.round(rng.uniform([4, 3, 2.5], [30, 20, 10]), 1)
+        alpha = seeded_alpha(4, int(rng.integers(1 << 31)))
         kind = "shoebox" if (q % 2 == 0) else "lroom"
         S = 2 * (dims[0] * dims[1] + dims[1] * dims[2] + dims[0] * dims[2])
         cell = math.sqrt(2 * S / target) if target > 12 else None
@@ -572,14 +577,30 @@ def batched_rooms(n_rooms=64, pairs=16, n_rays=262_144, n_bounces=30, seed=4,
             sc = dims[0] / 20.0
             h = max(0.05, math.sqrt(2 * 800 * sc * sc / target))
             h = 1.0 / max(1, round(1.0 / h * 1.0)) if h < 1 else round(h * 2) / 2
-            room = _scaled_lroom(sc, dims[2], h, rng)
+            soup, ext = _scaled_lroom(sc, dims[2], h, rng)
+            inside = lambda p, sc=sc: (p[0] < 10 * sc) or (p[1] < 7.5 * sc)
         else:
+            kind = "shoebox"
             soup = _Soup()
             _box_faces(soup, (0, 0, 0), dims, list(rng.integers(0, 4, 6)),
                        cells=None if cell is None else max(0.05, cell))
-            room = (soup, dims)
-        rooms.append((kind, room))
-    return rooms
+            ext = dims
+            inside = lambda p: True
+        margin = np.minimum(0.75, 0.2 * ext)
+        src, rcv = [], []
+        for _ in range(pairs):
+            for _try in range(1000):
+                a_ = rng.uniform(margin, ext - margin)
+                b_ = rng.uniform(margin, ext - margin)
+                if inside(a_) and inside(b_) and np.linalg.norm(a_ - b_) >= 1.0:
+                    break
+            src.append(a_)
+            rcv.append(b_)
+        room = _scene(f"batched room {q}", soup, alpha, np.zeros(N_BANDS), src, rcv, [radius] * pairs,
+                      np.arange(pairs), n_rays, n_bounces)
+        room.meta.update({"kind": kind, "target_tris": target})
+        out.append(room)
+    return out
 
 
 def _scaled_lroom(sc, height, h, rng):

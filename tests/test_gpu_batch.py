@@ -29,10 +29,7 @@ def _is_table(sc_list, isrc, rcv_base):
     return out
 
 
-def test_batch_matches_single_rooms():
-    N, B = 20_000, 20
-    scs = [scenes.shoebox(n_rays=N, n_bounces=B), scenes.lroom(h=0.5, n_rays=N, n_bounces=B),
-           scenes.icosphere(level=2, n_rays=N, n_bounces=B)]
+def _check_batch_equals_single(scs, N, B):
     trees = [_tree(sc) for sc in scs]
     rooms = [dict(tree=t, sources=sc.sources, rcv_center=sc.rcv_center, rcv_radius=sc.rcv_radius,
                   rcv_source=sc.rcv_source, band_absorption=sc.alpha) for t, sc in zip(trees, scs)]
@@ -43,7 +40,9 @@ def test_batch_matches_single_rooms():
     table_b = _is_table(scs, batch, rcv_base)
     off = 0
     for r, (sc, t) in enumerate(zip(scs, trees)):
-        single = rt.rt_trace(t, **rt.scene_args(sc))
+        kw = rt.scene_args(sc)
+        kw.update(n_rays=N, n_bounces=B)
+        single = rt.rt_trace(t, **kw)
         n = single.n_traced
         assert np.array_equal(hb[:, off:off + n], single.hist.cpu().numpy())
         assert np.array_equal(eb[off:off + n], single.ray_energy.cpu().numpy())
@@ -54,6 +53,23 @@ def test_batch_matches_single_rooms():
         assert sum(1 for key in table_b if key[0] == r) == len(ts)
         off += n
     assert off == batch.n_traced
+    return batch
+
+
+def test_batch_matches_single_rooms():
+    N, B = 20_000, 20
+    scs = [scenes.shoebox(n_rays=N, n_bounces=B), scenes.lroom(h=0.5, n_rays=N, n_bounces=B),
+           scenes.icosphere(level=2, n_rays=N, n_bounces=B)]
+    _check_batch_equals_single(scs, N, B)
+
+
+def test_batched_config_rooms_match_single_rooms():
+    """The first 8 rooms of the batched-rooms workload (12 to 200k triangles,
+    shoeboxes and L-rooms, several source / receiver pairs each) in one
+    launch give every room's own trace bit for bit."""
+    scs = scenes.batched_rooms(n_rooms=8, pairs=4, n_rays=4096, n_bounces=12)
+    batch = _check_batch_equals_single(scs, 4096, 12)
+    assert batch.n > 0
 
 
 def test_workspace_graph_replays_give_identical_results():
