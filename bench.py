@@ -60,9 +60,10 @@ def parse():
     ap.add_argument("--cpu-sample-rays", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clock-log", default=None, help="keep the nvidia-smi samples of the timed region here")
-    ap.add_argument("--workload", choices=["theatre", "batched"], default="theatre",
+    ap.add_argument("--workload", choices=["theatre", "batched", "tetra"], default="theatre",
                     help="theatre: the headline line; batched: 64 rooms x 16 pairs x 262,144 rays x 30 bounces "
-                         "in batched launches (one GPU, its own line)")
+                         "in batched launches; tetra: the N = M scaling sweep of one iteration on the refined "
+                         "tetrahedron (each its own line, one GPU)")
     ap.add_argument("--batch-chunk", type=int, default=65_536, help="rays per pair per batched launch")
     return ap.parse_args()
 
@@ -435,12 +436,81 @@ def run_batched(args):
         "gpu_launches": launches, "clocks": clk.summary()}))
 
 
+# single-core times of one iteration on the refined tetrahedron (N = M) as the
+# paper prints them (Sec. 2.2, Table 2): faces -> (without tree, with tree) seconds
+PAPER_TABLE2 = {1024: (0.26, 0.2), 2048: (0.4, 0.2), 4096: (0.91, 0.25), 8192: (3.05, 0.3), 16384: (11.44, 0.33),
+                32768: (46.02, 0.55), 65536: (181.61, 0.77), 131072: (725.17, 1.85), 262144: (2927.9, 2.76),
+                524288: (None, 8.36), 1048576: (None, 13.78)}
+
+
+def run_tetra(args):
+    """One ray-tracing iteration (one nearest-face query per ray) with N = M
+    rays and faces, source at the centre of the unit tetrahedron refined to
+    M = 4 * 4^level faces (M = 2^10 ... 2^20): tree build and iteration on the
+    GPU, and the FP64 oracle (its median-split tree) on the host cores."""
+    import torch
+    import oracle
+    from paper_1811_05784_gb300 import rt
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream()
+    rows = []
+    for level in range(4, 10):
+        sc = scenes.tetra(level)
+        M = len(sc.tris)
+        kw = rt.scene_args(sc)
+        mesh = tuple(torch.as_tensor(x, device=dev) for x in (sc.vertices, sc.tris, sc.material_id, sc.surface_id))
+        with torch.cuda.stream(stream):
+            for _ in range(max(args.warmup, 1)):
+                rt.rt_trace(rt.rt_build_tree(*mesh, stream=stream), stream=stream, **kw)
+            torch.cuda.synchronize()
+            b_ms, t_ms, q_ms = [], [], []
+            for _ in range(args.steps):
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record(stream)
+                tree = rt.rt_build_tree(*mesh, stream=stream)
+                e[1].record(stream)
+                isrc = rt.rt_trace(tree, stream=stream, **kw)
+                e[2].record(stream)
+                e[2].synchronize()
+                b_ms.append(e[0].elapsed_time(e[1]))
+                t_ms.append(e[1].elapsed_time(e[2]))
+                q_ms.append(isrc.ms_bounces)
+        t0 = time.perf_counter()
+        osc = oracle.OracleScene(sc, tree=True)
+        t1 = time.perf_counter()
+        tr = oracle.trace(osc)
+        t2 = time.perf_counter()
+        single = None
+        if M <= 65_536:
+            t3 = time.perf_counter()
+            oracle.trace(osc, threads=1)
+            single = time.perf_counter() - t3
+        paper = PAPER_TABLE2.get(M, (None, None))
+        rows.append({"faces": M, "rays": M, "queries": isrc.queries, "gpu_tree_ms": statistics.median(b_ms),
+                     "gpu_iteration_ms": statistics.median(t_ms), "gpu_query_loop_ms": statistics.median(q_ms),
+                     "oracle_tree_s": t1 - t0, "oracle_iteration_s": t2 - t1,
+                     "oracle_threads": oracle.default_threads(), "oracle_iteration_1thread_s": single,
+                     "oracle_queries": tr.queries, "paper_with_tree_s": paper[1], "paper_without_tree_s": paper[0]})
+        print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "time of one ray-tracing iteration, tetrahedron N = M", "unit": "s",
+                      "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "unit tetrahedron refined to M = 4 * 4^level faces (level 4..9), "
+                                             "N = M Fibonacci rays from the centre, 1 bounce",
+                                 "gpu_iteration": "rt_trace: ray generation, one query per ray, measurement "
+                                                  "sphere, image sources"},
+                      "sweep": rows}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "tetra":
+        run_tetra(args)
     else:
         run_native(args)
 

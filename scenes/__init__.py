@@ -539,16 +539,23 @@ def tetra(level=4, n_rays=None, n_bounces=1) -> Scene:
     F = [(0, 1, 2), (0, 3, 1), (0, 2, 3), (1, 3, 2)]
     soup = _Soup()
     n = 2 ** level
+    # lattice points (i, j), i + j <= n; per (i, j) an "up" triangle and, away
+    # from the far edge, a "down" one, in the same order as a row-by-row loop
+    ii, jj = [], []
+    for i in range(n):
+        jj.append(np.arange(n - i))
+        ii.append(np.full(n - i, i))
+    ii, jj = np.concatenate(ii), np.concatenate(jj)
+    down = jj < n - ii - 1
     for fi, (a, b, c_) in enumerate(F):
         A, B, C = V[a], V[b], V[c_]
-        tri = []
-        for i in range(n):
-            for j in range(n - i):
-                p = lambda u, v: A + (B - A) * u / n + (C - A) * v / n
-                tri.append([p(i, j), p(i + 1, j), p(i, j + 1)])
-                if j < n - i - 1:
-                    tri.append([p(i + 1, j), p(i + 1, j + 1), p(i, j + 1)])
-        soup.add(np.array(tri), 0, soup.new_surface())
+        p = lambda u, v: A + (B - A) * (u[:, None] / n) + (C - A) * (v[:, None] / n)
+        up_t = np.stack([p(ii, jj), p(ii + 1, jj), p(ii, jj + 1)], axis=1)
+        dn_t = np.stack([p(ii + 1, jj), p(ii + 1, jj + 1), p(ii, jj + 1)], axis=1)
+        # interleave: up(i, j), down(i, j) where it exists
+        order = np.argsort(np.concatenate([2 * np.arange(len(ii)), 2 * np.nonzero(down)[0] + 1]), kind="stable")
+        tri = np.concatenate([up_t, dn_t[down]])[order]
+        soup.add(tri, 0, soup.new_surface())
     M = 4 * 4 ** level
     return _scene("tetra", soup, np.full((1, N_BANDS), 0.1), np.zeros(N_BANDS), [(0, 0, 0)],
                   [(0.3, 0.1, 0.05)], [0.05], [0], n_rays or M, n_bounces)

@@ -256,6 +256,29 @@ def test_lroom_subset_against_oracle_tree():
     _check_free_running(sc, hist, ids, tr)
 
 
+@pytest.mark.parametrize("level", [5, 9])
+def test_tetra_scaling_workload_one_iteration(level):
+    """The paper's scaling workload (Sec. 2.2, Table 2): one iteration with
+    N = M rays from the centre of the refined unit tetrahedron.  Every query
+    agrees with the oracle (brute force at 4,096 faces, its tree on a sample
+    of 20,000 queries at 1,048,576 faces) except near-ties, and a closed mesh
+    lets no ray escape."""
+    sc = scenes.tetra(level)
+    M = len(sc.tris)
+    assert M == 4 * 4 ** level and sc.n_rays == M and sc.n_bounces == 1
+    ds_t = torch.empty((1, M, 6), dtype=torch.float32, device="cuda")
+    dt_t = torch.empty((1, M), dtype=torch.float32, device="cuda")
+    tree, isrc = _trace(sc, debug_state=ds_t, debug_t=dt_t)
+    hist = isrc.hist.cpu().numpy()
+    assert isrc.queries == M and (hist >= 0).all()
+    osc = oracle.OracleScene(sc, tree=level > 5)
+    pick = None
+    if level > 5:
+        rng = np.random.default_rng(7)
+        pick = np.stack([np.zeros(20_000, np.int64), np.sort(rng.choice(M, 20_000, replace=False))], 1)
+    _check_lockstep(sc, osc, ds_t.cpu().numpy(), dt_t.cpu().numpy(), hist, pick)
+
+
 def test_theatre_lockstep_and_free_running():
     sc = scenes.theatre()                                    # 436,796 triangles, 1M rays, 30 bounces
     B, N = sc.n_bounces, sc.n_rays
