@@ -161,6 +161,7 @@ typedef struct {
     float ms_rays;             /* device time of ray generation (CUDA events) */
     float ms_bounces;          /* device time of all bounce launches */
     float ms_image_sources;    /* device time of dedup + FP64 reconstruction */
+    int32_t n_rcv;             /* receivers of the trace (all rooms of a batch) */
 } rt_is_view;
 
 typedef struct {
@@ -294,6 +295,45 @@ rt_status rt_mlp_set_step(rt_mlp* net, int64_t step);
  * n_bins > 0, dt > 0, t0 >= 0 are checked (RT_ERR_INVALID_ARG). */
 rt_status rt_tail_prior(const float* rates, const float* air, const float* level, int32_t n, int32_t n_nodes,
                         float t0, float dt, int32_t n_bins, float* out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * What the impulse responses feed (Sec. 1.4 and the perceptive factors of
+ * Sec. 4).  The paper names the metrics and the octave-band FIR synthesis
+ * without formulas; these are the usual definitions, on a histogram of
+ * energies e[b] per bin [b / fs, (b + 1) / fs):
+ *   E = sum e;  S[b] = sum_{b' >= b} e[b'];  L[b] = 10 log10 (S[b] / E) at t = b / fs
+ *   b0 = first bin with e > 0 (the direct sound); n80 = ceil(0.08 fs), n50 = ceil(0.05 fs)
+ *   EDT, T20, T30: -60 / slope of the least-squares line through the (t, L)
+ *     of the bins b >= b0 with L in [0, -10], [-5, -25], [-5, -35] dB
+ *     (seconds; NaN when no finite L reaches the lower limit, fewer than 2
+ *     points qualify, or the slope is not negative)
+ *   C80 = 10 log10 (sum_{b - b0 < n80} e / sum_{b - b0 >= n80} e) dB (+inf without late energy)
+ *   D50 = sum_{b - b0 < n50} e / E;  Ts = sum ((b - b0 + 1/2) / fs) e / E seconds
+ *   SPL = 10 log10 E, dB re the source energy (E_0 = 1)
+ * ------------------------------------------------------------------------- */
+#define RT_N_ROOM_PARAMS 7   /* EDT, T20, T30, C80, D50, Ts, SPL */
+
+/* Parameters of device histograms H [n_rcv][8][n_bins] (float, e.g. an
+ * rt_response's data) into host out [n_rcv][8][RT_N_ROOM_PARAMS] (FP64 sums,
+ * fixed order: the same result on every run).  A band without energy gets
+ * NaN throughout.  Synchronises `stream`.  0 < n_rcv <= 65535, n_bins > 0,
+ * fs > 0 (RT_ERR_INVALID_ARG otherwise). */
+rt_status rt_room_parameters(const float* H, int32_t n_rcv, int64_t n_bins, double fs, double* out,
+                             void* stream);
+
+/* Pressure impulse responses of image sources (p = sqrt(E) per image source,
+ * Sec. 1.4), synthesised over the 8 octave bands:
+ *   p[k][t] = sum_{s of receiver k} sum_f sqrt(E_s(f)) g_f[t - floor(t_s fs) + D]
+ * for t in [0, n_out), with g_f the linear-phase octave band-pass filter of
+ * band f (centre 62.5 Hz * 2^f, edges f_c / sqrt 2 and f_c sqrt 2): the
+ * difference of two ideal low-pass sincs 2 F / fs sinc(2 F (n - D) / fs) for
+ * the two edges, times the Hann window 1/2 (1 - cos(2 pi n / (n_taps - 1))),
+ * n = 0 .. n_taps - 1, D = (n_taps - 1) / 2 (zero-phase alignment on the
+ * arrival bin).  out: device float [n_rcv][n_out], every sample written; sums
+ * in FP64 over the sources in (arrival bin, index) order.  Synchronises
+ * `stream`.  fs > 0, 0 < n_out < 2^31, odd 3 <= n_taps <= 2^20. */
+rt_status rt_pressure_rir(const rt_image_sources* is, double fs, int64_t n_out, int32_t n_taps, float* out,
+                          void* stream);
 
 /* Workspace: queues and counters kept between traces on one stream, and the
  * CUDA graph of the bounce loop.  Free it after its last trace finished. */

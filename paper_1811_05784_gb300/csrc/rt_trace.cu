@@ -1448,6 +1448,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     cudaEventElapsedTime(&v.ms_rays, ev.e[0], ev.e[1]);
     v.ms_bounces = ms_bounce;
     if (nr > 0) cudaEventElapsedTime(&v.ms_image_sources, ev.e[2], ev.e[3]);
+    v.n_rcv = is->n_rcv;
     cudaGetLastError();
     is->owned = keep.release();
     for (void* ptr : rec_arena.release()) is->owned.push_back(ptr);

@@ -33,7 +33,8 @@ EXPORTED = ["rt_build_tree", "rt_tree_free", "rt_tree_info", "rt_trace", "rt_tra
             "rt_response_free",
             "rt_last_error", "rt_api_version", "rt_launch_count", "rt_measure_l2_bandwidth", "rt_set_allocator",
             "rt_mlp_create", "rt_mlp_free", "rt_mlp_info", "rt_mlp_forward", "rt_mlp_gradients", "rt_mlp_train_step",
-            "rt_mlp_copy", "rt_mlp_set_weight_decay", "rt_mlp_get_step", "rt_mlp_set_step", "rt_tail_prior"]
+            "rt_mlp_copy", "rt_mlp_set_weight_decay", "rt_mlp_get_step", "rt_mlp_set_step", "rt_tail_prior",
+            "rt_room_parameters", "rt_pressure_rir"]
 
 
 class RtError(RuntimeError):
@@ -77,7 +78,8 @@ class rt_is_view(C.Structure):
                 ("hist", P), ("ray_energy", P), ("ray_length", P), ("ray_hits", P), ("n_records", C.c_int64),
                 ("rec_rcv", P), ("rec_ray", P), ("rec_order", P), ("rec_length", P), ("queries", C.c_int64),
                 ("hash_collisions", C.c_int64), ("block_size", C.c_int32), ("tail_rays", C.c_int64),
-                ("ms_rays", C.c_float), ("ms_bounces", C.c_float), ("ms_image_sources", C.c_float)]
+                ("ms_rays", C.c_float), ("ms_bounces", C.c_float), ("ms_image_sources", C.c_float),
+                ("n_rcv", C.c_int32)]
 
 
 class rt_response_view(C.Structure):
@@ -154,6 +156,10 @@ def lib():
             L.rt_mlp_get_step.argtypes = [P, C.POINTER(C.c_int64)]
             L.rt_mlp_set_step.restype = st
             L.rt_mlp_set_step.argtypes = [P, C.c_int64]
+            L.rt_room_parameters.restype = st
+            L.rt_room_parameters.argtypes = [P, C.c_int32, C.c_int64, C.c_double, P, P]
+            L.rt_pressure_rir.restype = st
+            L.rt_pressure_rir.argtypes = [P, C.c_double, C.c_int64, C.c_int32, P, P]
             L.rt_tail_prior.restype = st
             L.rt_tail_prior.argtypes = [P, P, P, C.c_int32, C.c_int32, C.c_float, C.c_float, C.c_int32, P, P]
             L.rt_set_allocator.restype = st
@@ -180,6 +186,33 @@ def rt_measure_l2_bandwidth(stream=None) -> float:
     v = C.c_double()
     _check(lib().rt_measure_l2_bandwidth(C.byref(v), _stream_ptr(stream)))
     return v.value
+
+
+ROOM_PARAMS = ("EDT", "T20", "T30", "C80", "D50", "Ts", "SPL")
+
+
+def rt_room_parameters(H, fs, stream=None):
+    """Room-acoustic parameters [n_rcv][8][7] (numpy, ROOM_PARAMS order) of
+    CUDA histograms H [n_rcv][8][n_bins] (e.g. Response.data)."""
+    H = H.contiguous().float()
+    R, nb = int(H.shape[0]), int(H.shape[-1])
+    if H.dim() != 3 or H.shape[1] != N_BANDS:
+        raise ValueError("rt_room_parameters: histograms [n_rcv][8][n_bins]")
+    out = np.zeros((R, N_BANDS, len(ROOM_PARAMS)), np.float64)
+    _check(lib().rt_room_parameters(P(H.data_ptr()), R, nb, float(fs), out.ctypes.data_as(P), _stream_ptr(stream)))
+    return out
+
+
+def rt_pressure_rir(image_sources, fs, n_out, n_taps=4095, out=None, stream=None):
+    """Pressure responses [n_rcv][n_out] (CUDA float tensor) of image sources,
+    synthesised with octave-band FIR filters of n_taps (odd) taps."""
+    import torch
+    R = image_sources.n_rcv
+    if out is None:
+        out = torch.empty((R, int(n_out)), dtype=torch.float32, device="cuda")
+    _check(lib().rt_pressure_rir(image_sources._h, float(fs), int(n_out), int(n_taps), P(out.data_ptr()),
+                                 _stream_ptr(stream)))
+    return out
 
 
 def rt_tail_prior(rates, air, level, n_nodes, t0, dt, n_bins, out=None, stream=None):
@@ -319,6 +352,7 @@ class ImageSources:
         self.hash_collisions = v.hash_collisions
         self.ms_rays, self.ms_bounces, self.ms_image_sources = v.ms_rays, v.ms_bounces, v.ms_image_sources
         self.block_size, self.tail_rays = v.block_size, v.tail_rays
+        self.n_rcv = v.n_rcv
 
     def __getattr__(self, name):
         f = ImageSources._FIELDS.get(name)
