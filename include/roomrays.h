@@ -117,6 +117,16 @@ typedef struct {
                                 non-default stream the bounce loop then runs as one CUDA
                                 graph launch (captured on the first call, parameters
                                 updated on later ones) */
+    const int32_t* replay_hist; /* NULL, or the hit history (rt_is_view.hist, device
+                                [n_bounces][n_traced]) of an earlier trace of the same rays:
+                                same trees, sources, n_rays, ray_begin / ray_count,
+                                n_bounces, max_distance, air and c; the receivers may differ.
+                                Each query then re-tests only the recorded triangle (no
+                                traversal), so a moved or added listener costs a fraction of
+                                a trace and gives exactly what a full trace with the new
+                                receivers gives.  A recorded id outside the mesh is reported
+                                (RT_ERR_INTERNAL); a history of other rays gives other
+                                (meaningless) paths. */
 } rt_trace_params;
 
 #define RT_TAIL_AUTOTUNE (-2)

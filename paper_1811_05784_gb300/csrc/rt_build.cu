@@ -418,23 +418,26 @@ __global__ void k_emit_wide(int64_t n_int, const int32_t* __restrict__ left, con
 }
 
 // single-triangle mesh: one 4-wide node holding one leaf
-__global__ void k_single(const float4* __restrict__ tv, float4* __restrict__ nodes, float4* __restrict__ tris) {
+__global__ void k_single(const float4* __restrict__ tv, float4* __restrict__ nodes, float4* __restrict__ tris,
+                         int32_t* __restrict__ pos_of) {
     Box b = tri_box(tv, 0);
     WideChild c;
     c.lo = make_float4(b.lo[0], b.lo[1], b.lo[2], 0.f);
     c.hi = make_float4(b.hi[0], b.hi[1], b.hi[2], 0.f);
     c.ref = leaf_ref(0, 1);
     store_wide(nodes, &c, 1);
+    pos_of[0] = 0;
     tris[0] = tv[0];
     tris[1] = tv[1];
     tris[2] = tv[2];
 }
 
 __global__ void k_reorder(const float4* __restrict__ tv, const uint32_t* __restrict__ order, int64_t M,
-                          float4* __restrict__ tris) {
+                          float4* __restrict__ tris, int32_t* __restrict__ pos_of) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
     int64_t t = order[j];
+    pos_of[t] = (int32_t)j;
     tris[3 * j] = tv[3 * t];
     tris[3 * j + 1] = tv[3 * t + 1];
     tris[3 * j + 2] = tv[3 * t + 2];
@@ -566,11 +569,13 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out) 
 
     float4* tris;
     RR_TRY(keep_arena.alloc(&tris, 3 * M));
+    int32_t* pos_of;
+    RR_TRY(keep_arena.alloc(&pos_of, M));
     float4* nodes;
     uint32_t* total = nullptr;
     if (M == 1) {
         RR_TRY(keep_arena.alloc(&nodes, 8));
-        RR_LAUNCH(k_single, 1, 1, 0, s, tv, nodes, tris);
+        RR_LAUNCH(k_single, 1, 1, 0, s, tv, nodes, tris, pos_of);
         RR_CUDA(cudaGetLastError());
     } else {
         const int64_t NI = M - 1;
@@ -608,7 +613,7 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out) 
         RR_TRY(keep_arena.alloc(&nodes, 8 * NI));
         RR_LAUNCH(k_emit_wide, grid_of(NI, 256), 256, 0, s, NI, left, right, first, last, keep, keep4, newidx,
                   leaf_box, node_box, nodes);
-        RR_LAUNCH(k_reorder, grid_of(M, 256), 256, 0, s, tv, vals, M, tris);
+        RR_LAUNCH(k_reorder, grid_of(M, 256), 256, 0, s, tv, vals, M, tris, pos_of);
         RR_CUDA(cudaGetLastError());
     }
     uint32_t nn = 1;
@@ -666,6 +671,7 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out) 
     tree->tris = tris;
     tree->tri_nrm = tri_nrm;
     tree->surf_of = surf_of;
+    tree->pos_of = pos_of;
     tree->mat_of_surf = mat_of_surf;
     tree->planes = planes;
     float lo[3], hi[3];

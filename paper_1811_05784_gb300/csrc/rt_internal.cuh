@@ -124,6 +124,7 @@ struct rt_tree {
     float4* tris = nullptr;       // [n_tris][3] tree order: v0 (w = id), v1 (w = surface id), v2
     float4* tri_nrm = nullptr;    // [n_tris] by id: unit normal (float32 of FP64), w = surface id bits
     int32_t* surf_of = nullptr;   // [n_tris] by id
+    int32_t* pos_of = nullptr;    // [n_tris] by id: position of the triangle in tree order
     int32_t* mat_of_surf = nullptr;  // [n_surfaces]
     Plane* planes = nullptr;      // [n_surfaces] FP64 plane n.x = d
     std::vector<void*> owned;

@@ -65,6 +65,7 @@ struct RoomDev {
     const int32_t* mat_of_surf;
     const int32_t* surf_of;
     const Plane* planes;
+    const int32_t* pos_of;  // triangle id -> position in tree order
     int64_t n_nodes, n_tris;
     int32_t mat_base;
     int32_t pad;
@@ -102,6 +103,7 @@ struct BounceArgs {
     float* debug_t;
     float* debug_state;
     int32_t* debug_cost;
+    const int32_t* __restrict__ replay;  // [B][n_traced] hits of an earlier trace of the same rays, or null
 };
 
 // ---------------------------------------------------------------------------
@@ -381,6 +383,28 @@ __device__ __forceinline__ void nearest_hit(const BounceArgs& a, const RoomDev& 
     if (best_id == 0x7FFFFFFF) best_id = -1;
 }
 
+// Replay of a recorded query: the triangle an earlier trace of this ray hit
+// at this bounce is tested alone (the same watertight test, so the same
+// distance); -1 (an escape) stays an escape.  Ids outside the mesh are
+// reported (ST_BOUNDS) and read as escapes.
+__device__ __forceinline__ void replay_hit(const BounceArgs& a, const RoomDev& rm, const RayPre& r, int exclude,
+                                           int bb, int q, float& best_t, int& best_id, unsigned int& err,
+                                           int& n_tests) {
+    best_t = INFINITY;
+    best_id = 0x7FFFFFFF;
+    const int tri = a.replay[(int64_t)bb * a.n_traced + q];
+    if (tri >= 0) {
+        const int j = (int64_t)tri < rm.n_tris ? rm.pos_of[tri] : -1;
+        if (j < 0 || (int64_t)j >= rm.n_tris) {
+            err |= ST_BOUNDS;
+        } else {
+            tri_test(r, rm.tris + 3 * (int64_t)j, exclude, best_t, best_id);
+            n_tests = 1;
+        }
+    }
+    if (best_id == 0x7FFFFFFF) best_id = -1;
+}
+
 struct RayState {
     float4 o, d, e0, e1;
     uint4 m;
@@ -396,7 +420,7 @@ __device__ __forceinline__ void load_ray(const Queue& q, unsigned int slot, RayS
 
 // One bounce of the ray in s (bounce index bb).  Every lane of the warp calls
 // it; lanes without a ray pass active = false.  Returns true if the ray goes on.
-template <int BT>
+template <int BT, bool REPLAY>
 __device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool active, int bb, RayState& s,
                                          int* __restrict__ stack) {
     const int q = (int)s.m.x;
@@ -408,7 +432,12 @@ __device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool act
     float4 o4 = s.o, d4 = s.d;
     RayPre rp = ray_pre(make_float3(o4.x, o4.y, o4.z), make_float3(d4.x, d4.y, d4.z));
     int n_nodes = 0, n_tests = 0;
-    if (active) nearest_hit<BT>(a, rm, rp, (int)s.m.y, best_t, hit, err, n_nodes, n_tests, stack);
+    if (active) {
+        if (REPLAY)  // the query re-tests the triangle an earlier trace recorded
+            replay_hit(a, rm, rp, (int)s.m.y, bb, q, best_t, hit, err, n_tests);
+        else
+            nearest_hit<BT>(a, rm, rp, (int)s.m.y, best_t, hit, err, n_nodes, n_tests, stack);
+    }
     if (err) atomicOr(a.status, err);
     const unsigned int amask = __ballot_sync(0xffffffffu, active);
     if (lane == 0 && amask) atomicAdd(a.n_queries, (unsigned long long)__popc(amask));
@@ -519,7 +548,7 @@ __device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool act
 //   wait for their slowest ray.  It writes no survivors, so the later
 //   launches of the same trace find no live rays and return at once.
 // ---------------------------------------------------------------------------
-template <int BT>
+template <int BT, bool REPLAY>
 __global__ void __launch_bounds__(BT) k_bounce(BounceArgs a) {
     extern __shared__ int s_stack[];  // STACK_SMEM * BT entries (stack_bytes)
     int* stack = s_stack + threadIdx.x;
@@ -541,7 +570,7 @@ __global__ void __launch_bounds__(BT) k_bounce(BounceArgs a) {
             s.e0 = s.e1 = s.o;
             s.m = make_uint4(0, 0xFFFFFFFFu, 0, 0);
             if (active) load_ray(a.in, slot, s);
-            const bool survive = step_ray<BT>(a, lane, active, b, s, stack);
+            const bool survive = step_ray<BT, REPLAY>(a, lane, active, b, s, stack);
             const unsigned int mask = __ballot_sync(0xffffffffu, survive);
             if (mask) {
                 unsigned int obase = 0;
@@ -586,7 +615,7 @@ __global__ void __launch_bounds__(BT) k_bounce(BounceArgs a) {
             exhausted = base + __popc(need) >= n_live;
         }
         if (__ballot_sync(0xffffffffu, has) == 0) break;
-        const bool survive = step_ray<BT>(a, lane, has, bb, s, stack);
+        const bool survive = step_ray<BT, REPLAY>(a, lane, has, bb, s, stack);
         if (has) {
             if (survive)
                 bb++;
@@ -832,18 +861,18 @@ static void tune_report(const std::string& key, int cand, float ms) {
 // dynamic shared memory of a bounce launch: the traversal stacks
 static size_t stack_bytes(int block) { return sizeof(int) * (size_t)STACK_SMEM * (size_t)block; }
 
-static void* kernel_of(int block) {
+static void* kernel_of(int block, bool replay = false) {
     switch (block) {
-        case 64: return (void*)k_bounce<64>;
-        case 256: return (void*)k_bounce<256>;
-        default: return (void*)k_bounce<128>;
+        case 64: return replay ? (void*)k_bounce<64, true> : (void*)k_bounce<64, false>;
+        case 256: return replay ? (void*)k_bounce<256, true> : (void*)k_bounce<256, false>;
+        default: return replay ? (void*)k_bounce<128, true> : (void*)k_bounce<128, false>;
     }
 }
 
 // allow the stacks above the 48 KB default (the 256-thread block needs 64 KB);
 // a function attribute of the current device, set before any launch or capture
-static rt_status allow_stack_smem(int block) {
-    RR_CUDA(cudaFuncSetAttribute(kernel_of(block), cudaFuncAttributeMaxDynamicSharedMemorySize,
+static rt_status allow_stack_smem(int block, bool replay = false) {
+    RR_CUDA(cudaFuncSetAttribute(kernel_of(block, replay), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)stack_bytes(block)));
     return RT_OK;
 }
@@ -852,7 +881,7 @@ template <int BT>
 static int occupancy_grid() {
     int occ = 0;
     if (allow_stack_smem(BT) == RT_OK)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bounce<BT>, BT, stack_bytes(BT));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bounce<BT, false>, BT, stack_bytes(BT));
     cudaGetLastError();
     return device_sm_count() * (occ > 0 ? occ : 1);
 }
@@ -880,6 +909,7 @@ struct rt_workspace {
     cudaGraph_t graph = nullptr;
     std::vector<cudaGraphNode_t> nodes;
     int g_b = 0, g_grid = 0, g_block = 0;
+    bool g_replay = false;
     long long graph_launches = 0;
     unsigned long long last_records = 0;  // capacity hint for the next trace
 
@@ -905,9 +935,10 @@ namespace rr {
 // kernel parameters (one graph launch per trace).
 static rt_status run_bounces(BounceArgs a, const Queue q[2], int B, int block, int grid, cudaStream_t s,
                              rt_workspace* ws) {
-    void* kern = kernel_of(block);
+    const bool replay = a.replay != nullptr;
+    void* kern = kernel_of(block, replay);
     const size_t smem = stack_bytes(block);
-    RR_TRY(allow_stack_smem(block));
+    RR_TRY(allow_stack_smem(block, replay));
     std::vector<BounceArgs> args((size_t)B, a);
     for (int b = 0; b < B; b++) {
         args[b].b = b;
@@ -926,7 +957,7 @@ static rt_status run_bounces(BounceArgs a, const Queue q[2], int B, int block, i
         }
         return RT_OK;
     }
-    if (!ws->exec || ws->g_b != B || ws->g_grid != grid || ws->g_block != block) {
+    if (!ws->exec || ws->g_b != B || ws->g_grid != grid || ws->g_block != block || ws->g_replay != replay) {
         ws->release_graph();
         RR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         for (int b = 0; b < B; b++) {
@@ -954,6 +985,7 @@ static rt_status run_bounces(BounceArgs a, const Queue q[2], int B, int block, i
         ws->g_b = B;
         ws->g_grid = grid;
         ws->g_block = block;
+        ws->g_replay = replay;
     } else {
         for (int b = 0; b < B; b++) {
             cudaKernelNodeParams kp{};
@@ -1064,6 +1096,7 @@ static rt_status gather_rooms(const rt_room* rooms, int n_rooms, HostRoomTables&
         d.mat_of_surf = rm.tree->mat_of_surf;
         d.surf_of = rm.tree->surf_of;
         d.planes = rm.tree->planes;
+        d.pos_of = rm.tree->pos_of;
         d.n_nodes = rm.tree->n_nodes;
         d.n_tris = rm.tree->n_tris;
         d.mat_base = mat_base;
@@ -1211,7 +1244,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     int block = p->block_size > 0 ? p->block_size : 128;
     int tail_mode = p->tail_rays < 0 ? 0 : 1;
     if (autotune) {
-        key = tune_key(h.total_tris, n_traced, B, n_rooms);
+        key = tune_key(h.total_tris, n_traced, B, n_rooms) + (p->replay_hist ? "_replay" : "");
         cand = tune_pick(key);
         block = CANDIDATES[cand].block;
         tail_mode = CANDIDATES[cand].tail_mode;
@@ -1296,6 +1329,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
         a.debug_t = p->debug_t;
         a.debug_state = p->debug_state;
         a.debug_cost = p->debug_cost;
+        a.replay = p->replay_hist;
         RR_TRY(run_bounces(a, q, B, block, grid, s, ws));
         RR_CUDA(cudaGetLastError());
         RR_CUDA(cudaEventRecord(ev.e[2], s));
@@ -1310,7 +1344,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
             return RT_ERR_STACK;
         }
         if (st & ST_BOUNDS) {
-            set_error("rt_trace: traversal met a node or leaf reference outside the tree");
+            set_error("rt_trace: a node, leaf or replayed triangle reference lies outside the tree");
             return RT_ERR_INTERNAL;
         }
         if (st & ST_STEPS) {

@@ -64,7 +64,19 @@ class rt_trace_params(C.Structure):
                 ("n_bounces", C.c_int32), ("max_distance", C.c_double), ("air_beta", P), ("c", C.c_double),
                 ("block_size", C.c_int32), ("max_node_visits", C.c_int32), ("tail_rays", C.c_int32),
                 ("stream", P), ("debug_t", P),
-                ("debug_state", P), ("debug_cost", P), ("workspace", P)]
+                ("debug_state", P), ("debug_cost", P), ("workspace", P), ("replay_hist", P)]
+
+
+def _replay_ptr(replay):
+    """Hit history of an earlier trace: an ImageSources or a CUDA int32 tensor
+    [n_bounces][n_traced]."""
+    if replay is None:
+        return None
+    if isinstance(replay, ImageSources):
+        return P(replay.view.hist)
+    if not (_is_cuda_tensor(replay) and str(replay.dtype) == "torch.int32" and replay.is_contiguous()):
+        raise ValueError("replay: an ImageSources or a contiguous CUDA int32 tensor [n_bounces][n_traced]")
+    return P(replay.data_ptr())
 
 
 class rt_room(C.Structure):
@@ -378,8 +390,10 @@ class ImageSources:
 def rt_trace(tree: Tree, sources, rcv_center, rcv_radius, rcv_source, band_absorption, n_rays, n_bounces,
              ray_begin=0, ray_count=0, max_distance=0.0, air_beta=None, c=343.2, block_size=0,
              max_node_visits=0, tail_rays=0, stream=None, debug_t=None, debug_state=None,
-             debug_cost=None, workspace=None) -> ImageSources:
-    """Propagate rays and build image sources (host inputs; see roomrays.h)."""
+             debug_cost=None, workspace=None, replay=None) -> ImageSources:
+    """Propagate rays and build image sources (host inputs; see roomrays.h).
+    replay: the result (or its hist) of an earlier trace of the same rays --
+    the queries then re-test the recorded triangles, for new receivers."""
     src, ps = _host(np.asarray(sources, np.float64).reshape(-1, 3), np.float64)
     rc, prc = _host(np.asarray(rcv_center, np.float64).reshape(-1, 3), np.float64)
     rr, prr = _host(np.asarray(rcv_radius, np.float64).reshape(-1), np.float64)
@@ -396,7 +410,7 @@ def rt_trace(tree: Tree, sources, rcv_center, rcv_radius, rcv_source, band_absor
                           P(debug_t.data_ptr()) if debug_t is not None else None,
                           P(debug_state.data_ptr()) if debug_state is not None else None,
                           P(debug_cost.data_ptr()) if debug_cost is not None else None,
-                          workspace._h if workspace is not None else None)
+                          workspace._h if workspace is not None else None, _replay_ptr(replay))
     out = P()
     _check(lib().rt_trace(tree._h, C.byref(S), C.byref(R), pal, len(al), C.byref(prm), C.byref(out)))
     res = ImageSources(out)
@@ -466,10 +480,12 @@ class Workspace:
 
 
 def rt_trace_batch(rooms, n_rays, n_bounces, ray_begin=0, ray_count=0, max_distance=0.0, air_beta=None, c=343.2,
-                   block_size=0, max_node_visits=0, tail_rays=0, stream=None, workspace=None) -> ImageSources:
+                   block_size=0, max_node_visits=0, tail_rays=0, stream=None, workspace=None,
+                   replay=None) -> ImageSources:
     """Trace many rooms in one persistent launch.  `rooms` is a list of dicts
     with keys tree, sources, rcv_center, rcv_radius, rcv_source,
-    band_absorption.  Receivers are numbered room after room."""
+    band_absorption.  Receivers are numbered room after room.  replay: see
+    rt_trace."""
     keep, arr = [], (rt_room * len(rooms))()
     n_rcv = 0
     for k, r in enumerate(rooms):
@@ -487,7 +503,7 @@ def rt_trace_batch(rooms, n_rays, n_bounces, ray_begin=0, ray_count=0, max_dista
         be, pbe = None, None
     prm = rt_trace_params(int(n_rays), int(ray_begin), int(ray_count), int(n_bounces), float(max_distance), pbe,
                           float(c), int(block_size), int(max_node_visits), int(tail_rays), _stream_ptr(stream),
-                          None, None, None, workspace._h if workspace is not None else None)
+                          None, None, None, workspace._h if workspace is not None else None, _replay_ptr(replay))
     out = P()
     _check(lib().rt_trace_batch(arr, len(rooms), C.byref(prm), C.byref(out)))
     res = ImageSources(out)

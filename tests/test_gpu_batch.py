@@ -72,6 +72,25 @@ def test_batched_config_rooms_match_single_rooms():
     assert batch.n > 0
 
 
+def test_batch_replay_with_moved_listeners():
+    scs = scenes.batched_rooms(n_rooms=6, pairs=3, n_rays=4096, n_bounces=12)
+    trees = [_tree(sc) for sc in scs]
+
+    def rooms(move):
+        out = []
+        for t, sc in zip(trees, scs):
+            c = sc.rcv_center + (np.float32(0.4) if move else np.float32(0))
+            out.append(dict(tree=t, sources=sc.sources, rcv_center=c, rcv_radius=sc.rcv_radius,
+                            rcv_source=sc.rcv_source, band_absorption=sc.alpha))
+        return out
+
+    first = rt.rt_trace_batch(rooms(False), 4096, 12)
+    full = rt.rt_trace_batch(rooms(True), 4096, 12)
+    rep = rt.rt_trace_batch(rooms(True), 4096, 12, replay=first)
+    for name in ("hist", "ray_energy", "rcv", "order", "count", "rep_ray", "pos", "time", "energy"):
+        assert torch.equal(getattr(full, name), getattr(rep, name)), name
+
+
 def test_workspace_graph_replays_give_identical_results():
     sc = scenes.theatre(n_rays=100_000)
     tree = _tree(sc)

@@ -279,6 +279,52 @@ def test_tetra_scaling_workload_one_iteration(level):
     _check_lockstep(sc, osc, ds_t.cpu().numpy(), dt_t.cpu().numpy(), hist, pick)
 
 
+def _moved_listeners(sc):
+    """The scene with its receivers moved and one added (all of source 0)."""
+    import copy
+    m = copy.copy(sc)
+    lo, hi = sc.vertices.min(0), sc.vertices.max(0)
+    g = np.random.default_rng(3)
+    n = len(sc.rcv_center) + 1
+    m.rcv_center = g.uniform(lo + 0.25 * (hi - lo), hi - 0.25 * (hi - lo), (n, 3)).astype(np.float32)
+    m.rcv_radius = g.uniform(0.3, 1.5, n).astype(np.float32)
+    m.rcv_source = np.zeros(n, np.int32)
+    return m
+
+
+def _same_trace(a, b):
+    for name in ("hist", "ray_energy", "ray_length", "ray_hits", "rcv", "order", "count", "rep_ray", "pos",
+                 "dist", "time", "energy"):
+        assert torch.equal(getattr(a, name), getattr(b, name)), name
+    assert a.n == b.n and a.n_records == b.n_records and a.queries == b.queries
+
+
+@pytest.mark.parametrize("scene,tail", [("shoebox", 0), ("shoebox", -1), ("theatre", 0)])
+def test_replay_with_moved_listeners_equals_a_full_trace(scene, tail):
+    """A moved listener: the recorded paths of an earlier trace replayed
+    (only the recorded triangle re-tested per query) give exactly what a
+    full trace with the new receivers gives."""
+    sc = scenes.shoebox(n_rays=20_000, n_bounces=25) if scene == "shoebox" else scenes.theatre(n_rays=100_000)
+    tree, first = _trace(sc, tail_rays=tail)
+    moved = _moved_listeners(sc)
+    kw = rt.scene_args(moved)
+    full = rt.rt_trace(tree, tail_rays=tail, **kw)
+    replay = rt.rt_trace(tree, tail_rays=tail, replay=first, **kw)
+    _same_trace(full, replay)
+    assert replay.n > 0
+    # replaying the replay (the same rays) again changes nothing
+    _same_trace(full, rt.rt_trace(tree, tail_rays=tail, replay=replay.hist.contiguous(), **kw))
+
+
+def test_replay_reports_foreign_histories():
+    sc = scenes.shoebox(n_rays=2_000, n_bounces=5)
+    tree, first = _trace(sc)
+    bad = first.hist.clone()
+    bad[2, 17] = len(sc.tris) + 5                     # an id outside this mesh
+    with pytest.raises(rt.RtError, match="outside the tree"):
+        rt.rt_trace(tree, replay=bad, **rt.scene_args(sc))
+
+
 def test_theatre_lockstep_and_free_running():
     sc = scenes.theatre()                                    # 436,796 triangles, 1M rays, 30 bounces
     B, N = sc.n_bounces, sc.n_rays
