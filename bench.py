@@ -60,10 +60,11 @@ def parse():
     ap.add_argument("--cpu-sample-rays", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--clock-log", default=None, help="keep the nvidia-smi samples of the timed region here")
-    ap.add_argument("--workload", choices=["theatre", "batched", "tetra"], default="theatre",
+    ap.add_argument("--workload", choices=["theatre", "batched", "tetra", "trees"], default="theatre",
                     help="theatre: the headline line; batched: 64 rooms x 16 pairs x 262,144 rays x 30 bounces "
                          "in batched launches; tetra: the N = M scaling sweep of one iteration on the refined "
-                         "tetrahedron (each its own line, one GPU)")
+                         "tetrahedron; trees: the LBVH against the paper's median-split tree "
+                         "(each its own line, one GPU)")
     ap.add_argument("--batch-chunk", type=int, default=65_536, help="rays per pair per batched launch")
     return ap.parse_args()
 
@@ -503,6 +504,53 @@ def run_tetra(args):
                       "sweep": rows}))
 
 
+def run_trees(args):
+    """The LBVH against the paper's median-split tree on the same meshes and
+    rays: build time, node visits and triangle tests per query, bounce-loop
+    time (the same 4-wide traversal kernel)."""
+    import torch
+    from paper_1811_05784_gb300 import rt
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream()
+    rows = []
+    for name, make in (("theatre", lambda: scenes.theatre(n_rays=N_RAYS, n_bounces=N_BOUNCES)),
+                       ("lroom", lambda: scenes.lroom(n_rays=N_RAYS, n_bounces=50)),
+                       ("tetra 2^20, 1 bounce", lambda: scenes.tetra(9))):
+        sc = make()
+        kw = rt.scene_args(sc)
+        mesh = tuple(torch.as_tensor(x, device=dev) for x in (sc.vertices, sc.tris, sc.material_id, sc.surface_id))
+        for median in (False, True):
+            with torch.cuda.stream(stream):
+                for _ in range(max(args.warmup, 1)):
+                    tree = rt.rt_build_tree(*mesh, stream=stream, median=median)
+                    rt.rt_trace(tree, tail_rays=N_RAYS, block_size=256, stream=stream, **kw)
+                torch.cuda.synchronize()
+                b_ms, q_ms = [], []
+                for _ in range(args.steps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    tree = rt.rt_build_tree(*mesh, stream=stream, median=median)
+                    e1.record(stream)
+                    isrc = rt.rt_trace(tree, tail_rays=N_RAYS, block_size=256, stream=stream, **kw)
+                    torch.cuda.synchronize()
+                    b_ms.append(e0.elapsed_time(e1))
+                    q_ms.append(isrc.ms_bounces)
+                cost = torch.zeros((sc.n_bounces, isrc.n_traced, 2), dtype=torch.int32, device=dev)
+                isrc = rt.rt_trace(tree, tail_rays=N_RAYS, block_size=256, stream=stream, debug_cost=cost, **kw)
+                torch.cuda.synchronize()
+                c = cost.double().sum((0, 1)).cpu().numpy()
+                del cost
+            info = tree.info()
+            rows.append({"mesh": name, "tris": len(sc.tris), "tree": "median split" if median else "LBVH",
+                         "depth": info["depth"], "wide_nodes": info["n_nodes"], "build_ms": statistics.median(b_ms),
+                         "bounce_ms": statistics.median(q_ms), "queries": isrc.queries,
+                         "nodes_per_query": c[0] / isrc.queries, "tris_per_query": c[1] / isrc.queries})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "tree comparison: build time and traversal cost", "n_gpus": 1, "steps": args.steps,
+                      "warmup": args.warmup, "data": "synthetic", "rows": rows}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -511,6 +559,8 @@ def main():
         run_batched(args)
     elif args.workload == "tetra":
         run_tetra(args)
+    elif args.workload == "trees":
+        run_trees(args)
     else:
         run_native(args)
 

@@ -186,6 +186,17 @@ typedef struct {
  * RT_ERR_DEGENERATE_MESH, RT_ERR_OOM, RT_ERR_CUDA. */
 rt_status rt_build_tree(const rt_mesh* mesh, void* stream, rt_tree** out);
 void rt_tree_free(rt_tree* tree);
+/* The paper's own tree (Sec. 2.2), built on the device, for comparison with
+ * the LBVH: the box of a node's triangles is split along its largest extent
+ * at the median (the left child takes the first ceil(count / 2) triangles in
+ * centroid order), recursively; nodes of at most two triangles are then
+ * stored as leaves, and the tree is stored 4-wide like rt_build_tree's, so
+ * every trace call takes it.  The build sorts once per level (ceil(log2 M)
+ * segmented radix sorts), so it is slower than rt_build_tree; traces give
+ * the same results on either tree.  Same arguments, errors and ownership as
+ * rt_build_tree. */
+rt_status rt_build_tree_median(const rt_mesh* mesh, void* stream, rt_tree** out);
+
 /* Tree statistics: nodes, leaves, depth, triangles, surfaces. */
 rt_status rt_tree_info(const rt_tree* tree, int64_t* n_nodes, int64_t* n_tris, int32_t* depth,
                        int32_t* n_surfaces);

@@ -255,6 +255,111 @@ __device__ __forceinline__ Box tri_box(const float4* __restrict__ tv, int64_t t)
 }
 
 // leaf boxes in sorted order
+// ---------------------------------------------------------------------------
+// The paper's tree (Sec. 2.2): the box of a node's triangles is split along
+// its largest extent at the median, recursively, down to one triangle.  Its
+// shape depends on M alone -- every node [s, e] gives its first
+// ceil(count / 2) triangles to the left child -- so the topology is written
+// directly, with internal node ids = split positions (the root relabelled
+// to 0); only the order of the triangles depends on the geometry.  Level L
+// sorts every node of depth L by centroid along its box's largest extent
+// (segmented, as one radix sort of (node start, coordinate) keys).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int64_t msplit(int64_t s, int64_t e) { return s + (e - s + 2) / 2 - 1; }
+
+__device__ __forceinline__ int32_t median_id(int64_t g, int64_t root) {
+    return (int32_t)(g == root ? 0 : (g == 0 ? root : g));
+}
+
+// the node of depth L that holds position p (or the leaf it reached earlier)
+__device__ __forceinline__ void median_segment(int64_t M, int64_t p, int L, int64_t& s, int64_t& e) {
+    s = 0;
+    e = M - 1;
+    for (int l = 0; l < L && e > s; l++) {
+        const int64_t m = msplit(s, e);
+        if (p <= m)
+            e = m;
+        else
+            s = m + 1;
+    }
+}
+
+__global__ void k_iota(int64_t n, uint32_t* __restrict__ v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = (uint32_t)i;
+}
+
+__global__ void k_median_boxes(const float4* __restrict__ tv, const uint32_t* __restrict__ order, int64_t M, int L,
+                               unsigned int* __restrict__ seg_lo, unsigned int* __restrict__ seg_hi) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M) return;
+    int64_t s, e;
+    median_segment(M, p, L, s, e);
+    if (e == s) return;
+    const Box b = tri_box(tv, order[p]);
+    for (int k = 0; k < 3; k++) {
+        atomicMin(&seg_lo[3 * s + k], f2ord(b.lo[k]));
+        atomicMax(&seg_hi[3 * s + k], f2ord(b.hi[k]));
+    }
+}
+
+__global__ void k_median_keys(const float4* __restrict__ tv, const uint32_t* __restrict__ order, int64_t M, int L,
+                              const unsigned int* __restrict__ seg_lo, const unsigned int* __restrict__ seg_hi,
+                              uint64_t* __restrict__ keys) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M) return;
+    int64_t s, e;
+    median_segment(M, p, L, s, e);
+    uint32_t c = 0;
+    if (e > s) {
+        float ext[3];
+        for (int k = 0; k < 3; k++) ext[k] = ord2f(seg_hi[3 * s + k]) - ord2f(seg_lo[3 * s + k]);
+        const int ax = (ext[0] >= ext[1] && ext[0] >= ext[2]) ? 0 : (ext[1] >= ext[2] ? 1 : 2);
+        const int64_t t = order[p];
+        const float4 a = tv[3 * t], b = tv[3 * t + 1], d = tv[3 * t + 2];
+        const float ca = ax == 0 ? a.x : (ax == 1 ? a.y : a.z);
+        const float cb = ax == 0 ? b.x : (ax == 1 ? b.y : b.z);
+        const float cd = ax == 0 ? d.x : (ax == 1 ? d.y : d.z);
+        c = f2ord((ca + cb + cd) * (1.0f / 3.0f));
+    }
+    keys[p] = ((uint64_t)s << 32) | c;
+}
+
+__global__ void k_median_topology(int64_t M, int32_t* __restrict__ left, int32_t* __restrict__ right,
+                                  int32_t* __restrict__ first, int32_t* __restrict__ last,
+                                  int32_t* __restrict__ parent_int, int32_t* __restrict__ parent_leaf) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= M - 1) return;
+    const int64_t root = msplit(0, M - 1);
+    int64_t s = 0, e = M - 1;
+    int32_t parent = -1;
+    for (int guard = 0; guard < 64; guard++) {  // depth <= ceil(log2 M) < 64
+        const int64_t m = msplit(s, e);
+        if (m == g) break;
+        parent = median_id(m, root);
+        if (g < m)
+            e = m;
+        else
+            s = m + 1;
+    }
+    const int32_t id = median_id(g, root);
+    first[id] = (int32_t)s;
+    last[id] = (int32_t)e;
+    parent_int[id] = parent;
+    if (s == g) {
+        left[id] = ~(int32_t)s;
+        parent_leaf[s] = id;
+    } else {
+        left[id] = median_id(msplit(s, g), root);
+    }
+    if (g + 1 == e) {
+        right[id] = ~(int32_t)e;
+        parent_leaf[e] = id;
+    } else {
+        right[id] = median_id(msplit(g + 1, e), root);
+    }
+}
+
 __global__ void k_leaf_boxes(const float4* __restrict__ tv, const uint32_t* __restrict__ order, int64_t M,
                              float4* __restrict__ leaf_box) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -472,7 +577,7 @@ static std::vector<int32_t> group_surfaces(const double* V, const int32_t* T, co
     return out;
 }
 
-static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out) {
+static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out, bool median = false) {
     if (!mesh || !out) {
         set_error("rt_build_tree: null argument");
         return RT_ERR_INVALID_ARG;
@@ -563,9 +668,27 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out) 
     RR_TRY(tmp.alloc(&vals_alt, M));
     void* sort_tmp;
     RR_TRY(tmp.alloc((char**)&sort_tmp, sort_temp_bytes(M)));
-    RR_LAUNCH(k_morton, grid_of(M, 256), 256, 0, s, tv, M, meta, keys, vals);
-    RR_CUDA(cudaGetLastError());
-    RR_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, M, 0, 64, sort_tmp, s));
+    if (!median) {
+        RR_LAUNCH(k_morton, grid_of(M, 256), 256, 0, s, tv, M, meta, keys, vals);
+        RR_CUDA(cudaGetLastError());
+        RR_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, M, 0, 64, sort_tmp, s));
+    } else {
+        // identity order, then one segmented sort per level
+        RR_LAUNCH(k_iota, grid_of(M, 256), 256, 0, s, M, vals);
+        unsigned int *seg_lo, *seg_hi;
+        RR_TRY(tmp.alloc(&seg_lo, 3 * M));
+        RR_TRY(tmp.alloc(&seg_hi, 3 * M));
+        int levels = 0;
+        while ((int64_t)1 << levels < M) levels++;
+        for (int L = 0; L < levels; L++) {
+            RR_CUDA(cudaMemsetAsync(seg_lo, 0xFF, sizeof(unsigned int) * 3 * M, s));
+            RR_CUDA(cudaMemsetAsync(seg_hi, 0x00, sizeof(unsigned int) * 3 * M, s));
+            RR_LAUNCH(k_median_boxes, grid_of(M, 256), 256, 0, s, tv, vals, M, L, seg_lo, seg_hi);
+            RR_LAUNCH(k_median_keys, grid_of(M, 256), 256, 0, s, tv, vals, M, L, seg_lo, seg_hi, keys);
+            RR_CUDA(cudaGetLastError());
+            RR_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, M, 0, 64, sort_tmp, s));
+        }
+    }
 
     float4* tris;
     RR_TRY(keep_arena.alloc(&tris, 3 * M));
@@ -600,7 +723,10 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out) 
         RR_TRY(tmp.alloc((char**)&scan_tmp, scan_temp_bytes(NI)));
         RR_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned int) * NI, s));
         RR_CUDA(cudaMemsetAsync(pint, 0xFF, sizeof(int32_t) * NI, s));  // root keeps -1
-        RR_LAUNCH(k_karras, grid_of(NI, 256), 256, 0, s, keys, M, left, right, first, last, pint, pleaf);
+        if (!median)
+            RR_LAUNCH(k_karras, grid_of(NI, 256), 256, 0, s, keys, M, left, right, first, last, pint, pleaf);
+        else
+            RR_LAUNCH(k_median_topology, grid_of(NI, 256), 256, 0, s, M, left, right, first, last, pint, pleaf);
         RR_LAUNCH(k_leaf_boxes, grid_of(M, 256), 256, 0, s, tv, vals, M, leaf_box);
         RR_LAUNCH(k_refit, grid_of(M, 256), 256, 0, s, M, left, right, pint, pleaf, leaf_box, node_box, flags);
         RR_LAUNCH(k_depth, grid_of(M, 256), 256, 0, s, M, pint, pleaf, meta);
@@ -696,6 +822,11 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out) 
 extern "C" rt_status rt_build_tree(const rt_mesh* mesh, void* stream, rt_tree** out) {
     rr::clear_error();
     return rr::build_impl(mesh, (cudaStream_t)stream, out);
+}
+
+extern "C" rt_status rt_build_tree_median(const rt_mesh* mesh, void* stream, rt_tree** out) {
+    rr::clear_error();
+    return rr::build_impl(mesh, (cudaStream_t)stream, out, true);
 }
 
 extern "C" void rt_tree_free(rt_tree* tree) {

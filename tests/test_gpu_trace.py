@@ -325,6 +325,23 @@ def test_replay_reports_foreign_histories():
         rt.rt_trace(tree, replay=bad, **rt.scene_args(sc))
 
 
+@pytest.mark.parametrize("scene", ["shoebox", "lroom", "theatre"])
+def test_median_split_tree_gives_the_same_trace(scene):
+    """The paper's median-split tree (Sec. 2.2) built on the device: a trace
+    over it equals the trace over the LBVH bit for bit (the nearest hit does
+    not depend on the tree), and its depth is ceil(log2 M) or one more."""
+    sc = {"shoebox": lambda: scenes.shoebox(n_rays=20_000, n_bounces=20),
+          "lroom": lambda: scenes.lroom(h=0.5, n_rays=50_000, n_bounces=20),
+          "theatre": lambda: scenes.theatre(n_rays=100_000)}[scene]()
+    lbvh = rt.rt_build_tree(sc.vertices, sc.tris, sc.material_id, sc.surface_id)
+    med = rt.rt_build_tree(sc.vertices, sc.tris, sc.material_id, sc.surface_id, median=True)
+    M = len(sc.tris)
+    assert med.info()["depth"] in (math.ceil(math.log2(M)), math.ceil(math.log2(M)) + 1)
+    a = rt.rt_trace(lbvh, **rt.scene_args(sc))
+    b = rt.rt_trace(med, **rt.scene_args(sc))
+    _same_trace(a, b)
+
+
 def test_theatre_lockstep_and_free_running():
     sc = scenes.theatre()                                    # 436,796 triangles, 1M rays, 30 bounces
     B, N = sc.n_bounces, sc.n_rays
