@@ -76,10 +76,19 @@ typedef struct {
     rt_memory memory;
 } rt_mesh;
 
-/* Point sources (host memory). */
+/* Point sources (host memory).  axis NULL: omnidirectional (the Fibonacci
+ * rule, Sec. 1.2).  Otherwise every source is directional (Sec. 1.2 footnote:
+ * a non-uniform spatial sampling): its N rays keep the energy 1/N and their
+ * directions have density (1 - a + a cos theta) / (4 pi (1 - a)) about its
+ * unit axis, a = pattern[k] in [0, 1/2] (NULL: 0) -- the uniform rule's z
+ * mapped through the inverse cumulative of that density and turned to the
+ * axis (roomrays reference: the FP64 steps in rt_trace.cu's directional_dir).
+ * Axes must be unit vectors within 1e-9 (RT_ERR_INVALID_ARG otherwise). */
 typedef struct {
     const double* pos;           /* [n][3] */
     int32_t n;
+    const double* axis;          /* [n][3] unit axes, or NULL */
+    const double* pattern;       /* [n] pattern coefficients a, or NULL */
 } rt_sources;
 
 /* Measurement spheres S(x_m, r) (Sec. 1.2, eq. 22), host memory.  Receiver k

@@ -65,11 +65,12 @@ def lib():
             L.orc_scene_diameter.restype = f64
             L.orc_scene_diameter.argtypes = [P]
             L.orc_fibonacci.argtypes = [i64, i64, P, P]
+            L.orc_directions.argtypes = [i64, i64, P, P, f64, P]
             L.orc_nearest.argtypes = [P, i64, P, P, P, i32, f64, i32, P, P, P, P]
             L.orc_crossings.restype = i64
             L.orc_crossings.argtypes = [i64, P, P, P, P, i64, P, P, P, i64, P, P, P]
             L.orc_trace.restype = i64
-            L.orc_trace.argtypes = [P, P, i64, P, P, P, i64, i64, P, P, i32, f64, i32, f64, i32,
+            L.orc_trace.argtypes = [P, P, P, P, i64, P, P, P, i64, i64, P, P, i32, f64, i32, f64, i32,
                                     P, P, P, P, P, P, i64, P, P, P, P, P, P, P]
             _lib = L
     return _lib
@@ -164,6 +165,17 @@ def fibonacci(N: int, ids=None) -> np.ndarray:
     return out
 
 
+def source_directions(N: int, axis, pattern: float, ids=None) -> np.ndarray:
+    """Ray directions of a directional source (Sec. 1.2 footnote: non-uniform
+    sampling with equal ray energies): density (1 - a + a cos theta) about
+    the unit `axis`, a = `pattern` in [0, 1/2]; float32-rounded."""
+    ids = np.arange(N, dtype=np.int64) if ids is None else np.ascontiguousarray(ids, np.int64)
+    w = np.ascontiguousarray(axis, np.float64).reshape(3)
+    out = np.empty((len(ids), 3))
+    lib().orc_directions(int(N), len(ids), _p(ids), _p(w), float(pattern), _p(out))
+    return out
+
+
 @dataclass
 class TraceResult:
     ray_src: np.ndarray        # int32 [n]
@@ -217,6 +229,11 @@ def trace(osc: OracleScene, ray_ids=None, ray_src=None, brute=False, n_bounces=N
     B = int(sc.n_bounces if n_bounces is None else n_bounces)
     dmax = float(sc.max_distance if max_distance is None else max_distance)
     src = np.ascontiguousarray(sc.sources, np.float64)
+    axis = getattr(sc, "src_axis", None)          # directional sources (Sec. 1.2 footnote), else None
+    pattern = None
+    if axis is not None:
+        axis = np.ascontiguousarray(axis, np.float64).reshape(-1, 3)
+        pattern = np.ascontiguousarray(sc.src_pattern, np.float64).reshape(-1)
     rc = np.ascontiguousarray(sc.rcv_center, np.float64)
     rr = np.ascontiguousarray(sc.rcv_radius, np.float64)
     rs = np.ascontiguousarray(sc.rcv_source, np.int32)
@@ -235,7 +252,9 @@ def trace(osc: OracleScene, ray_ids=None, ray_src=None, brute=False, n_bounces=N
         rmg = np.empty(cap)
         rpos = np.empty((cap, 3))
         rdir = np.empty((cap, 3))
-        k = lib().orc_trace(osc.h, _p(src), len(rc), _p(rc), _p(rr), _p(rs), N, n, _p(ray_src),
+        k = lib().orc_trace(osc.h, _p(src), _p(axis) if axis is not None else None,
+                            _p(pattern) if pattern is not None else None, len(rc), _p(rc), _p(rr), _p(rs), N, n,
+                            _p(ray_src),
                             _p(ray_ids), B, dmax, int(brute or not osc.has_tree), eps_edge_rel,
                             threads or default_threads(), _p(hist), _p(hist_t), _p(E), _p(L),
                             _p(famb), _p(nh), cap, _p(rr_), _p(rray), _p(rm), _p(rL), _p(rmg),

@@ -238,6 +238,45 @@ void orc_fibonacci(int64_t N, int64_t n, const int64_t* ids, double* out) {
     for (int64_t k = 0; k < n; k++) fib_dir(ids[k], N, out + 3 * k);
 }
 
+/* Directional source (Sec. 1.2, footnote: a non-uniform spatial sampling).
+ * Rays keep the energy 1/N; their directions follow the power pattern
+ * p(mu) = (1 - a + a mu) / (2 (1 - a)) of mu = cos(angle to the axis w),
+ * 0 <= a <= 1/2: the uniform rule's z, as u = (1 + z) / 2, is mapped through
+ * the inverse of the cumulative F(mu) = u, the root of
+ *   (a/2) mu^2 + (1 - a) mu + (1 - a) - a/2 - 2 (1 - a) u = 0
+ * in [-1, 1], taken as mu = -2 C / (B + sqrt(B^2 - 2 a C)) (no cancellation
+ * as a -> 0); a = 0 keeps mu = z.  The direction (rho cos phi, rho sin phi,
+ * mu) is then turned from +z to the unit axis w with the orthonormal basis of
+ * Duff et al. 2017 ("Building an orthonormal basis, revisited").  Every step
+ * is one rounded FP64 operation in a fixed order. */
+static void dir_dir(int64_t i, int64_t N, const double* w, double a, double* u) {
+    double g = (3.0 - sqrt(5.0)) / 2.0;
+    double z = 1.0 - (double)(2 * i + 1) / (double)N;
+    double mu = z;
+    if (a > 0.0) {
+        double uu = (1.0 + z) / 2.0;
+        double B = 1.0 - a;
+        double C = (B - a / 2.0) - (2.0 * B) * uu;
+        double D = B * B - (2.0 * a) * C;
+        mu = (-2.0 * C) / (B + sqrt(D));
+    }
+    double rho = sqrt(1.0 - mu * mu);
+    double f = (double)i * g;
+    f = f - floor(f);
+    double phi = 2.0 * M_PI * f;
+    double cx = rho * cos(phi), cy = rho * sin(phi);
+    double sg = w[2] >= 0.0 ? 1.0 : -1.0;
+    double A = -1.0 / (sg + w[2]);
+    double Bq = (w[0] * w[1]) * A;
+    double t1[3] = {1.0 + ((sg * w[0]) * w[0]) * A, sg * Bq, -(sg * w[0])};
+    double t2[3] = {Bq, sg + (w[1] * w[1]) * A, -w[1]};
+    for (int k = 0; k < 3; k++) u[k] = (double)(float)((cx * t1[k] + cy * t2[k]) + mu * w[k]);
+}
+
+void orc_directions(int64_t N, int64_t n, const int64_t* ids, const double* axis, double a, double* out) {
+    for (int64_t k = 0; k < n; k++) dir_dir(ids[k], N, axis, a, out + 3 * k);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Nearest element along a ray (Sec. 2.1, eq. 20-21; Moller-Trumbore).       */
 /* ------------------------------------------------------------------------ */
@@ -488,6 +527,8 @@ int64_t orc_crossings(int64_t n, const double* o, const double* u, const double*
 typedef struct {
     const orc_scene* s;
     const double* src;
+    const double* axis;     /* [S][3] unit source axes, or NULL: omnidirectional */
+    const double* pattern;  /* [S] pattern coefficient a of each source */
     int64_t n_rcv;
     const double *rc, *rr;
     const int32_t* rsrc;
@@ -520,7 +561,10 @@ static void tr_range(void* p, int64_t b, int64_t e, int tid) {
         int32_t si = c->lsrc[i];
         double o[3] = {c->src[3 * si], c->src[3 * si + 1], c->src[3 * si + 2]};
         double u[3];
-        fib_dir(c->lray[i], c->N, u);
+        if (c->axis)
+            dir_dir(c->lray[i], c->N, c->axis + 3 * c->lsrc[i], c->pattern[c->lsrc[i]], u);
+        else
+            fib_dir(c->lray[i], c->N, u);
         double E[NB];
         for (int f = 0; f < NB; f++) E[f] = 1.0 / (double)c->N;
         double L = 0.0;
@@ -572,7 +616,8 @@ static void tr_range(void* p, int64_t b, int64_t e, int tid) {
 /* Returns the number of records found; writes at most rec_cap of them (in
  * ray-list order, then bounce, then receiver).  Call again with a larger
  * capacity if the return value exceeds rec_cap. */
-int64_t orc_trace(void* scene, const double* src, int64_t n_rcv, const double* rcv_c, const double* rcv_r,
+int64_t orc_trace(void* scene, const double* src, const double* src_axis, const double* src_pattern,
+                  int64_t n_rcv, const double* rcv_c, const double* rcv_r,
                   const int32_t* rcv_src, int64_t N, int64_t n_list, const int32_t* list_src,
                   const int64_t* list_ray, int32_t B, double max_distance, int32_t brute, double eps_edge_rel,
                   int32_t nthreads, int32_t* hist, double* hist_t, double* E_final, double* L_final,
@@ -584,6 +629,8 @@ int64_t orc_trace(void* scene, const double* src, int64_t n_rcv, const double* r
     memset(&c, 0, sizeof c);
     c.s = (orc_scene*)scene;
     c.src = src;
+    c.axis = src_axis;
+    c.pattern = src_pattern;
     c.n_rcv = n_rcv;
     c.rc = rcv_c;
     c.rr = rcv_r;

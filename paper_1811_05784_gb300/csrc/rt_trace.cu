@@ -142,6 +142,45 @@ __device__ __forceinline__ float3 fibonacci_dir(int64_t i, int64_t N) {
     return make_float3((float)__dmul_rn(rho, c), (float)__dmul_rn(rho, s), (float)z);
 }
 
+// Directional source (Sec. 1.2, footnote: a non-uniform spatial sampling):
+// equal-energy rays with density (1 - a + a mu) / (2 (1 - a)) in mu = cos of
+// the angle to the unit axis w, 0 <= a <= 1/2.  The uniform rule's z, as
+// u = (1 + z) / 2, goes through the inverse cumulative: the root of
+// (a/2) mu^2 + (1 - a) mu + (1 - a) - a/2 - 2 (1 - a) u = 0 in [-1, 1], taken
+// as mu = -2 C / (B + sqrt(B^2 - 2 a C)) (no cancellation as a -> 0); a = 0
+// keeps mu = z.  The direction is then turned from +z to w with the
+// orthonormal basis of Duff et al. 2017.  One rounded FP64 operation per step,
+// in the same order as the FP64 reference, so the float32 directions agree.
+__device__ __forceinline__ float3 directional_dir(int64_t i, int64_t N, const double* w, double a) {
+    const double g = __ddiv_rn(__dsub_rn(3.0, __dsqrt_rn(5.0)), 2.0);
+    const double z = __dsub_rn(1.0, __ddiv_rn((double)(2 * i + 1), (double)N));
+    double mu = z;
+    if (a > 0.0) {
+        const double uu = __ddiv_rn(__dadd_rn(1.0, z), 2.0);
+        const double B = __dsub_rn(1.0, a);
+        const double C = __dsub_rn(__dsub_rn(B, __ddiv_rn(a, 2.0)), __dmul_rn(__dmul_rn(2.0, B), uu));
+        const double D = __dsub_rn(__dmul_rn(B, B), __dmul_rn(__dmul_rn(2.0, a), C));
+        mu = __ddiv_rn(__dmul_rn(-2.0, C), __dadd_rn(B, __dsqrt_rn(D)));
+    }
+    const double rho = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(mu, mu)));
+    double f = __dmul_rn((double)i, g);
+    f = __dsub_rn(f, floor(f));
+    const double phi = __dmul_rn(6.283185307179586, f);
+    double sn, cs;
+    sincos(phi, &sn, &cs);
+    const double cx = __dmul_rn(rho, cs), cy = __dmul_rn(rho, sn);
+    const double sg = w[2] >= 0.0 ? 1.0 : -1.0;
+    const double A = __ddiv_rn(-1.0, __dadd_rn(sg, w[2]));
+    const double Bq = __dmul_rn(__dmul_rn(w[0], w[1]), A);
+    const double t1[3] = {__dadd_rn(1.0, __dmul_rn(__dmul_rn(__dmul_rn(sg, w[0]), w[0]), A)), __dmul_rn(sg, Bq),
+                          -__dmul_rn(sg, w[0])};
+    const double t2[3] = {Bq, __dadd_rn(sg, __dmul_rn(__dmul_rn(w[1], w[1]), A)), -w[1]};
+    float u[3];
+    for (int k = 0; k < 3; k++)
+        u[k] = (float)__dadd_rn(__dadd_rn(__dmul_rn(cx, t1[k]), __dmul_rn(cy, t2[k])), __dmul_rn(mu, w[k]));
+    return make_float3(u[0], u[1], u[2]);
+}
+
 // Queue order of the primary rays: Fibonacci indices j, j+F, j+2F, ... (F a
 // Fibonacci number near sqrt(count)) lie along one spiral arm of the lattice,
 // so consecutive queue slots (one warp) get neighbouring directions.  The
@@ -160,14 +199,18 @@ __device__ __forceinline__ int64_t coherent_offset(int64_t r, int64_t count, int
     return j + k * F;
 }
 
-__global__ void k_gen_rays(Queue q, const float* __restrict__ src, int64_t n_traced, int64_t per_src,
-                           int64_t ray_begin, int64_t N, int64_t F) {
+__global__ void k_gen_rays(Queue q, const float* __restrict__ src, const double* __restrict__ srcdir,
+                           int64_t n_traced, int64_t per_src, int64_t ray_begin, int64_t N, int64_t F) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_traced) return;
     int64_t s = r / per_src;
     int64_t off = coherent_offset(r % per_src, per_src, F);
     int64_t i = ray_begin + off;
-    float3 u = fibonacci_dir(i, N);
+    float3 u;
+    if (srcdir && srcdir[4 * s + 3] >= 0.0)
+        u = directional_dir(i, N, srcdir + 4 * s, srcdir[4 * s + 3]);
+    else
+        u = fibonacci_dir(i, N);
     float e = (float)(1.0 / (double)N);
     q.o[r] = make_float4(src[3 * s], src[3 * s + 1], src[3 * s + 2], 0.f);
     q.d[r] = make_float4(u.x, u.y, u.z, 0.f);
@@ -1011,6 +1054,8 @@ struct HostRoomTables {
     std::vector<float4> rcv;
     std::vector<float> src;
     std::vector<double> src64, rcv64, alpha64;
+    std::vector<double> srcdir;  // [S][4] unit axis, pattern a; a < 0: omnidirectional
+    bool directional = false;
     std::vector<float> refl;
     int S = 0, R = 0;
     int64_t total_tris = 0;
@@ -1044,6 +1089,7 @@ static rt_status gather_rooms(const rt_room* rooms, int n_rooms, HostRoomTables&
     h.room_of_src.resize((size_t)h.S);
     h.src.resize((size_t)3 * h.S);
     h.src64.resize((size_t)3 * h.S);
+    h.srcdir.assign((size_t)4 * h.S, 0.0);
     h.room_of_rcv.resize((size_t)std::max(h.R, 1), 0);
     h.rcv64.resize((size_t)3 * std::max(h.R, 1), 0.0);
     std::vector<int> gsrc((size_t)std::max(h.R, 1), 0);  // global source of each global receiver
@@ -1069,6 +1115,20 @@ static rt_status gather_rooms(const rt_room* rooms, int n_rooms, HostRoomTables&
                 }
                 h.src64[3 * g + c] = x;
                 h.src[3 * g + c] = (float)x;
+            }
+            h.srcdir[4 * g + 3] = -1.0;
+            if (rm.sources.axis) {
+                const double* w = rm.sources.axis + 3 * k;
+                const double a = rm.sources.pattern ? rm.sources.pattern[k] : 0.0;
+                const double n2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+                if (!(std::fabs(n2 - 1.0) <= 1e-9) || !(a >= 0.0 && a <= 0.5)) {
+                    set_error("rt_trace: room %d: source axes must be unit vectors and patterns lie in [0, 1/2]",
+                              r);
+                    return RT_ERR_INVALID_ARG;
+                }
+                for (int c = 0; c < 3; c++) h.srcdir[4 * g + c] = w[c];
+                h.srcdir[4 * g + 3] = a;
+                h.directional = true;
             }
         }
         for (int k = 0; k < rm.receivers.n; k++) {
@@ -1184,7 +1244,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     int32_t *d_room_of_src, *d_room_of_rcv, *d_rcv_id, *d_beg;
     float4* d_rcv;
     float *d_src, *d_refl;
-    double *d_alpha64, *d_beta64, *d_src64, *d_rcv64;
+    double *d_alpha64, *d_beta64, *d_src64, *d_rcv64, *d_srcdir = nullptr;
     RR_TRY(upload(tmp, h.rooms, &d_rooms, s));
     RR_TRY(upload(tmp, h.room_of_src, &d_room_of_src, s));
     RR_TRY(upload(tmp, h.room_of_rcv, &d_room_of_rcv, s));
@@ -1192,6 +1252,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     RR_TRY(upload(tmp, h.rcv_id, &d_rcv_id, s));
     RR_TRY(upload(tmp, h.rcv_beg, &d_beg, s));
     RR_TRY(upload(tmp, h.src, &d_src, s));
+    if (h.directional) RR_TRY(upload(tmp, h.srcdir, &d_srcdir, s));
     RR_TRY(upload(tmp, h.refl, &d_refl, s));
     RR_TRY(upload(tmp, h.alpha64, &d_alpha64, s));
     RR_TRY(upload(tmp, h_beta64, &d_beta64, s));
@@ -1295,7 +1356,8 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
             F = F1;
             F1 = t;
         }
-        RR_LAUNCH(k_gen_rays, grid_of(n_traced, 256), 256, 0, s, q[0], d_src, n_traced, per_src, p->ray_begin, N, F);
+        RR_LAUNCH(k_gen_rays, grid_of(n_traced, 256), 256, 0, s, q[0], d_src, d_srcdir, n_traced, per_src,
+                  p->ray_begin, N, F);
         RR_CUDA(cudaGetLastError());
         RR_CUDA(cudaEventRecord(ev.e[1], s));
         BounceArgs a{};

@@ -52,7 +52,24 @@ class rt_mesh(C.Structure):
 
 
 class rt_sources(C.Structure):
-    _fields_ = [("pos", P), ("n", C.c_int32)]
+    _fields_ = [("pos", P), ("n", C.c_int32), ("axis", P), ("pattern", P)]
+
+
+def _sources(sources, src_axis=None, src_pattern=None):
+    """rt_sources over host copies (returned with it, to keep them alive).
+    src_axis [S][3] unit axes and src_pattern [S] (a in [0, 1/2]) make the
+    sources directional; None keeps them omnidirectional."""
+    src, ps = _host(np.asarray(sources, np.float64).reshape(-1, 3), np.float64)
+    keep = [src]
+    pax = ppa = None
+    if src_axis is not None:
+        ax, pax = _host(np.asarray(src_axis, np.float64).reshape(-1, 3), np.float64)
+        pat = np.zeros(len(src)) if src_pattern is None else src_pattern
+        pa, ppa = _host(np.asarray(pat, np.float64).reshape(-1), np.float64)
+        if len(ax) != len(src) or len(pa) != len(src):
+            raise ValueError("src_axis and src_pattern need one entry per source")
+        keep += [ax, pa]
+    return rt_sources(ps, len(src), pax, ppa), keep
 
 
 class rt_receivers(C.Structure):
@@ -395,11 +412,12 @@ class ImageSources:
 def rt_trace(tree: Tree, sources, rcv_center, rcv_radius, rcv_source, band_absorption, n_rays, n_bounces,
              ray_begin=0, ray_count=0, max_distance=0.0, air_beta=None, c=343.2, block_size=0,
              max_node_visits=0, tail_rays=0, stream=None, debug_t=None, debug_state=None,
-             debug_cost=None, workspace=None, replay=None) -> ImageSources:
+             debug_cost=None, workspace=None, replay=None, src_axis=None, src_pattern=None) -> ImageSources:
     """Propagate rays and build image sources (host inputs; see roomrays.h).
     replay: the result (or its hist) of an earlier trace of the same rays --
-    the queries then re-test the recorded triangles, for new receivers."""
-    src, ps = _host(np.asarray(sources, np.float64).reshape(-1, 3), np.float64)
+    the queries then re-test the recorded triangles, for new receivers.
+    src_axis / src_pattern: directional sources (see _sources)."""
+    S, keep_src = _sources(sources, src_axis, src_pattern)
     rc, prc = _host(np.asarray(rcv_center, np.float64).reshape(-1, 3), np.float64)
     rr, prr = _host(np.asarray(rcv_radius, np.float64).reshape(-1), np.float64)
     rs, prs = _host(np.asarray(rcv_source, np.int32).reshape(-1), np.int32)
@@ -408,7 +426,6 @@ def rt_trace(tree: Tree, sources, rcv_center, rcv_radius, rcv_source, band_absor
         be, pbe = _host(np.asarray(air_beta, np.float32).reshape(N_BANDS), np.float32)
     else:
         be, pbe = None, None
-    S = rt_sources(ps, len(src))
     R = rt_receivers(prc, prr, prs, len(rc))
     prm = rt_trace_params(int(n_rays), int(ray_begin), int(ray_count), int(n_bounces), float(max_distance), pbe,
                           float(c), int(block_size), int(max_node_visits), int(tail_rays), _stream_ptr(stream),
@@ -489,18 +506,18 @@ def rt_trace_batch(rooms, n_rays, n_bounces, ray_begin=0, ray_count=0, max_dista
                    replay=None) -> ImageSources:
     """Trace many rooms in one persistent launch.  `rooms` is a list of dicts
     with keys tree, sources, rcv_center, rcv_radius, rcv_source,
-    band_absorption.  Receivers are numbered room after room.  replay: see
-    rt_trace."""
+    band_absorption (and optionally src_axis, src_pattern).  Receivers are
+    numbered room after room.  replay: see rt_trace."""
     keep, arr = [], (rt_room * len(rooms))()
     n_rcv = 0
     for k, r in enumerate(rooms):
-        src, ps = _host(np.asarray(r["sources"], np.float64).reshape(-1, 3), np.float64)
+        S, keep_src = _sources(r["sources"], r.get("src_axis"), r.get("src_pattern"))
         rc, prc = _host(np.asarray(r["rcv_center"], np.float64).reshape(-1, 3), np.float64)
         rr, prr = _host(np.asarray(r["rcv_radius"], np.float64).reshape(-1), np.float64)
         rs, prs = _host(np.asarray(r["rcv_source"], np.int32).reshape(-1), np.int32)
         al, pal = _host(np.asarray(r["band_absorption"], np.float32).reshape(-1, N_BANDS), np.float32)
-        keep += [src, rc, rr, rs, al]
-        arr[k] = rt_room(r["tree"]._h, rt_sources(ps, len(src)), rt_receivers(prc, prr, prs, len(rc)), pal, len(al))
+        keep += keep_src + [rc, rr, rs, al]
+        arr[k] = rt_room(r["tree"]._h, S, rt_receivers(prc, prr, prs, len(rc)), pal, len(al))
         n_rcv += len(rc)
     if air_beta is not None:
         be, pbe = _host(np.asarray(air_beta, np.float32).reshape(N_BANDS), np.float32)
@@ -557,7 +574,8 @@ def scene_args(scene):
     return dict(sources=scene.sources, rcv_center=scene.rcv_center, rcv_radius=scene.rcv_radius,
                 rcv_source=scene.rcv_source, band_absorption=scene.alpha, n_rays=scene.n_rays,
                 n_bounces=scene.n_bounces, max_distance=scene.max_distance,
-                air_beta=scene.beta if np.any(scene.beta) else None, c=scene.c)
+                air_beta=scene.beta if np.any(scene.beta) else None, c=scene.c,
+                src_axis=getattr(scene, "src_axis", None), src_pattern=getattr(scene, "src_pattern", None))
 
 
 class MLP:

@@ -67,6 +67,8 @@ class Scene:
     c: float = 343.2              # sound speed (m/s)
     fs: float = 48000.0           # RIR sample rate (Hz)
     max_distance: float = 0.0     # <=0: off; else eq. 13 range cap on path length
+    src_axis: np.ndarray = None   # float64 [S,3] unit axes of directional sources, or None (omnidirectional)
+    src_pattern: np.ndarray = None  # float64 [S] pattern a in [0, 1/2]: ray density 1 - a + a cos(theta)
     meta: dict = field(default_factory=dict)
 
     @property
@@ -264,6 +266,21 @@ def paper_shoebox(n_rays=100_000, seed=0) -> Scene:
     return shoebox(L=(5.0, 4.0, 3.0), source=(4.0, 2.0, 1.7), receiver=(2.0, 2.0, 1.7),
                    radius=r, n_rays=n_rays, n_bounces=64, beta=iso9613_beta(),
                    face_materials=face_mat, alpha_table=alpha_tab, max_distance=dmax)
+
+
+def directional(sc: Scene, axis, pattern) -> Scene:
+    """A copy of `sc` whose sources are directional (Sec. 1.2 footnote): rays
+    of equal energy sampled with density 1 - a + a cos(theta) about `axis`
+    (one [3] for all sources or [S, 3]; normalised here), a = `pattern` in
+    [0, 1/2] (0 = omnidirectional lattice turned to the axis, 1/2 = cardioid)."""
+    import copy
+    out = copy.copy(sc)
+    S = len(sc.sources)
+    ax = np.broadcast_to(np.asarray(axis, np.float64).reshape(-1, 3), (S, 3)).copy()
+    ax /= np.sqrt((ax * ax).sum(1, keepdims=True))
+    out.src_axis = ax
+    out.src_pattern = np.broadcast_to(np.asarray(pattern, np.float64).reshape(-1), (S,)).copy()
+    return out
 
 
 LROOM_FOOTPRINT = [(0, 0), (20, 0), (20, 7.5), (10, 7.5), (10, 15), (0, 15)]

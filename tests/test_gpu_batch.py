@@ -32,7 +32,8 @@ def _is_table(sc_list, isrc, rcv_base):
 def _check_batch_equals_single(scs, N, B):
     trees = [_tree(sc) for sc in scs]
     rooms = [dict(tree=t, sources=sc.sources, rcv_center=sc.rcv_center, rcv_radius=sc.rcv_radius,
-                  rcv_source=sc.rcv_source, band_absorption=sc.alpha) for t, sc in zip(trees, scs)]
+                  rcv_source=sc.rcv_source, band_absorption=sc.alpha, src_axis=sc.src_axis,
+                  src_pattern=sc.src_pattern) for t, sc in zip(trees, scs)]
     batch = rt.rt_trace_batch(rooms, N, B, tail_rays=rt.RT_TAIL_AUTOTUNE)
     rcv_base = np.cumsum([0] + [len(sc.rcv_center) for sc in scs])
     hb = batch.hist.cpu().numpy()
@@ -60,6 +61,17 @@ def test_batch_matches_single_rooms():
     N, B = 20_000, 20
     scs = [scenes.shoebox(n_rays=N, n_bounces=B), scenes.lroom(h=0.5, n_rays=N, n_bounces=B),
            scenes.icosphere(level=2, n_rays=N, n_bounces=B)]
+    _check_batch_equals_single(scs, N, B)
+
+
+def test_batch_with_directional_rooms_matches_single_rooms():
+    """Omnidirectional and directional rooms in one launch (each source keeps
+    its own axis and pattern)."""
+    N, B = 12_000, 16
+    scs = [scenes.shoebox(n_rays=N, n_bounces=B),
+           scenes.directional(scenes.lroom(h=0.5, n_rays=N, n_bounces=B), [0.0, -0.6, 0.8], 0.5),
+           scenes.directional(scenes.shoebox(L=(6.0, 5.0, 3.0), source=(1.0, 1.0, 1.0), receiver=(4.0, 3.0, 1.5),
+                                             n_rays=N, n_bounces=B), [-1.0, 0.0, 0.0], 0.3)]
     _check_batch_equals_single(scs, N, B)
 
 

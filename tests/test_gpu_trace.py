@@ -479,3 +479,117 @@ def test_surface_grouping_when_ids_missing():
     a = rt.rt_trace(t_ids, **rt.scene_args(sc))
     b = rt.rt_trace(_tree(sc), **rt.scene_args(sc))
     assert torch.equal(a.hist, b.hist) and a.n == b.n
+
+
+# ---------------------------------------------------------------------------
+# directional sources (Sec. 1.2 footnote: non-uniform sampling, equal energies)
+def _two_directional_sources(n_rays, n_bounces, patterns=(0.5, 0.2)):
+    """Shoebox with two sources; the second axis points down (negative z)."""
+    import copy
+    sc = copy.copy(scenes.shoebox(n_rays=n_rays, n_bounces=n_bounces))
+    sc.sources = np.array([[2.0, 3.0, 1.5], [7.5, 2.0, 1.25]])
+    sc.rcv_center = np.array([[7.0, 4.0, 1.75], [3.0, 5.0, 2.0]])
+    sc.rcv_radius = np.array([0.5, 0.5])
+    sc.rcv_source = np.array([0, 1], np.int32)
+    return scenes.directional(sc, [[0.36, -0.48, 0.8], [0.6, 0.0, -0.8]], list(patterns))
+
+
+def test_directional_directions_match_oracle():
+    """Bounce-0 directions of two directional sources against the FP64
+    warp + rotation; the FP64 steps are the same on both sides, so at most
+    a last-bit difference of the double sine / cosine may surface."""
+    N = 50_021
+    sc = _two_directional_sources(N, 1)
+    ds = torch.empty((1, 2 * N, 6), dtype=torch.float32, device="cuda")
+    _trace(sc, debug_state=ds)
+    torch.cuda.synchronize()
+    d = ds[0, :, 3:].cpu().numpy().astype(np.float64)
+    for s in range(2):
+        ref = oracle.source_directions(N, sc.src_axis[s], sc.src_pattern[s])
+        diff = np.abs(d[s * N:(s + 1) * N] - ref)
+        assert (diff > 0).sum() <= 1e-4 * 3 * N, (s, int((diff > 0).sum()))
+        assert diff.max() <= 1.2e-7, (s, diff.max())
+        o = ds[0, s * N:(s + 1) * N, :3].cpu().numpy().astype(np.float64)
+        assert np.array_equal(o, np.broadcast_to(sc.sources[s], o.shape))
+
+
+def test_directional_trace_parity():
+    n_rays = 6001
+    sc = _two_directional_sources(n_rays, 12)
+    B, n = sc.n_bounces, 2 * n_rays
+    ds_t = torch.empty((B, n, 6), dtype=torch.float32, device="cuda")
+    dt_t = torch.empty((B, n), dtype=torch.float32, device="cuda")
+    tree, isrc = _trace(sc, debug_t=dt_t, debug_state=ds_t)
+    ds, dt = ds_t.cpu().numpy(), dt_t.cpu().numpy()
+    hist = isrc.hist.cpu().numpy()
+    osc = oracle.OracleScene(sc, tree=False)
+    bq, amb = _check_lockstep(sc, osc, ds, dt, hist)
+    assert amb.mean() < 0.01
+    tr = oracle.trace(osc, eps_edge_rel=EPS_FREE)       # the oracle draws its own directional rays
+    ok = tr.first_amb == B
+    assert ok.mean() > 0.95
+    assert np.array_equal(hist.T[ok], tr.hist[ok])
+    E = isrc.ray_energy.cpu().numpy().astype(np.float64)
+    assert np.abs(E[ok] / tr.E[ok] - 1).max() < TOL_E
+    # image sources of the GPU's crossings, grouped and rebuilt in FP64
+    ref = oracle.image_sources(sc, _gpu_as_oracle_trace(sc, isrc))
+    got = _gpu_is_table(sc, isrc)
+    assert len(got) == len(ref.n)
+    for k in range(len(ref.n)):
+        c, pos, dist, tim, en = got[(int(ref.rcv[k]), ref.seq[k])]
+        assert c == ref.n[k] and np.allclose(en, ref.E[k], rtol=1e-12, atol=0)
+
+
+def _direct_cap_fraction(a, d, r, side):
+    """Share of a source's rays, density (1 - a + a mu) / (2 (1 - a)) in mu,
+    aimed into a sphere of radius r at distance d in front of (side +1:
+    mu >= c) or behind (side -1: mu <= -c) the source."""
+    c = math.sqrt(1.0 - (r / d) ** 2)
+    return ((1 - a) * (1 - c) + side * 0.5 * a * (1 - c * c)) / (2 * (1 - a))
+
+
+@pytest.mark.parametrize("a", [0.0, 0.25, 0.5])
+def test_directional_direct_sound_follows_pattern(a):
+    """Direct sound in front of and behind a source pointing along +x: the
+    counts n (energy n / N, eq. 19) follow the cap integral of the pattern;
+    the front / back ratio is about 1 / (1 - 2 a) (for a = 1/2 only the
+    rim of the back cap, where 1 + mu > 0, is reached)."""
+    import copy
+    N = 1_000_000
+    sc = copy.copy(scenes.shoebox(L=(40.0, 40.0, 40.0), source=(20.0, 20.0, 20.0), alpha=1.0,
+                                  n_rays=N, n_bounces=1))
+    sc.rcv_center = np.array([[23.0, 20.0, 20.0], [17.0, 20.0, 20.0]])
+    sc.rcv_radius = np.array([0.5, 0.5])
+    sc.rcv_source = np.array([0, 0], np.int32)
+    sc = scenes.directional(sc, [1.0, 0.0, 0.0], a)
+    _, isrc = _trace(sc)
+    order = isrc.order.cpu().numpy()
+    rcv = isrc.rcv.cpu().numpy()
+    cnt = isrc.count.cpu().numpy()
+    en = isrc.energy.cpu().numpy()
+    direct = {int(rcv[k]): (int(cnt[k]), en[k]) for k in range(isrc.n) if order[k] == 0}
+    front = _direct_cap_fraction(a, 3.0, 0.5, +1) * N
+    back = _direct_cap_fraction(a, 3.0, 0.5, -1) * N
+    # the warped lattice is stratified in mu about the axis, so a cap centred
+    # on it holds N times its share to within a ray or two (plus float32
+    # rounding of the rays that graze the sphere)
+    n_f, e_f = direct[0]
+    n_b = direct[1][0] if 1 in direct else 0
+    assert abs(n_f - front) <= 3 + 0.002 * front, (n_f, front)
+    assert abs(n_b - back) <= 3 + 0.002 * back, (n_b, back)
+    assert np.allclose(e_f, n_f / N, rtol=1e-6)
+    if a < 0.5:
+        assert n_f / n_b == pytest.approx(1.0 / (1.0 - 2.0 * a), rel=0.02)
+
+
+def test_directional_sources_are_validated():
+    sc = scenes.shoebox(n_rays=1000, n_bounces=4)
+    tree = _tree(sc)
+    for axis, pat in (([1.0, 1.0, 0.0], 0.2), ([1.0, 0.0, 0.0], 0.6), ([1.0, 0.0, 0.0], -0.1)):
+        with pytest.raises(rt.RtError) as e:
+            rt.rt_trace(tree, **dict(rt.scene_args(sc), src_axis=[axis], src_pattern=[pat]))
+        assert e.value.status == rt.RT_ERR_INVALID_ARG
+    # a = 0 turned to +z is the omnidirectional lattice itself
+    a = rt.rt_trace(tree, **dict(rt.scene_args(sc), src_axis=[[0.0, 0.0, 1.0]], src_pattern=[0.0]))
+    b = rt.rt_trace(tree, **rt.scene_args(sc))
+    assert torch.equal(a.hist, b.hist) and torch.equal(a.ray_energy, b.ray_energy)

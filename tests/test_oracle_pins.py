@@ -346,3 +346,26 @@ def test_decay_metrics_on_exponential(T):
     h = np.exp(-6 * math.log(10) * n / (fs * T))      # 60 dB per T seconds
     assert oracle.t30(h, fs) == pytest.approx(T, rel=1e-3)
     assert oracle.edt(h, fs) == pytest.approx(T, rel=1e-3)
+
+
+def test_directional_source_sampling():
+    """Directional sources (Sec. 1.2 footnote): equal-energy rays whose
+    directions have density (1 - a + a cos theta) / (4 pi (1 - a)) about the
+    axis.  a = 0 about +z is the Fibonacci rule itself; the mean of cos theta
+    is a / (3 (1 - a)); a cardioid (a = 1/2) sends 3/4 of its rays forward;
+    the mean direction lies along the axis."""
+    N = 200_000
+    assert np.array_equal(oracle.source_directions(N, (0, 0, 1), 0.0), oracle.fibonacci(N))
+    g = np.random.default_rng(0)
+    for a in (0.1, 0.3, 0.5):
+        w = g.normal(size=3)
+        w /= np.linalg.norm(w)
+        d = oracle.source_directions(N, w, a)
+        assert np.allclose(np.linalg.norm(d, axis=1), 1.0, atol=1e-6)
+        mu = d @ w
+        assert abs(mu.mean() - a / (3 * (1 - a))) < 2e-3
+        fwd = (1 - a / 2) / (2 * (1 - a))
+        assert abs((mu > 0).mean() - fwd) < 2e-3
+        perp = d - np.outer(mu, w)
+        assert np.linalg.norm(perp.mean(0)) < 2e-3
+    assert abs((oracle.source_directions(N, (1, 0, 0), 0.5) @ np.array([1, 0, 0]) > 0).mean() - 0.75) < 2e-3
