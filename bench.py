@@ -13,8 +13,9 @@ value      nearest-element queries resolved (hits + escapes) per second, over
            launching stream, L2 flushed (256 MB write) before every step.
 e2e        the same metric through the C ABI from pinned host buffers: mesh
            H2D, trace, histograms and their D2H copy inside the timed region.
-roofline   the bounce kernel's algorithmic L2-path bytes (64 B per node
-           visited + 48 B per triangle tested, counted by an instrumented
+roofline   the bounce kernel's algorithmic L2-path bytes (112 B per 4-wide
+           node visited: six float4 of child boxes and one of child
+           references; 48 B per triangle tested; counted by an instrumented
            pass) over its live duration, against the L2 read bandwidth
            measured in the same run; HBM fraction beside it.
 cpu_baseline  the FP64 oracle (oracle/, C + numpy) on a bounded sample of the
