@@ -18,6 +18,10 @@ roofline   the bounce kernel's algorithmic L2-path bytes (112 B per 4-wide
            references; 48 B per triangle tested; counted by an instrumented
            pass) over its live duration, against the L2 read bandwidth
            measured in the same run; HBM fraction beside it.
+phases_ms  medians over the timed steps (CUDA events): tree build, ray
+           generation, bounce loop, image sources (dedup + FP64
+           reconstruction), the rest of rt_trace (uploads, queue set-up,
+           result sizes), RIR binning.
 cpu_baseline  the FP64 oracle (oracle/, C + numpy) on a bounded sample of the
            same workload on this host's cores.
 
@@ -233,6 +237,21 @@ def profiled_traffic(tail):
     return float(kv["traffic_bytes_per_trace"])
 
 
+def host_cpu():
+    """Architecture and model name of the host cores (for the oracle timing)."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return f"{platform.machine()} {model} x{os.cpu_count()}".strip()
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -260,9 +279,13 @@ def run_native(args):
     ws_trace = rt.Workspace()
     tail = rt.RT_TAIL_AUTOTUNE if args.tail_rays is None else args.tail_rays
 
-    def step(tail):
+    def step(tail, ev=None):
         tree = rt.rt_build_tree(V, T, Mt, St, stream=stream)
+        if ev is not None:
+            ev[0].record(stream)
         isrc = rt.rt_trace(tree, tail_rays=tail, stream=stream, workspace=ws_trace, **kw)
+        if ev is not None:
+            ev[1].record(stream)
         resp = rt.rt_rir(isrc, sc.fs, duration=DURATION, stream=stream)
         return tree, isrc, resp
 
@@ -280,17 +303,26 @@ def run_native(args):
         torch.cuda.synchronize()
         launches0 = rt.rt_launch_count()
         ms, queries, ms_bounce = [], [], []
+        phases = {k: [] for k in ("build", "rays", "bounces", "image_sources", "trace_other", "rir")}
         with ClockSampler(torch.cuda.current_device(), args.clock_log) as clk:
             for _ in range(args.steps):
                 flush.zero_()
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
                 a.record(stream)
-                tree, isrc, resp = step(tail)
+                tree, isrc, resp = step(tail, ev)
                 b.record(stream)
                 b.synchronize()
                 ms.append(a.elapsed_time(b))
                 queries.append(isrc.queries)
                 ms_bounce.append(isrc.ms_bounces)
+                t_trace = ev[0].elapsed_time(ev[1])
+                phases["build"].append(a.elapsed_time(ev[0]))
+                phases["rays"].append(isrc.ms_rays)
+                phases["bounces"].append(isrc.ms_bounces)
+                phases["image_sources"].append(isrc.ms_image_sources)
+                phases["trace_other"].append(t_trace - isrc.ms_rays - isrc.ms_bounces - isrc.ms_image_sources)
+                phases["rir"].append(ev[1].elapsed_time(b))
         torch.cuda.synchronize()
         launches = rt.rt_launch_count() - launches0
         if ws > 1:
@@ -366,6 +398,7 @@ def run_native(args):
                              "frac": hbm_bytes / bounce_s / 1e9 / hbm_peak, "peak_source": hbm_src},
                      "ms_per_launch_set": bounce_s * 1e3,
                      "nodes_per_query": c[0] / n_q, "tris_per_query": c[1] / n_q},
+        "phases_ms": {k: statistics.median(v) for k, v in phases.items()},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }
@@ -373,7 +406,8 @@ def run_native(args):
         q, dt, threads = oracle_sample(sc, args.cpu_sample_rays)
         result["cpu_baseline"] = {"value": q / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
                                   "sample": f"{args.cpu_sample_rays:,} seeded rays of the workload "
-                                            f"(oracle median-split tree, image sources, RIR): {q:,} queries"}
+                                            f"(oracle median-split tree, image sources, RIR): {q:,} queries",
+                                  "cpu": host_cpu()}
     if rank == 0:
         print(json.dumps(result))
     if ws > 1:

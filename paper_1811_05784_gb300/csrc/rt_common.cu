@@ -212,89 +212,167 @@ rt_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint3
 }
 
 // ---------------------------------------------------------------------------
-// stable LSD radix sort, 8-bit digits
-//   pass = histogram per tile -> exclusive scan (digit-major) -> scatter.
-//   The scatter ranks keys inside a warp with __match_any_sync, keeping the
-//   input order among equal digits, so every pass is stable.
+// stable LSD radix sort, 8-bit digits, one scatter launch per pass
+//   * one launch counts the digits of every pass at once (global histograms);
+//   * per pass, blocks take tile indices in launch order from an atomic
+//     counter, publish their tile's digit counts, and find each digit's
+//     offset by decoupled look-back (Merrill & Garland 2016; the single-pass
+//     radix sort of Adinets & Merrill 2022): walk back over the earlier tiles
+//     adding their published counts until one that already published its
+//     inclusive prefix.  Keys are ranked inside the tile with
+//     __match_any_sync per warp, keeping the input order among equal digits,
+//     so every pass is stable.
+// A tile index goes only to a block that is running, and every block
+// publishes its counts before it waits, so each wait ends; the wait is
+// bounded all the same: past the limit the block counts that tile's digit
+// itself from the keys, which gives the same number.
+// Look-back words (64-bit): bits 63-62 state (1 counts of the tile, 2
+// inclusive prefix), bits 61-58 the pass, bits 57-0 the count.
 // ---------------------------------------------------------------------------
 static constexpr int SORT_THREADS = 256;
 static constexpr int SORT_WARPS = SORT_THREADS / 32;
-static constexpr int SORT_ITEMS = 8;
-static constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 2048 keys
+static constexpr int SORT_ITEMS = 15;
+static constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 3840 keys
 static constexpr int RADIX = 256;
+static constexpr int SORT_MAX_PASSES = 8;
+static constexpr uint64_t LB_AGG = 1ull << 62, LB_INC = 2ull << 62, LB_COUNT = (1ull << 58) - 1;
+static constexpr int LB_SPIN = 1 << 14;
 
-__global__ void k_sort_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, int nblocks,
-                            uint32_t* __restrict__ counts) {
-    __shared__ uint32_t h[RADIX];
-    h[threadIdx.x] = 0;
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const uint64_t* __restrict__ keys, int64_t n,
+                                                            int begin_bit, int passes,
+                                                            uint32_t* __restrict__ counts) {
+    __shared__ uint32_t h[SORT_MAX_PASSES * RADIX];
+    for (int i = threadIdx.x; i < SORT_MAX_PASSES * RADIX; i += SORT_THREADS) h[i] = 0;
     __syncthreads();
-    int64_t base = (int64_t)blockIdx.x * SORT_TILE;
-#pragma unroll
-    for (int k = 0; k < SORT_ITEMS; k++) {
-        int64_t i = base + (int64_t)k * SORT_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[(uint32_t)(keys[i] >> shift) & 0xFFu], 1u);
+    for (int64_t i = (int64_t)blockIdx.x * SORT_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * SORT_THREADS) {
+        const uint64_t k = keys[i];
+        for (int p = 0; p < passes; p++) atomicAdd(&h[p * RADIX + ((uint32_t)(k >> (begin_bit + 8 * p)) & 0xFFu)], 1u);
     }
     __syncthreads();
-    counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    for (int i = threadIdx.x; i < passes * RADIX; i += SORT_THREADS)
+        if (h[i]) atomicAdd(&counts[i], h[i]);
 }
 
-__global__ void k_sort_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                               uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
-                               int nblocks, const uint32_t* __restrict__ offsets) {
+__device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.volatile.global.u64 %0, [%1];\n" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_volatile_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.volatile.global.u64 [%0], %1;\n" ::"l"(p), "l"(v) : "memory");
+}
+
+// digit d's count in tile j, recounted from the keys (the bounded wait's fallback)
+__device__ uint64_t tile_digit_count(const uint64_t* __restrict__ kin, int64_t n, int64_t j, int shift, uint32_t d) {
+    uint64_t c = 0;
+    const int64_t lo = j * SORT_TILE, hi = lo + SORT_TILE < n ? lo + SORT_TILE : n;
+    for (int64_t i = lo; i < hi; i++) c += ((uint32_t)(kin[i] >> shift) & 0xFFu) == d;
+    return c;
+}
+
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const uint64_t* __restrict__ kin,
+                                                               const uint32_t* __restrict__ vin,
+                                                               uint64_t* __restrict__ kout,
+                                                               uint32_t* __restrict__ vout, int64_t n, int shift,
+                                                               int pass, const uint32_t* __restrict__ counts,
+                                                               uint64_t* __restrict__ look,
+                                                               uint32_t* __restrict__ tile_ctr) {
     __shared__ uint32_t whist[SORT_WARPS][RADIX];
-    __shared__ uint32_t boff[RADIX];
+    __shared__ uint64_t boff[RADIX];
+    __shared__ uint32_t wsum[SORT_WARPS];
+    __shared__ uint32_t s_tile;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&whist[0][0])[i] = 0;
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    // exclusive prefix of the global digit counts (thread d: digit d)
+    const uint32_t d = threadIdx.x;
+    const uint32_t gc = counts[d];
+    uint32_t incl = gc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
     __syncthreads();
-    const int64_t wbase = (int64_t)blockIdx.x * SORT_TILE + (int64_t)warp * 32 * SORT_ITEMS;
+    uint32_t gbase = incl - gc;
+    for (int w = 0; w < warp; w++) gbase += wsum[w];
+    const int64_t tile = s_tile;
+    const int64_t wbase = tile * SORT_TILE + (int64_t)warp * 32 * SORT_ITEMS;
     uint64_t k[SORT_ITEMS];
     uint32_t v[SORT_ITEMS], rank[SORT_ITEMS], dig[SORT_ITEMS];
 #pragma unroll
     for (int it = 0; it < SORT_ITEMS; it++) {
-        int64_t idx = wbase + it * 32 + lane;
-        bool valid = idx < n;
+        const int64_t idx = wbase + it * 32 + lane;
+        const bool valid = idx < n;
         k[it] = valid ? kin[idx] : 0ull;
         v[it] = valid ? vin[idx] : 0u;
-        uint32_t d = valid ? ((uint32_t)(k[it] >> shift) & 0xFFu) : 0xFFFFFFFFu;
-        dig[it] = d;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t below = peers & ((1u << lane) - 1u);
+        const uint32_t dd = valid ? ((uint32_t)(k[it] >> shift) & 0xFFu) : 0xFFFFFFFFu;
+        dig[it] = dd;
+        const uint32_t peers = __match_any_sync(0xffffffffu, dd);
+        const uint32_t below = peers & ((1u << lane) - 1u);
         uint32_t r = 0;
-        if (valid) r = whist[warp][d] + __popc(below);
+        if (valid) r = whist[warp][dd] + __popc(below);
         rank[it] = r;
         __syncwarp();
-        if (valid && below == 0) whist[warp][d] += __popc(peers);
+        if (valid && below == 0) whist[warp][dd] += __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    {
-        int d = threadIdx.x;
-        uint32_t sum = 0;
+    // this tile's count of digit d; offsets of the warps inside the tile
+    uint32_t cnt = 0;
 #pragma unroll
-        for (int w = 0; w < SORT_WARPS; w++) {
-            uint32_t c = whist[w][d];
-            whist[w][d] = sum;
-            sum += c;
-        }
-        boff[d] = offsets[(int64_t)d * nblocks + blockIdx.x];
+    for (int w = 0; w < SORT_WARPS; w++) {
+        const uint32_t c = whist[w][d];
+        whist[w][d] = cnt;
+        cnt += c;
     }
+    const uint64_t tag = (uint64_t)pass << 58;
+    uint64_t* mine = look + tile * RADIX + d;
+    st_volatile_u64(mine, (tile == 0 ? LB_INC : LB_AGG) | tag | cnt);
+    uint64_t excl = 0;
+    for (int64_t j = tile - 1; j >= 0; j--) {
+        const uint64_t* w = look + j * RADIX + d;
+        uint64_t x = 0;
+        bool ok = false;
+        for (int spin = 0; spin < LB_SPIN; spin++) {
+            x = ld_volatile_u64(w);
+            if ((x >> 62) != 0 && ((x >> 58) & 15u) == (uint64_t)pass) {
+                ok = true;
+                break;
+            }
+        }
+        if (!ok) {  // not published in time: count it here
+            excl += tile_digit_count(kin, n, j, shift, d);
+            continue;
+        }
+        excl += x & LB_COUNT;
+        if ((x >> 62) == 2) break;
+    }
+    if (tile != 0) st_volatile_u64(mine, LB_INC | tag | (excl + cnt));
+    boff[d] = (uint64_t)gbase + excl;
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < SORT_ITEMS; it++) {
-        uint32_t d = dig[it];
-        if (d != 0xFFFFFFFFu) {
-            uint32_t pos = boff[d] + whist[warp][d] + rank[it];
-            kout[pos] = k[it];
-            vout[pos] = v[it];
+        const uint32_t dd = dig[it];
+        if (dd != 0xFFFFFFFFu) {
+            const uint64_t pos = boff[dd] + whist[warp][dd] + rank[it];
+            if (pos < (uint64_t)n) {  // always, for consistent counts
+                kout[pos] = k[it];
+                vout[pos] = v[it];
+            }
         }
     }
 }
 
+// scratch: global digit counts of every pass, the passes' tile counters and
+// one look-back word per (tile, digit), reused by the passes (tagged)
+static size_t sort_counts_bytes() { return sizeof(uint32_t) * SORT_MAX_PASSES * RADIX + 256; }
+
 size_t sort_temp_bytes(int64_t n) {
-    int64_t nb = (n + SORT_TILE - 1) / SORT_TILE;
-    size_t counts = (size_t)nb * RADIX * sizeof(uint32_t);
-    counts = (counts + 255) & ~(size_t)255;
-    return counts + scan_temp_bytes(nb * RADIX) + 256;
+    const int64_t tiles = (n + SORT_TILE - 1) / SORT_TILE;
+    return sort_counts_bytes() + sizeof(uint64_t) * RADIX * (size_t)std::max<int64_t>(tiles, 1) + 256;
 }
 
 rt_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
@@ -304,25 +382,26 @@ rt_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, u
         set_error("radix sort of %lld keys exceeds 32-bit positions", (long long)n);
         return RT_ERR_INVALID_ARG;
     }
-    int nb = (int)((n + SORT_TILE - 1) / SORT_TILE);
-    uint32_t* counts = (uint32_t*)temp;
-    size_t cbytes = ((size_t)nb * RADIX * sizeof(uint32_t) + 255) & ~(size_t)255;
-    void* scan_tmp = (char*)temp + cbytes;
+    const int passes = (end_bit - begin_bit + 7) / 8;
+    if (passes > SORT_MAX_PASSES || begin_bit < 0 || begin_bit + 8 * passes > 64) {
+        set_error("radix sort: bit range [%d, %d) not supported", begin_bit, end_bit);
+        return RT_ERR_INVALID_ARG;
+    }
+    const int64_t tiles = (n + SORT_TILE - 1) / SORT_TILE;
+    uint32_t* counts = (uint32_t*)temp;                                // [passes][256]
+    uint32_t* tile_ctr = counts + SORT_MAX_PASSES * RADIX;              // [passes]
+    uint64_t* look = (uint64_t*)((char*)temp + sort_counts_bytes());  // [tiles][256]
+    RR_CUDA(cudaMemsetAsync(temp, 0, sort_temp_bytes(n), s));
+    const int hist_grid = (int)std::min<int64_t>((n + SORT_THREADS - 1) / SORT_THREADS, 2 * (int64_t)device_sm_count());
+    RR_LAUNCH(k_sort_hist, hist_grid, SORT_THREADS, 0, s, keys, n, begin_bit, passes, counts);
     uint64_t *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
-    int passes = 0;
-    for (int shift = begin_bit; shift < end_bit; shift += 8) {
-        RR_LAUNCH(k_sort_hist, nb, SORT_THREADS, 0, s, ki, n, shift, nb, counts);
-        RR_TRY(exclusive_scan_u32(counts, counts, (int64_t)nb * RADIX, nullptr, scan_tmp, s));
-        RR_LAUNCH(k_sort_scatter, nb, SORT_THREADS, 0, s, ki, vi, ko, vo, n, shift, nb, counts);
+    for (int p = 0; p < passes; p++) {
+        RR_LAUNCH(k_sort_scatter, (unsigned)tiles, SORT_THREADS, 0, s, ki, vi, ko, vo, n, begin_bit + 8 * p, p,
+                  counts + p * RADIX, look, tile_ctr + p);
         RR_CUDA(cudaGetLastError());
-        uint64_t* tk = ki;
-        ki = ko;
-        ko = tk;
-        uint32_t* tv = vi;
-        vi = vo;
-        vo = tv;
-        passes++;
+        std::swap(ki, ko);
+        std::swap(vi, vo);
     }
     if (passes & 1) {
         RR_CUDA(cudaMemcpyAsync(keys, ki, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, s));

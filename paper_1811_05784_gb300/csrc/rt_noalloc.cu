@@ -33,14 +33,16 @@ __global__ void k_bin_sum(const uint64_t* __restrict__ keys, const uint32_t* __r
                           float* __restrict__ H);
 
 static constexpr int64_t STATIC_MAX = RT_RIR_STATIC_MAX_SOURCES;
-static constexpr size_t SORT_TILE_KEYS = 2048;  // keys per radix-sort tile (rt_common.cu)
+static constexpr size_t SORT_TILE_KEYS = 2048;  // sizing unit of the radix-sort scratch below
 static constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 static constexpr size_t OFF_KEYS = 0;
 static constexpr size_t OFF_KEYS_ALT = OFF_KEYS + align256(sizeof(uint64_t) * STATIC_MAX);
 static constexpr size_t OFF_VALS = OFF_KEYS_ALT + align256(sizeof(uint64_t) * STATIC_MAX);
 static constexpr size_t OFF_VALS_ALT = OFF_VALS + align256(sizeof(uint32_t) * STATIC_MAX);
 static constexpr size_t OFF_SORT = OFF_VALS_ALT + align256(sizeof(uint32_t) * STATIC_MAX);
-// radix-sort scratch: 256 counters per tile plus the scan's tile sums, with slack
+// radix-sort scratch: 1 KB per 2048 keys plus 64 KB, above what the sort asks
+// for (8 KB of digit counts and 2 KB of look-back words per 3840-key tile;
+// checked against sort_temp_bytes at run time)
 static constexpr size_t SORT_BYTES =
     align256(sizeof(uint32_t) * 256 * ((STATIC_MAX + SORT_TILE_KEYS - 1) / SORT_TILE_KEYS)) + 65536;
 static constexpr size_t SCRATCH_BYTES = OFF_SORT + SORT_BYTES;
