@@ -1184,12 +1184,26 @@ static rt_status gather_rooms(const rt_room* rooms, int n_rooms, HostRoomTables&
     return RT_OK;
 }
 
-template <class T>
-static rt_status upload(Arena& ar, const std::vector<T>& v, T** out, cudaStream_t s) {
-    RR_TRY(ar.alloc(out, std::max<size_t>(v.size(), 1)));
-    if (!v.empty()) RR_CUDA(cudaMemcpyAsync(*out, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, s));
-    return RT_OK;
-}
+// Host tables gathered into one buffer and copied with one call (16-byte
+// aligned slices), so that the GPU does not wait for a chain of small copies.
+struct Packer {
+    std::vector<unsigned char> host;
+    std::vector<std::pair<size_t, void**>> slots;
+    template <class T>
+    void add(const std::vector<T>& v, T** out) {
+        const size_t off = (host.size() + 15) & ~(size_t)15;
+        host.resize(off + std::max<size_t>(sizeof(T) * v.size(), 16), 0);
+        if (!v.empty()) memcpy(host.data() + off, v.data(), sizeof(T) * v.size());
+        slots.emplace_back(off, reinterpret_cast<void**>(out));
+    }
+    rt_status upload(Arena& ar, cudaStream_t s) {
+        unsigned char* d;
+        RR_TRY(ar.alloc(&d, host.size()));
+        RR_CUDA(cudaMemcpyAsync(d, host.data(), host.size(), cudaMemcpyHostToDevice, s));
+        for (auto& sl : slots) *sl.second = d + sl.first;
+        return RT_OK;
+    }
+};
 
 static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_trace_params* p,
                                   rt_image_sources** out) {
@@ -1245,19 +1259,23 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     float4* d_rcv;
     float *d_src, *d_refl;
     double *d_alpha64, *d_beta64, *d_src64, *d_rcv64, *d_srcdir = nullptr;
-    RR_TRY(upload(tmp, h.rooms, &d_rooms, s));
-    RR_TRY(upload(tmp, h.room_of_src, &d_room_of_src, s));
-    RR_TRY(upload(tmp, h.room_of_rcv, &d_room_of_rcv, s));
-    RR_TRY(upload(tmp, h.rcv, &d_rcv, s));
-    RR_TRY(upload(tmp, h.rcv_id, &d_rcv_id, s));
-    RR_TRY(upload(tmp, h.rcv_beg, &d_beg, s));
-    RR_TRY(upload(tmp, h.src, &d_src, s));
-    if (h.directional) RR_TRY(upload(tmp, h.srcdir, &d_srcdir, s));
-    RR_TRY(upload(tmp, h.refl, &d_refl, s));
-    RR_TRY(upload(tmp, h.alpha64, &d_alpha64, s));
-    RR_TRY(upload(tmp, h_beta64, &d_beta64, s));
-    RR_TRY(upload(tmp, h.src64, &d_src64, s));
-    RR_TRY(upload(tmp, h.rcv64, &d_rcv64, s));
+    {
+        Packer pk;
+        pk.add(h.rooms, &d_rooms);
+        pk.add(h.room_of_src, &d_room_of_src);
+        pk.add(h.room_of_rcv, &d_room_of_rcv);
+        pk.add(h.rcv, &d_rcv);
+        pk.add(h.rcv_id, &d_rcv_id);
+        pk.add(h.rcv_beg, &d_beg);
+        pk.add(h.src, &d_src);
+        if (h.directional) pk.add(h.srcdir, &d_srcdir);
+        pk.add(h.refl, &d_refl);
+        pk.add(h.alpha64, &d_alpha64);
+        pk.add(h_beta64, &d_beta64);
+        pk.add(h.src64, &d_src64);
+        pk.add(h.rcv64, &d_rcv64);
+        RR_TRY(pk.upload(tmp, s));
+    }
 
     // scratch: queues and counters (from the workspace when given)
     Queue q[2];
@@ -1288,6 +1306,30 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
         RR_TRY(tmp.alloc(&counters, n_counters));
         RR_TRY(tmp.alloc(&n2d, 2));
     }
+    // primary rays first, so that the GPU works while the host prepares the rest
+    struct Events {
+        cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+        ~Events() {
+            for (auto x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    for (auto& x : ev.e) RR_CUDA(cudaEventCreate(&x));
+    int64_t F = 1, F1 = 1;  // largest Fibonacci number <= sqrt(per_src)
+    while (F1 * F1 <= per_src) {
+        int64_t t = F + F1;
+        F = F1;
+        F1 = t;
+    }
+    auto gen_rays = [&]() -> rt_status {
+        RR_CUDA(cudaEventRecord(ev.e[0], s));
+        RR_LAUNCH(k_gen_rays, grid_of(n_traced, 256), 256, 0, s, q[0], d_src, d_srcdir, n_traced, per_src,
+                  p->ray_begin, N, F);
+        RR_CUDA(cudaGetLastError());
+        RR_CUDA(cudaEventRecord(ev.e[1], s));
+        return RT_OK;
+    };
+    RR_TRY(gen_rays());
     int32_t* hist;
     float4* ray_e;
     float* ray_len;
@@ -1324,14 +1366,6 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     unsigned long long cap = (unsigned long long)std::min<int64_t>(
         std::max<int64_t>(1 << 20, 2 * n_traced), std::max<int64_t>(1, n_traced * (int64_t)B * std::max(R, 1)));
     if (ws && ws->last_records + ws->last_records / 4 > cap) cap = ws->last_records + ws->last_records / 4;
-    struct Events {
-        cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
-        ~Events() {
-            for (auto x : e)
-                if (x) cudaEventDestroy(x);
-        }
-    } ev;
-    for (auto& x : ev.e) RR_CUDA(cudaEventCreate(&x));
     unsigned long long n_rec = 0, n2[2] = {0, 0};
     std::vector<unsigned int> h_cnt((size_t)n_counters);
     Arena rec_arena(s);
@@ -1349,17 +1383,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
         RR_CUDA(cudaMemsetAsync(n2d, 0, 2 * sizeof(unsigned long long), s));
         unsigned int n0 = (unsigned int)n_traced;
         RR_CUDA(cudaMemcpyAsync(counters, &n0, sizeof n0, cudaMemcpyHostToDevice, s));
-        RR_CUDA(cudaEventRecord(ev.e[0], s));
-        int64_t F = 1, F1 = 1;  // largest Fibonacci number <= sqrt(per_src)
-        while (F1 * F1 <= per_src) {
-            int64_t t = F + F1;
-            F = F1;
-            F1 = t;
-        }
-        RR_LAUNCH(k_gen_rays, grid_of(n_traced, 256), 256, 0, s, q[0], d_src, d_srcdir, n_traced, per_src,
-                  p->ray_begin, N, F);
-        RR_CUDA(cudaGetLastError());
-        RR_CUDA(cudaEventRecord(ev.e[1], s));
+        if (attempt > 0) RR_TRY(gen_rays());  // the first attempt consumed the queue
         BounceArgs a{};
         a.rooms = d_rooms;
         a.room_of_src = d_room_of_src;
