@@ -45,9 +45,11 @@ __device__ __forceinline__ float ord2f(unsigned int o) {
 }
 
 // pass 1: validate, convert to float32, per-triangle normal, bounds, id ranges.
-// Bounds and id ranges are reduced within each warp first (one atomic per
-// warp and quantity instead of one per triangle).
-__global__ void k_tri_prep(const double* __restrict__ V, int64_t nV, const int32_t* __restrict__ T, int64_t M,
+// Bounds and id ranges are reduced within each warp, then within the block
+// (one atomic per block and quantity instead of one per triangle).
+static constexpr int TRI_PREP_THREADS = 256;
+
+__global__ void __launch_bounds__(TRI_PREP_THREADS) k_tri_prep(const double* __restrict__ V, int64_t nV, const int32_t* __restrict__ T, int64_t M,
                            const int32_t* __restrict__ mat, const int32_t* __restrict__ surf,
                            float4* __restrict__ tv, float4* __restrict__ nrm, BuildMeta* meta) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -106,39 +108,63 @@ __global__ void k_tri_prep(const double* __restrict__ V, int64_t nV, const int32
     smin = __reduce_min_sync(full, smin);
     mmax = __reduce_max_sync(full, mmax);
     mmin = __reduce_min_sync(full, mmin);
-    if ((threadIdx.x & 31) == 0 && (int64_t)blockIdx.x * blockDim.x + threadIdx.x < M) {
-        for (int k = 0; k < 3; k++) {
-            atomicMin(&meta->cmin[k], cmin[k]);
-            atomicMax(&meta->cmax[k], cmax[k]);
+    // then across the block: one atomic per block and quantity
+    __shared__ unsigned int s_u[TRI_PREP_THREADS / 32][6];
+    __shared__ int s_i[TRI_PREP_THREADS / 32][4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        for (int k = 0; k < 3; k++) s_u[warp][k] = cmin[k], s_u[warp][3 + k] = cmax[k];
+        s_i[warp][0] = smax, s_i[warp][1] = smin, s_i[warp][2] = mmax, s_i[warp][3] = mmin;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = TRI_PREP_THREADS / 32;
+        if (lane < 3) {
+            unsigned int lo = s_u[0][lane], hi = s_u[0][3 + lane];
+            for (int w = 1; w < nw; w++) lo = min(lo, s_u[w][lane]), hi = max(hi, s_u[w][3 + lane]);
+            atomicMin(&meta->cmin[lane], lo);
+            atomicMax(&meta->cmax[lane], hi);
+        } else if (lane < 7) {
+            const int q = lane - 3;
+            int v = s_i[0][q];
+            for (int w = 1; w < nw; w++) v = (q & 1) ? min(v, s_i[w][q]) : max(v, s_i[w][q]);
+            if (q == 0) atomicMax(&meta->max_surf, v);
+            if (q == 1) atomicMin(&meta->min_surf, v);
+            if (q == 2) atomicMax(&meta->max_mat, v);
+            if (q == 3) atomicMin(&meta->min_mat, v);
         }
-        atomicMax(&meta->max_surf, smax);
-        atomicMin(&meta->min_surf, smin);
-        atomicMax(&meta->max_mat, mmax);
-        atomicMin(&meta->min_mat, mmin);
     }
 }
 
-// lowest triangle id per surface
-__global__ void k_surf_first(const int32_t* __restrict__ surf, int64_t M, int32_t* __restrict__ first) {
+// Surface tables.  They run on the raw input before it has been validated
+// on the host, so every id and index is checked before it is used: surface
+// ids outside [0, cap) and vertex indices outside [0, nV) are skipped (the
+// host then reports them from the build's own checks).
+// lowest triangle id per surface (first[] starts at 0x7F7F7F7F >= M)
+__global__ void k_surf_first(const int32_t* __restrict__ surf, int64_t M, int64_t cap, int32_t* __restrict__ first) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < M) atomicMin(&first[surf[t]], (int32_t)t);
+    if (t >= M) return;
+    const int32_t sid = surf[t];
+    if (sid >= 0 && sid < cap) atomicMin(&first[sid], (int32_t)t);
 }
 
 // FP64 plane of each surface from its lowest-id triangle; its material
-__global__ void k_planes(const double* __restrict__ V, const int32_t* __restrict__ T,
-                         const int32_t* __restrict__ mat, const int32_t* __restrict__ first, int S,
+__global__ void k_planes(const double* __restrict__ V, int64_t nV, const int32_t* __restrict__ T, int64_t M,
+                         const int32_t* __restrict__ mat, const int32_t* __restrict__ first, int64_t S,
                          Plane* __restrict__ planes, int32_t* __restrict__ mat_of_surf) {
-    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= S) return;
     int32_t t = first[s];
-    if (t == INT_MAX) {  // unused surface id
-        planes[s] = Plane{0.0, 0.0, 0.0, 0.0};
-        mat_of_surf[s] = 0;
+    int32_t ia = 0, ib = 0, ic = 0;
+    if (t >= 0 && t < M) ia = T[3 * (int64_t)t], ib = T[3 * (int64_t)t + 1], ic = T[3 * (int64_t)t + 2];
+    if (t < 0 || t >= M || ia < 0 || ib < 0 || ic < 0 || ia >= nV || ib >= nV || ic >= nV) {
+        planes[s] = Plane{0.0, 0.0, 0.0, 0.0};  // unused surface id, or input the host rejects
+        mat_of_surf[s] = t >= 0 && t < M ? mat[t] : 0;
         return;
     }
-    const double* a = V + 3 * (int64_t)T[3 * (int64_t)t];
-    const double* b = V + 3 * (int64_t)T[3 * (int64_t)t + 1];
-    const double* c = V + 3 * (int64_t)T[3 * (int64_t)t + 2];
+    const double* a = V + 3 * (int64_t)ia;
+    const double* b = V + 3 * (int64_t)ib;
+    const double* c = V + 3 * (int64_t)ic;
     double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
     double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
     double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
@@ -152,9 +178,11 @@ __global__ void k_planes(const double* __restrict__ V, const int32_t* __restrict
 }
 
 __global__ void k_surf_check(const int32_t* __restrict__ surf, const int32_t* __restrict__ mat, int64_t M,
-                             const int32_t* __restrict__ mat_of_surf, BuildMeta* meta) {
+                             int64_t cap, const int32_t* __restrict__ mat_of_surf, BuildMeta* meta) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < M && mat[t] != mat_of_surf[surf[t]]) atomicAdd(&meta->mixed_material, 1u);
+    if (t >= M) return;
+    const int32_t sid = surf[t];
+    if (sid >= 0 && sid < cap && mat[t] != mat_of_surf[sid]) atomicAdd(&meta->mixed_material, 1u);
 }
 
 // 63-bit Morton code of the float32 centroid within the centroid bounds
@@ -653,7 +681,8 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out, 
     float4 *tv, *tri_nrm;
     RR_TRY(tmp.alloc(&tv, 3 * M));
     RR_TRY(keep_arena.alloc(&tri_nrm, M));
-    RR_LAUNCH(k_tri_prep, grid_of(M, 256), 256, 0, s, dV, nV, dT, M, dmat, dsurf, tv, tri_nrm, meta);
+    RR_LAUNCH(k_tri_prep, grid_of(M, TRI_PREP_THREADS), TRI_PREP_THREADS, 0, s, dV, nV, dT, M, dmat, dsurf, tv,
+              tri_nrm, meta);
     RR_CUDA(cudaGetLastError());
     // Everything up to the 4-wide nodes depends only on M, so it is queued
     // before the first synchronisation; invalid input (reported below) was
@@ -742,6 +771,27 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out, 
         RR_LAUNCH(k_reorder, grid_of(M, 256), 256, 0, s, tv, vals, M, tris, pos_of);
         RR_CUDA(cudaGetLastError());
     }
+    // surface tables, sized for ids below M (the usual dense numbering), queued
+    // before the synchronisation as well; sparse ids larger than that are
+    // handled after it
+    int32_t *mat_of_surf = nullptr, *surf_of = nullptr;
+    Plane* planes = nullptr;
+    RR_TRY(keep_arena.alloc(&surf_of, M));
+    RR_CUDA(cudaMemcpyAsync(surf_of, dsurf, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, s));
+    auto surface_tables = [&](int64_t cap) -> rt_status {
+        int32_t* sfirst;
+        RR_TRY(tmp.alloc(&sfirst, cap));
+        RR_TRY(keep_arena.alloc(&mat_of_surf, cap));
+        RR_TRY(keep_arena.alloc(&planes, cap));
+        RR_CUDA(cudaMemsetAsync(sfirst, 0x7F, sizeof(int32_t) * cap, s));
+        RR_CUDA(cudaMemsetAsync(&meta->mixed_material, 0, sizeof(unsigned int), s));
+        RR_LAUNCH(k_surf_first, grid_of(M, 256), 256, 0, s, dsurf, M, cap, sfirst);
+        RR_LAUNCH(k_planes, grid_of(cap, 128), 128, 0, s, dV, nV, dT, M, dmat, sfirst, cap, planes, mat_of_surf);
+        RR_LAUNCH(k_surf_check, grid_of(M, 256), 256, 0, s, dsurf, dmat, M, cap, mat_of_surf, meta);
+        RR_CUDA(cudaGetLastError());
+        return RT_OK;
+    };
+    RR_TRY(surface_tables(M));
     uint32_t nn = 1;
     if (total) RR_CUDA(cudaMemcpyAsync(&nn, total, sizeof nn, cudaMemcpyDeviceToHost, s));
     RR_CUDA(cudaMemcpyAsync(&hm, meta, sizeof hm, cudaMemcpyDeviceToHost, s));
@@ -768,25 +818,12 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out, 
     tree->n_surfaces = S;
     tree->n_materials = hm.max_mat + 1;
 
-    int32_t *sfirst, *mat_of_surf, *surf_of;
-    Plane* planes;
-    RR_TRY(tmp.alloc(&sfirst, S));
-    RR_TRY(keep_arena.alloc(&mat_of_surf, S));
-    RR_TRY(keep_arena.alloc(&planes, S));
-    RR_TRY(keep_arena.alloc(&surf_of, M));
-    RR_CUDA(cudaMemcpyAsync(surf_of, dsurf, sizeof(int32_t) * M, cudaMemcpyDeviceToDevice, s));
-    {
-        std::vector<int32_t> init((size_t)S, INT_MAX);
-        RR_CUDA(cudaMemcpyAsync(sfirst, init.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, s));
-        RR_LAUNCH(k_surf_first, grid_of(M, 256), 256, 0, s, dsurf, M, sfirst);
-        RR_LAUNCH(k_planes, grid_of(S, 128), 128, 0, s, dV, dT, dmat, sfirst, S, planes, mat_of_surf);
-        RR_LAUNCH(k_surf_check, grid_of(M, 256), 256, 0, s, dsurf, dmat, M, mat_of_surf, meta);
-        RR_CUDA(cudaGetLastError());
-        // init is a pageable host buffer: the copy completes before returning
+    unsigned int mixed = hm.mixed_material;
+    if (S > M) {  // sparse surface ids: the tables again, at their full size
+        RR_TRY(surface_tables(S));
+        RR_CUDA(cudaMemcpyAsync(&mixed, &meta->mixed_material, sizeof mixed, cudaMemcpyDeviceToHost, s));
+        RR_CUDA(cudaStreamSynchronize(s));
     }
-    unsigned int mixed = 0;
-    RR_CUDA(cudaMemcpyAsync(&mixed, &meta->mixed_material, sizeof mixed, cudaMemcpyDeviceToHost, s));
-    RR_CUDA(cudaStreamSynchronize(s));
     if (mixed) {
         set_error("rt_build_tree: %u triangles differ in material from their surface", mixed);
         return RT_ERR_INVALID_ARG;

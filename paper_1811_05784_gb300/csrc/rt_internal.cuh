@@ -8,9 +8,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/roomrays.h"
@@ -71,6 +73,28 @@ struct Arena {
         std::vector<void*> v;
         v.swap(ptrs);
         return v;
+    }
+};
+
+// Several arrays carved out of one allocation (256-byte aligned slices): fewer
+// allocator calls, and blocks of the same size from one call to the next, so
+// the stream-ordered pool reuses them instead of growing.
+struct Carve {
+    size_t total = 0;
+    std::vector<std::pair<size_t, void*>> parts;  // offset, address of the caller's pointer
+    std::vector<void (*)(void*, unsigned char*)> setters;
+    template <class T>
+    void add(T** out, size_t count) {
+        const size_t off = (total + 255) & ~(size_t)255;
+        total = off + std::max<size_t>(count * sizeof(T), 16);
+        parts.emplace_back(off, (void*)out);
+        setters.push_back([](void* o, unsigned char* p) { *static_cast<T**>(o) = reinterpret_cast<T*>(p); });
+    }
+    rt_status alloc(Arena& ar) {
+        unsigned char* base;
+        RR_TRY(ar.alloc(&base, total));
+        for (size_t k = 0; k < parts.size(); k++) setters[k](parts[k].second, base + parts[k].first);
+        return RT_OK;
     }
 };
 

@@ -750,6 +750,8 @@ struct ReconArgs {
 };
 
 // one thread per image source: beam size, representative ray, FP64 mirror chain
+static constexpr int RECON_GROUP = 4;
+
 __global__ void k_reconstruct(ReconArgs a) {
     const unsigned int u = blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= *a.n_unique_dev) return;
@@ -763,21 +765,40 @@ __global__ void k_reconstruct(ReconArgs a) {
     double prod[RT_N_BANDS];
 #pragma unroll
     for (int f = 0; f < RT_N_BANDS; f++) prod[f] = 1.0;
-    for (int k = 0; k < m; k++) {
-        int tri = a.hist[(int64_t)k * a.n_traced + rep];
-        if (tri < 0) {  // cannot happen for a consistent history; reported, never read
-            atomicOr(a.status, ST_HISTORY);
-            break;
-        }
-        int sid = rm.surf_of[tri];
-        Plane P = rm.planes[sid];
-        double dist = P.x * x + P.y * y + P.z * z - P.w;
-        x -= 2.0 * dist * P.x;
-        y -= 2.0 * dist * P.y;
-        z -= 2.0 * dist * P.z;
-        const double* al = a.alpha64 + 8 * (rm.mat_base + rm.mat_of_surf[sid]);
+    // the sequence is read RECON_GROUP reflections at a time: the history,
+    // surface and plane loads of a group are independent of one another, so
+    // they are issued together instead of one dependent chain per reflection
+    bool ok = true;
+    for (int k0 = 0; k0 < m && ok; k0 += RECON_GROUP) {
+        int tri[RECON_GROUP], sid[RECON_GROUP];
 #pragma unroll
-        for (int f = 0; f < RT_N_BANDS; f++) prod[f] *= (1.0 - al[f]);
+        for (int j = 0; j < RECON_GROUP; j++)
+            tri[j] = k0 + j < m ? a.hist[(int64_t)(k0 + j) * a.n_traced + rep] : 0;
+#pragma unroll
+        for (int j = 0; j < RECON_GROUP; j++) sid[j] = tri[j] >= 0 ? rm.surf_of[tri[j]] : 0;
+        Plane P[RECON_GROUP];
+        int mt[RECON_GROUP];
+#pragma unroll
+        for (int j = 0; j < RECON_GROUP; j++) {
+            P[j] = rm.planes[sid[j]];
+            mt[j] = rm.mat_of_surf[sid[j]];
+        }
+#pragma unroll
+        for (int j = 0; j < RECON_GROUP; j++) {
+            if (k0 + j >= m) break;
+            if (tri[j] < 0) {  // cannot happen for a consistent history; reported, never read
+                atomicOr(a.status, ST_HISTORY);
+                ok = false;
+                break;
+            }
+            double dist = P[j].x * x + P[j].y * y + P[j].z * z - P[j].w;
+            x -= 2.0 * dist * P[j].x;
+            y -= 2.0 * dist * P[j].y;
+            z -= 2.0 * dist * P[j].z;
+            const double* al = a.alpha64 + 8 * (rm.mat_base + mt[j]);
+#pragma unroll
+            for (int f = 0; f < RT_N_BANDS; f++) prod[f] *= (1.0 - al[f]);
+        }
     }
     const double* xm = a.rcv64 + 3 * rcv;
     double dx = x - xm[0], dy = y - xm[1], dz = z - xm[2];
@@ -797,9 +818,6 @@ __global__ void k_reconstruct(ReconArgs a) {
 
 static unsigned grid_of(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-// ---------------------------------------------------------------------------
-// host driver
-// ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
@@ -1334,10 +1352,14 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     float4* ray_e;
     float* ray_len;
     int32_t* ray_hits;
-    RR_TRY(keep.alloc(&hist, (int64_t)B * n_traced));
-    RR_TRY(keep.alloc(&ray_e, 2 * n_traced));
-    RR_TRY(keep.alloc(&ray_len, n_traced));
-    RR_TRY(keep.alloc(&ray_hits, n_traced));
+    {
+        Carve cv;
+        cv.add(&hist, (size_t)B * n_traced);
+        cv.add(&ray_e, 2 * (size_t)n_traced);
+        cv.add(&ray_len, (size_t)n_traced);
+        cv.add(&ray_hits, (size_t)n_traced);
+        RR_TRY(cv.alloc(keep));
+    }
 
     // bounce-kernel configuration
     const int a_step_cap = p->max_node_visits > 0 ? p->max_node_visits : DEFAULT_NODE_VISITS;
@@ -1373,11 +1395,15 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     float* rec_len = nullptr;
     uint64_t* rec_key = nullptr;
     for (int attempt = 0; attempt < 2; attempt++) {
-        RR_TRY(rec_arena.alloc(&rec_rcv, (int64_t)cap));
-        RR_TRY(rec_arena.alloc(&rec_ray, (int64_t)cap));
-        RR_TRY(rec_arena.alloc(&rec_m, (int64_t)cap));
-        RR_TRY(rec_arena.alloc(&rec_len, (int64_t)cap));
-        RR_TRY(rec_arena.alloc(&rec_key, (int64_t)cap));
+        {
+            Carve cv;
+            cv.add(&rec_rcv, (size_t)cap);
+            cv.add(&rec_ray, (size_t)cap);
+            cv.add(&rec_m, (size_t)cap);
+            cv.add(&rec_len, (size_t)cap);
+            cv.add(&rec_key, (size_t)cap);
+            RR_TRY(cv.alloc(rec_arena));
+        }
         RR_CUDA(cudaMemsetAsync(hist, 0xFF, sizeof(int32_t) * (size_t)B * n_traced, s));
         RR_CUDA(cudaMemsetAsync(counters, 0, sizeof(unsigned int) * n_counters, s));
         RR_CUDA(cudaMemsetAsync(n2d, 0, 2 * sizeof(unsigned long long), s));
@@ -1470,32 +1496,38 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     int32_t *o_rcv, *o_order, *o_count, *o_rep;
     double *o_pos, *o_dist, *o_time, *o_energy;
     const int64_t ncap = std::max<int64_t>(nr, 1);
-    RR_TRY(keep.alloc(&o_rcv, ncap));
-    RR_TRY(keep.alloc(&o_order, ncap));
-    RR_TRY(keep.alloc(&o_count, ncap));
-    RR_TRY(keep.alloc(&o_rep, ncap));
-    RR_TRY(keep.alloc(&o_pos, 3 * ncap));
-    RR_TRY(keep.alloc(&o_dist, ncap));
-    RR_TRY(keep.alloc(&o_time, ncap));
-    RR_TRY(keep.alloc(&o_energy, 8 * ncap));
+    {
+        Carve cv;
+        cv.add(&o_rcv, (size_t)ncap);
+        cv.add(&o_order, (size_t)ncap);
+        cv.add(&o_count, (size_t)ncap);
+        cv.add(&o_rep, (size_t)ncap);
+        cv.add(&o_pos, 3 * (size_t)ncap);
+        cv.add(&o_dist, (size_t)ncap);
+        cv.add(&o_time, (size_t)ncap);
+        cv.add(&o_energy, 8 * (size_t)ncap);
+        RR_TRY(cv.alloc(keep));
+    }
     unsigned int n_unique = 0;
     unsigned long long collisions = 0;
     if (nr > 0) {
         uint64_t *keys, *keys_alt;
         uint32_t *vals, *vals_alt, *flags, *segid, *heads, *nuniq;
         unsigned long long* d_coll;
-        RR_TRY(tmp.alloc(&keys, nr));
-        RR_TRY(tmp.alloc(&keys_alt, nr));
-        RR_TRY(tmp.alloc(&vals, nr));
-        RR_TRY(tmp.alloc(&vals_alt, nr));
-        RR_TRY(tmp.alloc(&flags, nr));
-        RR_TRY(tmp.alloc(&segid, nr));
-        RR_TRY(tmp.alloc(&heads, nr + 1));
-        RR_TRY(tmp.alloc(&nuniq, 1));
-        RR_TRY(tmp.alloc(&d_coll, 1));
-        void *sort_tmp, *scan_tmp;
-        RR_TRY(tmp.alloc((char**)&sort_tmp, sort_temp_bytes(nr)));
-        RR_TRY(tmp.alloc((char**)&scan_tmp, scan_temp_bytes(nr)));
+        Carve cv;
+        cv.add(&keys, (size_t)nr);
+        cv.add(&keys_alt, (size_t)nr);
+        cv.add(&vals, (size_t)nr);
+        cv.add(&vals_alt, (size_t)nr);
+        cv.add(&flags, (size_t)nr);
+        cv.add(&segid, (size_t)nr);
+        cv.add(&heads, (size_t)nr + 1);
+        cv.add(&nuniq, 1);
+        cv.add(&d_coll, 1);
+        unsigned char *sort_tmp, *scan_tmp;
+        cv.add(&sort_tmp, sort_temp_bytes(nr));
+        cv.add(&scan_tmp, scan_temp_bytes(nr));
+        RR_TRY(cv.alloc(tmp));
         RR_CUDA(cudaMemsetAsync(d_coll, 0, sizeof(unsigned long long), s));
         RR_LAUNCH(k_dedup_init, grid_of(nr, 256), 256, 0, s, rec_key, nr, keys, vals);
         RR_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, nr, 0, 64, sort_tmp, s));

@@ -449,6 +449,29 @@ def test_errors_are_reported():
     with pytest.raises(rt.RtError) as e:
         rt.rt_build_tree(sc.vertices, sc.tris, mixed, sc.surface_id)
     assert e.value.status == rt.RT_ERR_INVALID_ARG
+    neg = sc.surface_id.copy()
+    neg[5] = -3
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_build_tree(sc.vertices, sc.tris, sc.material_id, neg)
+    assert e.value.status == rt.RT_ERR_INVALID_ARG
+
+
+def test_sparse_surface_ids():
+    """Surface ids far above the triangle count (tables sized by the largest
+    id) trace exactly like the dense numbering of the same surfaces."""
+    sc = scenes.shoebox(n_rays=5000, n_bounces=12)
+    dense = rt.rt_trace(_tree(sc), **rt.scene_args(sc))
+    t_sp = rt.rt_build_tree(sc.vertices, sc.tris, sc.material_id, sc.surface_id * 100_003 + 7)
+    assert t_sp.info()["n_surfaces"] == 5 * 100_003 + 8
+    sparse = rt.rt_trace(t_sp, **rt.scene_args(sc))
+    assert torch.equal(dense.hist, sparse.hist) and torch.equal(dense.ray_energy, sparse.ray_energy)
+    assert sparse.n == dense.n
+    # image sources of equal distance exist (5^2 + 15^2 = 9^2 + 13^2 m^2 in
+    # the unfolded lattice): match them by reflection order too
+    order = lambda x: np.lexsort((x.order.cpu().numpy(), x.count.cpu().numpy(), x.dist.cpu().numpy()))
+    for f in ("count", "dist", "order", "energy"):
+        a, b = getattr(dense, f).cpu().numpy(), getattr(sparse, f).cpu().numpy()
+        assert np.array_equal(a[order(dense)], b[order(sparse)]), f
 
 
 def test_node_visit_cap_is_reported():
