@@ -84,7 +84,8 @@ __global__ void __launch_bounds__(TRI_PREP_THREADS) k_tri_prep(const double* __r
             len = 1.0;
         }
         const int32_t s = surf[t], m = mat[t];
-        nrm[t] = make_float4((float)(n[0] / len), (float)(n[1] / len), (float)(n[2] / len), __int_as_float(s));
+        const double il = 1.0 / len;  // one FP64 division instead of three (FP64 division is costly)
+        nrm[t] = make_float4((float)(n[0] * il), (float)(n[1] * il), (float)(n[2] * il), __int_as_float(s));
         float4 fa = make_float4((float)a[0], (float)a[1], (float)a[2], __int_as_float((int)t));
         float4 fb = make_float4((float)b[0], (float)b[1], (float)b[2], __int_as_float(s));
         float4 fc = make_float4((float)c[0], (float)c[1], (float)c[2], 0.f);
@@ -141,11 +142,14 @@ __global__ void __launch_bounds__(TRI_PREP_THREADS) k_tri_prep(const double* __r
 // ids outside [0, cap) and vertex indices outside [0, nV) are skipped (the
 // host then reports them from the build's own checks).
 // lowest triangle id per surface (first[] starts at 0x7F7F7F7F >= M)
+// (lanes of a warp holding the same surface send one atomic: the lowest lane's
+// triangle, the lowest id among them)
 __global__ void k_surf_first(const int32_t* __restrict__ surf, int64_t M, int64_t cap, int32_t* __restrict__ first) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= M) return;
-    const int32_t sid = surf[t];
-    if (sid >= 0 && sid < cap) atomicMin(&first[sid], (int32_t)t);
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int32_t sid = t < M ? surf[t] : -1;
+    const unsigned int peers = __match_any_sync(0xffffffffu, sid);
+    if (sid >= 0 && sid < cap && (peers & ((1u << lane) - 1u)) == 0) atomicMin(&first[sid], (int32_t)t);
 }
 
 // FP64 plane of each surface from its lowest-id triangle; its material

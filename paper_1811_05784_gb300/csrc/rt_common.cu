@@ -237,6 +237,8 @@ static constexpr int RADIX = 256;
 static constexpr int SORT_MAX_PASSES = 8;
 static constexpr uint64_t LB_AGG = 1ull << 62, LB_INC = 2ull << 62, LB_COUNT = (1ull << 58) - 1;
 static constexpr int LB_SPIN = 1 << 14;
+static constexpr int LB_WINDOW = 8;
+static constexpr int DIRECT_MAX_TILES = 256;  // up to this many tiles the prefix is summed directly
 
 __global__ void __launch_bounds__(SORT_THREADS) k_sort_hist(const uint64_t* __restrict__ keys, int64_t n,
                                                             int begin_bit, int passes,
@@ -259,6 +261,12 @@ __device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t* p) {
     return v;
 }
 
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.volatile.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void st_volatile_u64(uint64_t* p, uint64_t v) {
     asm volatile("st.volatile.global.u64 [%0], %1;\n" ::"l"(p), "l"(v) : "memory");
 }
@@ -277,11 +285,14 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const uint64_t* _
                                                                uint32_t* __restrict__ vout, int64_t n, int shift,
                                                                int pass, const uint32_t* __restrict__ counts,
                                                                uint64_t* __restrict__ look,
-                                                               uint32_t* __restrict__ tile_ctr) {
+                                                               uint32_t* __restrict__ rows,
+                                                               uint32_t* __restrict__ ready,
+                                                               uint32_t* __restrict__ tile_ctr, int64_t tiles) {
     __shared__ uint32_t whist[SORT_WARPS][RADIX];
     __shared__ uint64_t boff[RADIX];
     __shared__ uint32_t wsum[SORT_WARPS];
     __shared__ uint32_t s_tile;
+    __shared__ uint32_t late[DIRECT_MAX_TILES / 32];  // tiles whose counts did not appear in time
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < SORT_WARPS * RADIX; i += SORT_THREADS) (&whist[0][0])[i] = 0;
     if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
@@ -302,12 +313,17 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const uint64_t* _
     const int64_t wbase = tile * SORT_TILE + (int64_t)warp * 32 * SORT_ITEMS;
     uint64_t k[SORT_ITEMS];
     uint32_t v[SORT_ITEMS], rank[SORT_ITEMS], dig[SORT_ITEMS];
+    // all loads first: the warp synchronisations of the ranking below would
+    // otherwise keep each load behind the previous item's ranking
 #pragma unroll
     for (int it = 0; it < SORT_ITEMS; it++) {
         const int64_t idx = wbase + it * 32 + lane;
-        const bool valid = idx < n;
-        k[it] = valid ? kin[idx] : 0ull;
-        v[it] = valid ? vin[idx] : 0u;
+        k[it] = idx < n ? kin[idx] : 0ull;
+        v[it] = idx < n ? vin[idx] : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; it++) {
+        const bool valid = wbase + it * 32 + lane < n;
         const uint32_t dd = valid ? ((uint32_t)(k[it] >> shift) & 0xFFu) : 0xFFFFFFFFu;
         dig[it] = dd;
         const uint32_t peers = __match_any_sync(0xffffffffu, dd);
@@ -328,29 +344,79 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const uint64_t* _
         whist[w][d] = cnt;
         cnt += c;
     }
-    const uint64_t tag = (uint64_t)pass << 58;
-    uint64_t* mine = look + tile * RADIX + d;
-    st_volatile_u64(mine, (tile == 0 ? LB_INC : LB_AGG) | tag | cnt);
     uint64_t excl = 0;
-    for (int64_t j = tile - 1; j >= 0; j--) {
-        const uint64_t* w = look + j * RADIX + d;
-        uint64_t x = 0;
-        bool ok = false;
-        for (int spin = 0; spin < LB_SPIN; spin++) {
-            x = ld_volatile_u64(w);
-            if ((x >> 62) != 0 && ((x >> 58) & 15u) == (uint64_t)pass) {
-                ok = true;
-                break;
+    if (tiles <= DIRECT_MAX_TILES) {
+        // few tiles: publish this tile's counts and a ready flag, wait for the
+        // earlier tiles' flags (one per thread, in parallel), then sum their
+        // counts with independent loads
+        if (d < DIRECT_MAX_TILES / 32) late[d] = 0;
+        __stcg(rows + tile * RADIX + d, cnt);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicExch(ready + tile, (uint32_t)pass + 1u);
+        }
+        for (int64_t i = threadIdx.x; i < tile; i += SORT_THREADS) {
+            bool ok = false;
+            for (int spin = 0; spin < LB_SPIN && !ok; spin++)
+                ok = ld_volatile_u32(ready + i) == (uint32_t)pass + 1u;
+            if (!ok) atomicOr(&late[i >> 5], 1u << (i & 31));
+        }
+        __threadfence();
+        __syncthreads();
+        uint32_t part[4] = {0u, 0u, 0u, 0u};
+        int64_t i = 0;
+        for (; i + 4 <= tile; i += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint32_t c = __ldcg(rows + (i + q) * RADIX + d);
+                part[q] += (late[(i + q) >> 5] >> ((i + q) & 31)) & 1u ? 0u : c;
             }
         }
-        if (!ok) {  // not published in time: count it here
-            excl += tile_digit_count(kin, n, j, shift, d);
-            continue;
+        for (; i < tile; i++) {
+            const uint32_t c = __ldcg(rows + i * RADIX + d);
+            part[0] += (late[i >> 5] >> (i & 31)) & 1u ? 0u : c;
         }
-        excl += x & LB_COUNT;
-        if ((x >> 62) == 2) break;
+        excl = (uint64_t)part[0] + part[1] + part[2] + part[3];
+        for (int64_t w = 0; w * 32 < tile; w++) {
+            uint32_t bits = late[w];
+            while (bits) {  // counts that were not published in time: recount them
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int64_t j = w * 32 + b;
+                if (j < tile) excl += tile_digit_count(kin, n, j, shift, d);
+            }
+        }
+    } else {
+        const uint64_t tag = (uint64_t)pass << 58;
+        uint64_t* mine = look + tile * RADIX + d;
+        st_volatile_u64(mine, (tile == 0 ? LB_INC : LB_AGG) | tag | cnt);
+        // look back LB_WINDOW tiles at a time (independent loads), nearest first
+        bool found = false;
+        for (int64_t j0 = tile - 1; j0 >= 0 && !found; j0 -= LB_WINDOW) {
+            uint64_t win[LB_WINDOW];
+#pragma unroll
+            for (int q = 0; q < LB_WINDOW; q++) win[q] = j0 - q >= 0 ? ld_volatile_u64(look + (j0 - q) * RADIX + d) : 0ull;
+#pragma unroll
+            for (int q = 0; q < LB_WINDOW; q++) {
+                const int64_t j = j0 - q;
+                if (found || j < 0) break;
+                uint64_t x = win[q];
+                bool ok = (x >> 62) != 0 && ((x >> 58) & 15u) == (uint64_t)pass;
+                for (int spin = 0; !ok && spin < LB_SPIN; spin++) {
+                    x = ld_volatile_u64(look + j * RADIX + d);
+                    ok = (x >> 62) != 0 && ((x >> 58) & 15u) == (uint64_t)pass;
+                }
+                if (!ok) {  // not published in time: count it here
+                    excl += tile_digit_count(kin, n, j, shift, d);
+                    continue;
+                }
+                excl += x & LB_COUNT;
+                found = (x >> 62) == 2;
+            }
+        }
+        if (tile != 0) st_volatile_u64(mine, LB_INC | tag | (excl + cnt));
     }
-    if (tile != 0) st_volatile_u64(mine, LB_INC | tag | (excl + cnt));
     boff[d] = (uint64_t)gbase + excl;
     __syncthreads();
 #pragma unroll
@@ -370,9 +436,18 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const uint64_t* _
 // one look-back word per (tile, digit), reused by the passes (tagged)
 static size_t sort_counts_bytes() { return sizeof(uint32_t) * SORT_MAX_PASSES * RADIX + 256; }
 
+// For up to DIRECT_MAX_TILES tiles the 32-bit counts and ready flags serve;
+// beyond that the 64-bit look-back words.
+static size_t sort_lookback_bytes(int64_t tiles) {
+    tiles = std::max<int64_t>(tiles, 1);
+    if (tiles <= DIRECT_MAX_TILES)
+        return sizeof(uint32_t) * RADIX * (size_t)tiles + ((sizeof(uint32_t) * (size_t)tiles + 255) & ~(size_t)255);
+    return sizeof(uint64_t) * RADIX * (size_t)tiles;
+}
+
 size_t sort_temp_bytes(int64_t n) {
     const int64_t tiles = (n + SORT_TILE - 1) / SORT_TILE;
-    return sort_counts_bytes() + sizeof(uint64_t) * RADIX * (size_t)std::max<int64_t>(tiles, 1) + 256;
+    return sort_counts_bytes() + sort_lookback_bytes(tiles) + 256;
 }
 
 rt_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, uint32_t* vals_alt, int64_t n,
@@ -390,7 +465,10 @@ rt_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, u
     const int64_t tiles = (n + SORT_TILE - 1) / SORT_TILE;
     uint32_t* counts = (uint32_t*)temp;                                // [passes][256]
     uint32_t* tile_ctr = counts + SORT_MAX_PASSES * RADIX;              // [passes]
-    uint64_t* look = (uint64_t*)((char*)temp + sort_counts_bytes());  // [tiles][256]
+    char* lb = (char*)temp + sort_counts_bytes();
+    uint64_t* look = (uint64_t*)lb;                                     // [tiles][256], many tiles
+    uint32_t* ready = (uint32_t*)lb;                                    // [tiles], few tiles
+    uint32_t* rows = (uint32_t*)(lb + ((sizeof(uint32_t) * (size_t)tiles + 255) & ~(size_t)255));  // [tiles][256]
     RR_CUDA(cudaMemsetAsync(temp, 0, sort_temp_bytes(n), s));
     const int hist_grid = (int)std::min<int64_t>((n + SORT_THREADS - 1) / SORT_THREADS, 2 * (int64_t)device_sm_count());
     RR_LAUNCH(k_sort_hist, hist_grid, SORT_THREADS, 0, s, keys, n, begin_bit, passes, counts);
@@ -398,7 +476,7 @@ rt_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, u
     uint32_t *vi = vals, *vo = vals_alt;
     for (int p = 0; p < passes; p++) {
         RR_LAUNCH(k_sort_scatter, (unsigned)tiles, SORT_THREADS, 0, s, ki, vi, ko, vo, n, begin_bit + 8 * p, p,
-                  counts + p * RADIX, look, tile_ctr + p);
+                  counts + p * RADIX, look, rows, ready, tile_ctr + p, tiles);
         RR_CUDA(cudaGetLastError());
         std::swap(ki, ko);
         std::swap(vi, vo);

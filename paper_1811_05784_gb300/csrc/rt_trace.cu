@@ -130,8 +130,7 @@ __device__ __forceinline__ uint64_t record_key(uint64_t h, int32_t rcv, int32_t 
 // z_i = 1 - (2i+1)/N, rho = sqrt(1 - z^2), phi = 2 pi frac(i g), g = (3-sqrt5)/2.
 // Explicit _rn intrinsics keep every operation rounded as written.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float3 fibonacci_dir(int64_t i, int64_t N) {
-    const double g = __ddiv_rn(__dsub_rn(3.0, __dsqrt_rn(5.0)), 2.0);
+__device__ __forceinline__ float3 fibonacci_dir(int64_t i, int64_t N, double g) {
     double z = __dsub_rn(1.0, __ddiv_rn((double)(2 * i + 1), (double)N));
     double rho = __dsqrt_rn(__dsub_rn(1.0, __dmul_rn(z, z)));
     double f = __dmul_rn((double)i, g);
@@ -151,8 +150,7 @@ __device__ __forceinline__ float3 fibonacci_dir(int64_t i, int64_t N) {
 // keeps mu = z.  The direction is then turned from +z to w with the
 // orthonormal basis of Duff et al. 2017.  One rounded FP64 operation per step,
 // in the same order as the FP64 reference, so the float32 directions agree.
-__device__ __forceinline__ float3 directional_dir(int64_t i, int64_t N, const double* w, double a) {
-    const double g = __ddiv_rn(__dsub_rn(3.0, __dsqrt_rn(5.0)), 2.0);
+__device__ __forceinline__ float3 directional_dir(int64_t i, int64_t N, const double* w, double a, double g) {
     const double z = __dsub_rn(1.0, __ddiv_rn((double)(2 * i + 1), (double)N));
     double mu = z;
     if (a > 0.0) {
@@ -181,6 +179,11 @@ __device__ __forceinline__ float3 directional_dir(int64_t i, int64_t N, const do
     return make_float3(u[0], u[1], u[2]);
 }
 
+// g = (3 - sqrt 5) / 2 of the Fibonacci rule, formed once on the host: IEEE
+// square root, subtraction and division round the same way there as in the
+// FP64 steps of the device code, so the value is the same double.
+static const double GOLDEN_G = (3.0 - std::sqrt(5.0)) / 2.0;
+
 // Queue order of the primary rays: Fibonacci indices j, j+F, j+2F, ... (F a
 // Fibonacci number near sqrt(count)) lie along one spiral arm of the lattice,
 // so consecutive queue slots (one warp) get neighbouring directions.  The
@@ -200,7 +203,7 @@ __device__ __forceinline__ int64_t coherent_offset(int64_t r, int64_t count, int
 }
 
 __global__ void k_gen_rays(Queue q, const float* __restrict__ src, const double* __restrict__ srcdir,
-                           int64_t n_traced, int64_t per_src, int64_t ray_begin, int64_t N, int64_t F) {
+                           int64_t n_traced, int64_t per_src, int64_t ray_begin, int64_t N, int64_t F, double g) {
     int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_traced) return;
     int64_t s = r / per_src;
@@ -208,9 +211,9 @@ __global__ void k_gen_rays(Queue q, const float* __restrict__ src, const double*
     int64_t i = ray_begin + off;
     float3 u;
     if (srcdir && srcdir[4 * s + 3] >= 0.0)
-        u = directional_dir(i, N, srcdir + 4 * s, srcdir[4 * s + 3]);
+        u = directional_dir(i, N, srcdir + 4 * s, srcdir[4 * s + 3], g);
     else
-        u = fibonacci_dir(i, N);
+        u = fibonacci_dir(i, N, g);
     float e = (float)(1.0 / (double)N);
     q.o[r] = make_float4(src[3 * s], src[3 * s + 1], src[3 * s + 2], 0.f);
     q.d[r] = make_float4(u.x, u.y, u.z, 0.f);
@@ -671,11 +674,17 @@ __global__ void __launch_bounds__(BT) k_bounce(BounceArgs a) {
 // ---------------------------------------------------------------------------
 // image sources
 // ---------------------------------------------------------------------------
-__global__ void k_dedup_init(const uint64_t* __restrict__ rec_key, int64_t n, uint64_t* __restrict__ keys,
-                             uint32_t* __restrict__ vals) {
+// Sort keys of the records: the reflection order (capped at 31) in the top 5
+// bits above 59 bits of the record hash, so that the image sources come out
+// grouped by order and the lanes of a reconstruction warp mirror the source
+// about the same number of planes.  Equal keys of different beams (a 59-bit
+// collision) are caught by the exact sequence comparison of k_seg_flags.
+__global__ void k_dedup_init(const uint64_t* __restrict__ rec_key, const int32_t* __restrict__ rec_m, int64_t n,
+                             uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    keys[i] = rec_key[i];
+    const uint64_t m = (uint64_t)min(max(rec_m[i], 0), 31);
+    keys[i] = (m << 59) | (rec_key[i] >> 5);
     vals[i] = (uint32_t)i;
 }
 
@@ -739,7 +748,7 @@ struct ReconArgs {
     const int32_t* hist;
     const RoomDev* rooms;
     const int32_t* room_of_rcv;
-    const double* alpha64;   // [sum of n_mat][8]
+    const double* refl64;    // [sum of n_mat][8] 1 - alpha (FP64, formed on the host)
     const double* beta64;    // [8]
     const double* src64;     // [S][3]
     const double* rcv64;     // [R][3] by original receiver id
@@ -795,9 +804,9 @@ __global__ void k_reconstruct(ReconArgs a) {
             x -= 2.0 * dist * P[j].x;
             y -= 2.0 * dist * P[j].y;
             z -= 2.0 * dist * P[j].z;
-            const double* al = a.alpha64 + 8 * (rm.mat_base + mt[j]);
+            const double* rf = a.refl64 + 8 * (rm.mat_base + mt[j]);
 #pragma unroll
-            for (int f = 0; f < RT_N_BANDS; f++) prod[f] *= (1.0 - al[f]);
+            for (int f = 0; f < RT_N_BANDS; f++) prod[f] *= rf[f];
         }
     }
     const double* xm = a.rcv64 + 3 * rcv;
@@ -1071,7 +1080,7 @@ struct HostRoomTables {
     std::vector<int32_t> room_of_src, room_of_rcv, rcv_id, rcv_beg;
     std::vector<float4> rcv;
     std::vector<float> src;
-    std::vector<double> src64, rcv64, alpha64;
+    std::vector<double> src64, rcv64, refl64;
     std::vector<double> srcdir;  // [S][4] unit axis, pattern a; a < 0: omnidirectional
     bool directional = false;
     std::vector<float> refl;
@@ -1120,7 +1129,7 @@ static rt_status gather_rooms(const rt_room* rooms, int n_rooms, HostRoomTables&
                 return RT_ERR_INVALID_ARG;
             }
             h.refl.push_back(1.0f - al);
-            h.alpha64.push_back((double)al);
+            h.refl64.push_back(1.0 - (double)al);
         }
         for (int k = 0; k < rm.sources.n; k++) {
             const int g = src_base[r] + k;
@@ -1276,7 +1285,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     int32_t *d_room_of_src, *d_room_of_rcv, *d_rcv_id, *d_beg;
     float4* d_rcv;
     float *d_src, *d_refl;
-    double *d_alpha64, *d_beta64, *d_src64, *d_rcv64, *d_srcdir = nullptr;
+    double *d_refl64, *d_beta64, *d_src64, *d_rcv64, *d_srcdir = nullptr;
     {
         Packer pk;
         pk.add(h.rooms, &d_rooms);
@@ -1288,7 +1297,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
         pk.add(h.src, &d_src);
         if (h.directional) pk.add(h.srcdir, &d_srcdir);
         pk.add(h.refl, &d_refl);
-        pk.add(h.alpha64, &d_alpha64);
+        pk.add(h.refl64, &d_refl64);
         pk.add(h_beta64, &d_beta64);
         pk.add(h.src64, &d_src64);
         pk.add(h.rcv64, &d_rcv64);
@@ -1342,7 +1351,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     auto gen_rays = [&]() -> rt_status {
         RR_CUDA(cudaEventRecord(ev.e[0], s));
         RR_LAUNCH(k_gen_rays, grid_of(n_traced, 256), 256, 0, s, q[0], d_src, d_srcdir, n_traced, per_src,
-                  p->ray_begin, N, F);
+                  p->ray_begin, N, F, GOLDEN_G);
         RR_CUDA(cudaGetLastError());
         RR_CUDA(cudaEventRecord(ev.e[1], s));
         return RT_OK;
@@ -1529,7 +1538,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
         cv.add(&scan_tmp, scan_temp_bytes(nr));
         RR_TRY(cv.alloc(tmp));
         RR_CUDA(cudaMemsetAsync(d_coll, 0, sizeof(unsigned long long), s));
-        RR_LAUNCH(k_dedup_init, grid_of(nr, 256), 256, 0, s, rec_key, nr, keys, vals);
+        RR_LAUNCH(k_dedup_init, grid_of(nr, 256), 256, 0, s, rec_key, rec_m, nr, keys, vals);
         RR_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, nr, 0, 64, sort_tmp, s));
         RR_LAUNCH(k_seg_flags, grid_of(nr, 256), 256, 0, s, keys, vals, nr, rec_rcv, rec_ray, rec_m, hist, d_rooms,
                   d_room_of_rcv, n_traced, flags, d_coll);
@@ -1549,7 +1558,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
         ra.hist = hist;
         ra.rooms = d_rooms;
         ra.room_of_rcv = d_room_of_rcv;
-        ra.alpha64 = d_alpha64;
+        ra.refl64 = d_refl64;
         ra.beta64 = d_beta64;
         ra.src64 = d_src64;
         ra.rcv64 = d_rcv64;
