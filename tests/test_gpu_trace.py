@@ -181,6 +181,23 @@ def test_shoebox_trace_parity(n_rays):
     assert isrc.hash_collisions == 0
 
 
+def test_dedup_beyond_the_direct_prefix_path():
+    """More than 983,040 records (256 sort tiles): the dedup sort finds its
+    digit offsets by decoupled look-back; the grouping must still equal the
+    oracle's grouping of the same crossings."""
+    sc = scenes.shoebox(n_rays=400_000, n_bounces=30, radius=1.5)
+    tree, isrc = _trace(sc)
+    assert isrc.n_records > 983_040, isrc.n_records
+    ref = oracle.image_sources(sc, _gpu_as_oracle_trace(sc, isrc))
+    got = _gpu_is_table(sc, isrc)
+    assert len(got) == len(ref.n)
+    for k in range(len(ref.n)):
+        n, pos, dist, tim, en = got[(int(ref.rcv[k]), ref.seq[k])]
+        assert n == ref.n[k]
+        assert np.allclose(en, ref.E[k], rtol=1e-12, atol=0)
+    assert isrc.hash_collisions == 0
+
+
 def test_shoebox_image_sources_and_rir_parity():
     sc = scenes.shoebox()
     tree, isrc = _trace(sc)
