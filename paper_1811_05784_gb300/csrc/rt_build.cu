@@ -412,26 +412,32 @@ __device__ __forceinline__ void child_box(int32_t c, const float4* leaf_box, con
     }
 }
 
-// bottom-up refit: the second child to reach a node computes its box
+// bottom-up refit: the second child to reach a node computes its box.  The
+// thread carries the box of the subtree it comes from, so it loads only the
+// sibling's box, and it reads the node's children and parent before its
+// atomic so that those loads overlap the atomic's round trip.
 __global__ void k_refit(int64_t M, const int32_t* __restrict__ left, const int32_t* __restrict__ right,
                         const int32_t* __restrict__ parent_int, const int32_t* __restrict__ parent_leaf,
                         const float4* __restrict__ leaf_box, float4* node_box, unsigned int* flags) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
     int32_t p = parent_leaf[j];
+    int32_t from = ~(int32_t)j;  // child reference of the subtree this thread carries
+    float4 clo = leaf_box[2 * j], chi = leaf_box[2 * j + 1];
     for (int64_t step = 0; p >= 0 && step < M; step++) {
+        const int32_t l = left[p], r = right[p], pp = parent_int[p];
         __threadfence();
         unsigned int old = atomicAdd(&flags[p], 1u);
         if (old == 0) return;
         __threadfence();
-        float4 al, ah, bl, bh;
-        child_box(left[p], leaf_box, node_box, al, ah);
-        child_box(right[p], leaf_box, node_box, bl, bh);
-        float4 lo = make_float4(fminf(al.x, bl.x), fminf(al.y, bl.y), fminf(al.z, bl.z), 0.f);
-        float4 hi = make_float4(fmaxf(ah.x, bh.x), fmaxf(ah.y, bh.y), fmaxf(ah.z, bh.z), 0.f);
-        __stcg(node_box + 2 * (int64_t)p, lo);
-        __stcg(node_box + 2 * (int64_t)p + 1, hi);
-        p = parent_int[p];
+        float4 sl, sh;
+        child_box(l == from ? r : l, leaf_box, node_box, sl, sh);
+        clo = make_float4(fminf(clo.x, sl.x), fminf(clo.y, sl.y), fminf(clo.z, sl.z), 0.f);
+        chi = make_float4(fmaxf(chi.x, sh.x), fmaxf(chi.y, sh.y), fmaxf(chi.z, sh.z), 0.f);
+        __stcg(node_box + 2 * (int64_t)p, clo);
+        __stcg(node_box + 2 * (int64_t)p + 1, chi);
+        from = p;
+        p = pp;
     }
 }
 

@@ -231,8 +231,11 @@ rt_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint3
 // ---------------------------------------------------------------------------
 static constexpr int SORT_THREADS = 256;
 static constexpr int SORT_WARPS = SORT_THREADS / 32;
-static constexpr int SORT_ITEMS = 15;
-static constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;  // 3840 keys
+// keys per thread: 15 (3840-key tiles) for large sorts, 8 (2048-key tiles)
+// up to SORT_SMALL keys, where shorter per-tile chains pay more than fewer tiles
+static constexpr int SORT_ITEMS_LARGE = 15, SORT_ITEMS_SMALL = 8;
+static constexpr int64_t SORT_SMALL = 262144;
+static int64_t sort_tile(int64_t n) { return SORT_THREADS * (int64_t)(n <= SORT_SMALL ? SORT_ITEMS_SMALL : SORT_ITEMS_LARGE); }
 static constexpr int RADIX = 256;
 static constexpr int SORT_MAX_PASSES = 8;
 static constexpr uint64_t LB_AGG = 1ull << 62, LB_INC = 2ull << 62, LB_COUNT = (1ull << 58) - 1;
@@ -272,13 +275,15 @@ __device__ __forceinline__ void st_volatile_u64(uint64_t* p, uint64_t v) {
 }
 
 // digit d's count in tile j, recounted from the keys (the bounded wait's fallback)
-__device__ uint64_t tile_digit_count(const uint64_t* __restrict__ kin, int64_t n, int64_t j, int shift, uint32_t d) {
+__device__ uint64_t tile_digit_count(const uint64_t* __restrict__ kin, int64_t n, int64_t j, int64_t tile_keys,
+                                     int shift, uint32_t d) {
     uint64_t c = 0;
-    const int64_t lo = j * SORT_TILE, hi = lo + SORT_TILE < n ? lo + SORT_TILE : n;
+    const int64_t lo = j * tile_keys, hi = lo + tile_keys < n ? lo + tile_keys : n;
     for (int64_t i = lo; i < hi; i++) c += ((uint32_t)(kin[i] >> shift) & 0xFFu) == d;
     return c;
 }
 
+template <int SORT_ITEMS>
 __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const uint64_t* __restrict__ kin,
                                                                const uint32_t* __restrict__ vin,
                                                                uint64_t* __restrict__ kout,
@@ -310,6 +315,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const uint64_t* _
     uint32_t gbase = incl - gc;
     for (int w = 0; w < warp; w++) gbase += wsum[w];
     const int64_t tile = s_tile;
+    constexpr int64_t SORT_TILE = SORT_THREADS * SORT_ITEMS;
     const int64_t wbase = tile * SORT_TILE + (int64_t)warp * 32 * SORT_ITEMS;
     uint64_t k[SORT_ITEMS];
     uint32_t v[SORT_ITEMS], rank[SORT_ITEMS], dig[SORT_ITEMS];
@@ -384,7 +390,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const uint64_t* _
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
                 const int64_t j = w * 32 + b;
-                if (j < tile) excl += tile_digit_count(kin, n, j, shift, d);
+                if (j < tile) excl += tile_digit_count(kin, n, j, SORT_TILE, shift, d);
             }
         }
     } else {
@@ -408,7 +414,7 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_scatter(const uint64_t* _
                     ok = (x >> 62) != 0 && ((x >> 58) & 15u) == (uint64_t)pass;
                 }
                 if (!ok) {  // not published in time: count it here
-                    excl += tile_digit_count(kin, n, j, shift, d);
+                    excl += tile_digit_count(kin, n, j, SORT_TILE, shift, d);
                     continue;
                 }
                 excl += x & LB_COUNT;
@@ -446,7 +452,7 @@ static size_t sort_lookback_bytes(int64_t tiles) {
 }
 
 size_t sort_temp_bytes(int64_t n) {
-    const int64_t tiles = (n + SORT_TILE - 1) / SORT_TILE;
+    const int64_t tiles = (n + sort_tile(n) - 1) / sort_tile(n);
     return sort_counts_bytes() + sort_lookback_bytes(tiles) + 256;
 }
 
@@ -462,7 +468,7 @@ rt_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, u
         set_error("radix sort: bit range [%d, %d) not supported", begin_bit, end_bit);
         return RT_ERR_INVALID_ARG;
     }
-    const int64_t tiles = (n + SORT_TILE - 1) / SORT_TILE;
+    const int64_t tiles = (n + sort_tile(n) - 1) / sort_tile(n);
     uint32_t* counts = (uint32_t*)temp;                                // [passes][256]
     uint32_t* tile_ctr = counts + SORT_MAX_PASSES * RADIX;              // [passes]
     char* lb = (char*)temp + sort_counts_bytes();
@@ -475,8 +481,12 @@ rt_status radix_sort_pairs(uint64_t* keys, uint32_t* vals, uint64_t* keys_alt, u
     uint64_t *ki = keys, *ko = keys_alt;
     uint32_t *vi = vals, *vo = vals_alt;
     for (int p = 0; p < passes; p++) {
-        RR_LAUNCH(k_sort_scatter, (unsigned)tiles, SORT_THREADS, 0, s, ki, vi, ko, vo, n, begin_bit + 8 * p, p,
-                  counts + p * RADIX, look, rows, ready, tile_ctr + p, tiles);
+        if (n <= SORT_SMALL)
+            RR_LAUNCH(k_sort_scatter<SORT_ITEMS_SMALL>, (unsigned)tiles, SORT_THREADS, 0, s, ki, vi, ko, vo, n,
+                      begin_bit + 8 * p, p, counts + p * RADIX, look, rows, ready, tile_ctr + p, tiles);
+        else
+            RR_LAUNCH(k_sort_scatter<SORT_ITEMS_LARGE>, (unsigned)tiles, SORT_THREADS, 0, s, ki, vi, ko, vo, n,
+                      begin_bit + 8 * p, p, counts + p * RADIX, look, rows, ready, tile_ctr + p, tiles);
         RR_CUDA(cudaGetLastError());
         std::swap(ki, ko);
         std::swap(vi, vo);
