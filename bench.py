@@ -18,6 +18,8 @@ roofline   the bounce kernel's algorithmic L2-path bytes (112 B per 4-wide
            references; 48 B per triangle tested; counted by an instrumented
            pass) over its live duration, against the L2 read bandwidth
            measured in the same run; HBM fraction beside it.
+ms_step_spread  median, min and max of the timed steps (Python's garbage
+           collector is off during them).
 phases_ms  medians over the timed steps (CUDA events): tree build, ray
            generation, bounce loop, image sources (dedup + FP64
            reconstruction), the rest of rt_trace (uploads, queue set-up,
@@ -32,6 +34,7 @@ job (weak scaling, no collective on the data path).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -304,6 +307,10 @@ def run_native(args):
         launches0 = rt.rt_launch_count()
         ms, queries, ms_bounce = [], [], []
         phases = {k: [] for k in ("build", "rays", "bounces", "image_sources", "trace_other", "rir")}
+        # no Python garbage collection inside the timed steps: a collection
+        # pause stalls the host while the GPU waits for the next launch
+        gc.collect()
+        gc.disable()
         with ClockSampler(torch.cuda.current_device(), args.clock_log) as clk:
             for _ in range(args.steps):
                 flush.zero_()
@@ -324,6 +331,7 @@ def run_native(args):
                 phases["trace_other"].append(t_trace - isrc.ms_rays - isrc.ms_bounces - isrc.ms_image_sources)
                 phases["rir"].append(ev[1].elapsed_time(b))
         torch.cuda.synchronize()
+        gc.enable()
         launches = rt.rt_launch_count() - launches0
         if ws > 1:
             dist.barrier()
@@ -399,6 +407,7 @@ def run_native(args):
                      "ms_per_launch_set": bounce_s * 1e3,
                      "nodes_per_query": c[0] / n_q, "tris_per_query": c[1] / n_q},
         "phases_ms": {k: statistics.median(v) for k, v in phases.items()},
+        "ms_step_spread": {"median": statistics.median(ms), "min": min(ms), "max": max(ms)},
         "gpu_launches": int(launches),
         "clocks": clocks,
     }

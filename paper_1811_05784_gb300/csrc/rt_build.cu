@@ -4,7 +4,7 @@
 // mother box, split along the largest dimension at the median, recursively,
 // one element per leaf (Sec. 2.2).  On the GPU the tree is a linear BVH
 // (Karras 2012, "Maximizing parallelism in the construction of BVHs, octrees
-// and k-d trees"): 63-bit Morton codes of triangle centroids are sorted with
+// and k-d trees"): 48-bit Morton codes of triangle centroids are sorted with
 // the device radix sort, every internal node finds its key range and split
 // independently, boxes are refitted bottom-up with one atomic flag per node
 // (the second child to arrive computes the union and climbs on), and
@@ -189,7 +189,12 @@ __global__ void k_surf_check(const int32_t* __restrict__ surf, const int32_t* __
     if (sid >= 0 && sid < cap && mat[t] != mat_of_surf[sid]) atomicAdd(&meta->mixed_material, 1u);
 }
 
-// 63-bit Morton code of the float32 centroid within the centroid bounds
+// Morton code of the float32 centroid within the centroid bounds: 48 bits
+// (16 per axis, cells of 1/65536 of the bounds) sort in 6 radix passes instead
+// of the 8 of 63-bit codes; equal codes are ordered by index, as in Karras's
+// construction
+static constexpr int MORTON_BITS_PER_AXIS = 16;
+
 __global__ void k_morton(const float4* __restrict__ tv, int64_t M, const BuildMeta* meta,
                          uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -202,12 +207,12 @@ __global__ void k_morton(const float4* __restrict__ tv, int64_t M, const BuildMe
         float lo = ord2f(meta->cmin[k]), hi = ord2f(meta->cmax[k]);
         float ext = hi - lo;
         float x = ext > 0.f ? (cen[k] - lo) / ext : 0.f;
-        float s = x * 2097152.0f;  // 2^21
-        uint32_t v = s <= 0.f ? 0u : (s >= 2097151.0f ? 2097151u : (uint32_t)s);
+        float s = x * 65536.0f;  // 2^16 cells per axis
+        uint32_t v = s <= 0.f ? 0u : (s >= 65535.0f ? 65535u : (uint32_t)s);
         q[k] = v;
     }
     uint64_t code = 0;
-    for (int bit = 0; bit < 21; bit++) {
+    for (int bit = 0; bit < MORTON_BITS_PER_AXIS; bit++) {
         code |= (uint64_t)((q[0] >> bit) & 1u) << (3 * bit + 2);
         code |= (uint64_t)((q[1] >> bit) & 1u) << (3 * bit + 1);
         code |= (uint64_t)((q[2] >> bit) & 1u) << (3 * bit);
@@ -710,7 +715,7 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out, 
     if (!median) {
         RR_LAUNCH(k_morton, grid_of(M, 256), 256, 0, s, tv, M, meta, keys, vals);
         RR_CUDA(cudaGetLastError());
-        RR_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, M, 0, 64, sort_tmp, s));
+        RR_TRY(radix_sort_pairs(keys, vals, keys_alt, vals_alt, M, 0, 3 * MORTON_BITS_PER_AXIS, sort_tmp, s));
     } else {
         // identity order, then one segmented sort per level
         RR_LAUNCH(k_iota, grid_of(M, 256), 256, 0, s, M, vals);
