@@ -135,6 +135,17 @@ class ClockSampler:
             self.proc = None
         return self
 
+    def wait_first_sample(self, timeout=3.0):
+        """Block until nvidia-smi has written its first sample (its start-up
+        calls into the driver then happen before, not inside, a timed region)."""
+        t_end = time.time() + timeout
+        while self.proc is not None and time.time() < t_end:
+            self.f.flush()
+            if os.path.getsize(self.path) > 0:
+                return True
+            time.sleep(0.01)
+        return False
+
     def __exit__(self, *a):
         if self.proc is not None:
             self.proc.terminate()
@@ -293,12 +304,16 @@ def run_native(args):
         return tree, isrc, resp
 
     # warm-up; with the default the library's online autotuner tries its block
-    # sizes and tail thresholds on these calls and keeps the fastest
+    # sizes and tail thresholds on these calls and keeps the fastest.  The
+    # clock sampler starts here and runs through the timed steps.
+    clk = ClockSampler(torch.cuda.current_device(), args.clock_log)
+    clk.__enter__()
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 1)):
             _, isrc_w, _ = step(tail)
         torch.cuda.synchronize()
         chosen = {"block_size": isrc_w.block_size, "tail_rays": int(isrc_w.tail_rays)}
+        clk.wait_first_sample()
 
         # -- timed region (device-resident inputs) --------------------------
         if ws > 1:
@@ -311,26 +326,26 @@ def run_native(args):
         # pause stalls the host while the GPU waits for the next launch
         gc.collect()
         gc.disable()
-        with ClockSampler(torch.cuda.current_device(), args.clock_log) as clk:
-            for _ in range(args.steps):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-                a.record(stream)
-                tree, isrc, resp = step(tail, ev)
-                b.record(stream)
-                b.synchronize()
-                ms.append(a.elapsed_time(b))
-                queries.append(isrc.queries)
-                ms_bounce.append(isrc.ms_bounces)
-                t_trace = ev[0].elapsed_time(ev[1])
-                phases["build"].append(a.elapsed_time(ev[0]))
-                phases["rays"].append(isrc.ms_rays)
-                phases["bounces"].append(isrc.ms_bounces)
-                phases["image_sources"].append(isrc.ms_image_sources)
-                phases["trace_other"].append(t_trace - isrc.ms_rays - isrc.ms_bounces - isrc.ms_image_sources)
-                phases["rir"].append(ev[1].elapsed_time(b))
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            a.record(stream)
+            tree, isrc, resp = step(tail, ev)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            queries.append(isrc.queries)
+            ms_bounce.append(isrc.ms_bounces)
+            t_trace = ev[0].elapsed_time(ev[1])
+            phases["build"].append(a.elapsed_time(ev[0]))
+            phases["rays"].append(isrc.ms_rays)
+            phases["bounces"].append(isrc.ms_bounces)
+            phases["image_sources"].append(isrc.ms_image_sources)
+            phases["trace_other"].append(t_trace - isrc.ms_rays - isrc.ms_bounces - isrc.ms_image_sources)
+            phases["rir"].append(ev[1].elapsed_time(b))
         torch.cuda.synchronize()
+        clk.__exit__(None, None, None)
         gc.enable()
         launches = rt.rt_launch_count() - launches0
         if ws > 1:
@@ -387,6 +402,7 @@ def run_native(args):
         e2e_t, q_all, e2e_q_all = sum(e2e_ms) / 1e3, q_total, e2e_q
     value = q_all / t_max
     clocks = clk.summary()
+    clocks["window"] = "nvidia-smi every 200 ms from the first warm-up step to the last timed step"
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
