@@ -1,0 +1,46 @@
+"""Host-side helpers of bench.py (no GPU): the clock-log summary and the
+host description."""
+import importlib.util
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+class _Proc:  # stands in for the nvidia-smi process
+    pass
+
+
+def test_clock_summary_reads_samples_and_reasons(tmp_path):
+    b = _bench()
+    path = tmp_path / "clocks.csv"
+    path.write_text("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                    "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+                    "0, 2055, 2070, 1200.5, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                    "garbled line\n")
+    c = b.ClockSampler(0, str(path))
+    c.proc = _Proc()
+    s = c.summary()
+    assert s["sm_mhz"] == 2055.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_summary_without_samples(tmp_path):
+    b = _bench()
+    c = b.ClockSampler(0, str(tmp_path / "none.csv"))
+    assert c.summary()["reasons"] == ["nvidia-smi unavailable"]
+    c.proc = _Proc()
+    (tmp_path / "none.csv").write_text("")
+    assert c.summary()["reasons"] == ["no samples"]
+
+
+def test_host_cpu_names_the_architecture():
+    b = _bench()
+    import platform
+    assert b.host_cpu().startswith(platform.machine())
