@@ -722,11 +722,18 @@ __global__ void k_seg_flags(const uint64_t* __restrict__ keys, const uint32_t* _
 
 // lowest ray index of every beam (atomicMin over the beam's records); the
 // exclusive scan of the head flags gives a record's beam as segid + flag - 1
+// lowest ray of each segment; the records of a segment are adjacent, so the
+// lanes of a warp that share one reduce first and send one atomic
 __global__ void k_seg_min(const uint32_t* __restrict__ vals, const uint32_t* __restrict__ flags,
                           const uint32_t* __restrict__ segid, int64_t n, const int32_t* __restrict__ rec_ray,
                           int32_t* __restrict__ rep) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n) atomicMin(rep + (segid[j] + flags[j] - 1u), rec_ray[vals[j]]);
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const uint32_t seg = j < n ? segid[j] + flags[j] - 1u : 0xFFFFFFFFu;
+    const int32_t ray = j < n ? rec_ray[vals[j]] : INT_MAX;
+    const unsigned int peers = __match_any_sync(0xffffffffu, seg);
+    const int32_t lo = __reduce_min_sync(peers, ray);
+    if (j < n && (peers & ((1u << lane) - 1u)) == 0) atomicMin(rep + seg, lo);
 }
 
 __global__ void k_seg_heads(const uint32_t* __restrict__ flags, const uint32_t* __restrict__ segid, int64_t n,
