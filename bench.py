@@ -137,7 +137,8 @@ class ClockSampler:
 
     def wait_first_sample(self, timeout=3.0):
         """Block until nvidia-smi has written its first sample (its start-up
-        calls into the driver then happen before, not inside, a timed region)."""
+        calls into the NVIDIA driver then happen before, not inside, a timed
+        region)."""
         t_end = time.time() + timeout
         while self.proc is not None and time.time() < t_end:
             self.f.flush()
