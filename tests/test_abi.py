@@ -51,3 +51,40 @@ def test_oracle_and_cuda_path_share_no_code():
             txt = open(os.path.join(ROOT, "oracle", f)).read()
             assert not re.search(r"^\s*(import|from)\s+paper_1811_05784_gb300", txt, re.M), f
             assert not re.search(r"#include.*roomrays", txt), f
+
+
+STRUCTS = ("rt_mesh", "rt_sources", "rt_receivers", "rt_trace_params", "rt_room", "rt_is_view",
+           "rt_response_view")
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors have the C compiler's size and field offsets for
+    every public struct of roomrays.h (a field added on one side only would
+    shift every later field)."""
+    import shutil
+    import subprocess
+    from paper_1811_05784_gb300 import rt
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "roomrays.h"', "int main(void) {"]
+    for name in STRUCTS:
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in getattr(rt, name)._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for line in out:
+        if not line.strip():
+            continue
+        name, field, value = line.split()
+        cls = getattr(rt, name)
+        want = ctypes.sizeof(cls) if field == "size" else getattr(cls, field).offset
+        assert int(value) == want, (name, field, int(value), want)
+        seen += 1
+    assert seen == sum(1 + len(getattr(rt, n)._fields_) for n in STRUCTS)
