@@ -311,8 +311,8 @@ def run_native(args):
     clk.__enter__()
     with torch.cuda.stream(stream):
         # the autotuner tries one configuration per call until it has timed
-        # them all (7); finish that before the W warm-up steps, so that the
-        # timed steps run the chosen configuration whatever W is
+        # each of its 7 twice; finish that before the W warm-up steps, so that
+        # the timed steps run the chosen configuration whatever W is
         if tail == rt.RT_TAIL_AUTOTUNE:
             prev = None
             for _ in range(20):

@@ -114,9 +114,10 @@ typedef struct {
     int32_t tail_rays;     /* once a bounce starts with at most this many live rays, one
                               launch finishes all their remaining bounces (0 = the number
                               of resident threads, -1 = never: one launch per bounce,
-                              RT_TAIL_AUTOTUNE = the library times its candidate block
-                              sizes and thresholds on the first calls of each workload
-                              class and keeps the fastest; results do not depend on it) */
+                              RT_TAIL_AUTOTUNE = the library times each of its candidate
+                              block sizes and thresholds twice on the first calls of each
+                              workload class and keeps the fastest; results do not depend
+                              on it) */
     void* stream;          /* cudaStream_t */
     /* optional device outputs for parity checks (NULL = off) */
     float* debug_t;        /* [n_bounces][n_traced] hit distance, +inf on escape */

@@ -850,7 +850,8 @@ static rt_status alloc_queue(Arena& ar, Queue& q, int64_t n) {
 // A configuration is a block size and a tail threshold (never / resident
 // threads / every ray).  Every configuration gives identical results per ray,
 // so the autotuner times the real calls: the first calls of a workload class
-// each run the next candidate, and once all have run the fastest is kept
+// each run the next candidate, every candidate twice (the faster time counts,
+// which keeps one noisy call from deciding), and then the fastest is kept
 // (optionally persisted in the file named by RT_AUTOTUNE_CACHE).
 struct Config {
     int block;
@@ -858,6 +859,7 @@ struct Config {
 };
 static const Config CANDIDATES[] = {{128, 2}, {128, 1}, {64, 2}, {256, 2}, {128, 0}, {64, 1}, {256, 1}};
 static constexpr int N_CANDIDATES = sizeof(CANDIDATES) / sizeof(CANDIDATES[0]);
+static constexpr int TUNE_ROUNDS = 2;
 
 struct TuneState {
     float ms[N_CANDIDATES];
@@ -880,7 +882,7 @@ static void tune_load_locked() {
     while (fscanf(f, "%255s %d", key, &best) == 2) {
         if (best >= 0 && best < N_CANDIDATES) {
             TuneState t;
-            t.next = N_CANDIDATES;
+            t.next = TUNE_ROUNDS * N_CANDIDATES;
             t.best = best;
             for (float& x : t.ms) x = 0.f;
             g_tune[key] = t;
@@ -917,16 +919,16 @@ static int tune_pick(const std::string& key) {
     tune_load_locked();
     TuneState& t = g_tune[key];
     if (t.best >= 0) return t.best;
-    return t.next < N_CANDIDATES ? t.next : 0;
+    return t.next < TUNE_ROUNDS * N_CANDIDATES ? t.next % N_CANDIDATES : 0;
 }
 
 static void tune_report(const std::string& key, int cand, float ms) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     TuneState& t = g_tune[key];
-    if (t.best >= 0 || cand != t.next) return;
-    t.ms[cand] = ms;
+    if (t.best >= 0 || cand != t.next % N_CANDIDATES) return;
+    t.ms[cand] = t.next < N_CANDIDATES ? ms : std::min(t.ms[cand], ms);
     t.next++;
-    if (t.next == N_CANDIDATES) {
+    if (t.next == TUNE_ROUNDS * N_CANDIDATES) {
         int b = 0;
         for (int k = 1; k < N_CANDIDATES; k++)
             if (t.ms[k] < t.ms[b]) b = k;
