@@ -1,5 +1,5 @@
-"""Host-side helpers of bench.py (no GPU): the clock-log summary and the
-host description."""
+"""Host-side helpers (no GPU): bench.py's clock-log summary and host
+description, and the binding's marshalling of source tables."""
 import importlib.util
 import os
 
@@ -44,3 +44,19 @@ def test_host_cpu_names_the_architecture():
     b = _bench()
     import platform
     assert b.host_cpu().startswith(platform.machine())
+
+
+def test_directional_source_arguments_are_checked_before_any_call():
+    """The binding's source tables: one axis and one pattern per source,
+    omnidirectional when no axis is given (no GPU needed)."""
+    import numpy as np
+    import pytest
+    from paper_1811_05784_gb300 import rt
+    S, keep = rt._sources(np.zeros((2, 3)))
+    assert S.n == 2 and not S.axis and not S.pattern
+    S, keep = rt._sources(np.zeros((2, 3)), [[0, 0, 1], [1, 0, 0]], [0.5, 0.0])
+    assert S.n == 2 and S.axis and S.pattern and len(keep) == 3
+    S, keep = rt._sources(np.zeros((1, 3)), [[0, 0, 1]])          # pattern defaults to 0
+    assert np.asarray(keep[2]).tolist() == [0.0]
+    with pytest.raises(ValueError):
+        rt._sources(np.zeros((2, 3)), [[0, 0, 1]], [0.1])
