@@ -369,3 +369,28 @@ def test_directional_source_sampling():
         perp = d - np.outer(mu, w)
         assert np.linalg.norm(perp.mean(0)) < 2e-3
     assert abs((oracle.source_directions(N, (1, 0, 0), 0.5) @ np.array([1, 0, 0]) > 0).mean() - 0.75) < 2e-3
+
+
+@pytest.mark.parametrize("a", [0.0, 0.25, 0.5])
+def test_directional_direct_sound_counts(a):
+    """Direct sound of a directional source (Sec. 1.2 footnote) through the
+    whole oracle trace: the rays of a source pointing along +x that cross a
+    sphere of radius r at distance d in front of / behind it number N times
+    the cap integral of the density (1 - a + a mu) / (2 (1 - a)) over
+    mu >= c, resp. mu <= -c, c = sqrt(1 - r^2 / d^2).  The warped lattice is
+    stratified in mu about the axis, so the counts hold to a ray or two."""
+    import copy
+    N, d, r = 200_000, 3.0, 0.5
+    sc = copy.copy(scenes.shoebox(L=(40.0, 40.0, 40.0), source=(20.0, 20.0, 20.0), alpha=1.0,
+                                  n_rays=N, n_bounces=1))
+    sc.rcv_center = np.array([[20.0 + d, 20.0, 20.0], [20.0 - d, 20.0, 20.0]])
+    sc.rcv_radius = np.array([r, r])
+    sc.rcv_source = np.array([0, 0], np.int32)
+    sc = scenes.directional(sc, [1.0, 0.0, 0.0], a)
+    tr = oracle.trace(oracle.OracleScene(sc, tree=False))
+    direct = tr.rec_m == 0
+    c = math.sqrt(1.0 - (r / d) ** 2)
+    for k, side in ((0, 1.0), (1, -1.0)):
+        n = int(np.sum(direct & (tr.rec_rcv == k)))
+        want = N * ((1 - a) * (1 - c) + side * 0.5 * a * (1 - c * c)) / (2 * (1 - a))
+        assert abs(n - want) <= 2 + 1e-3 * want, (k, n, want)
