@@ -214,20 +214,25 @@ rt_status exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint3
 // ---------------------------------------------------------------------------
 // stable LSD radix sort, 8-bit digits, one scatter launch per pass
 //   * one launch counts the digits of every pass at once (global histograms);
-//   * per pass, blocks take tile indices in launch order from an atomic
-//     counter, publish their tile's digit counts, and find each digit's
-//     offset by decoupled look-back (Merrill & Garland 2016; the single-pass
-//     radix sort of Adinets & Merrill 2022): walk back over the earlier tiles
-//     adding their published counts until one that already published its
-//     inclusive prefix.  Keys are ranked inside the tile with
-//     __match_any_sync per warp, keeping the input order among equal digits,
-//     so every pass is stable.
+//   * per pass, one scatter launch: blocks take tile indices in launch order
+//     from an atomic counter and publish their tile's digit counts.  Each
+//     digit's offset is the sum of the earlier tiles' counts:
+//       - up to DIRECT_MAX_TILES tiles, every tile also sets a ready flag; a
+//         block waits for the earlier tiles' flags (one per thread) and sums
+//         their counts with independent loads;
+//       - beyond, by decoupled look-back (Merrill & Garland 2016; the
+//         single-pass radix sort of Adinets & Merrill 2022): walk back over
+//         the earlier tiles adding their counts until one that already
+//         published its inclusive prefix.
+//     Keys are ranked inside the tile with __match_any_sync per warp,
+//     keeping the input order among equal digits, so every pass is stable.
 // A tile index goes only to a block that is running, and every block
 // publishes its counts before it waits, so each wait ends; the wait is
 // bounded all the same: past the limit the block counts that tile's digit
 // itself from the keys, which gives the same number.
 // Look-back words (64-bit): bits 63-62 state (1 counts of the tile, 2
-// inclusive prefix), bits 61-58 the pass, bits 57-0 the count.
+// inclusive prefix), bits 61-58 the pass, bits 57-0 the count.  Ready flags
+// hold the pass + 1, so a flag left by the previous pass is not taken.
 // ---------------------------------------------------------------------------
 static constexpr int SORT_THREADS = 256;
 static constexpr int SORT_WARPS = SORT_THREADS / 32;
