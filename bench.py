@@ -25,7 +25,8 @@ phases_ms  medians over the timed steps (CUDA events): tree build, ray
            reconstruction), the rest of rt_trace (uploads, queue set-up,
            result sizes), RIR binning.
 cpu_baseline  the FP64 oracle (oracle/, C + numpy) on a bounded sample of the
-           same workload on this host's cores.
+           same workload on this host's cores; beside it the oracle's trace
+           on one thread and the paper's single-core rate (Table 2).
 
 --impl reference runs that oracle as the reference arm.
 Under torchrun each rank traces its own ray shard of a world_size x 1M-ray
@@ -196,6 +197,19 @@ def oracle_sample(sc, n_rays, seed=0):
     oracle.rir(isrc, len(sc.rcv_center), sc.fs, DURATION)
     dt = time.perf_counter() - t0
     return tr.queries, dt, oracle.default_threads()
+
+
+def oracle_single_thread(sc, n_rays, seed=1):
+    """The oracle's trace alone (tree built beforehand) on one host thread,
+    for a seeded subset of the workload's rays: queries per second."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    osc = oracle.OracleScene(sc, tree=True)
+    ids = np.sort(rng.choice(sc.n_rays, min(n_rays, sc.n_rays), replace=False))
+    t0 = time.perf_counter()
+    tr = oracle.trace(osc, ray_ids=ids, threads=1)
+    dt = time.perf_counter() - t0
+    return {"value": tr.queries / dt, "unit": UNIT, "sample": f"{len(ids):,} seeded rays, trace only, 1 thread"}
 
 
 def run_reference(args):
@@ -442,6 +456,10 @@ def run_native(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         q, dt, threads = oracle_sample(sc, args.cpu_sample_rays)
         result["cpu_baseline"] = {"value": q / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                  "single_thread": oracle_single_thread(sc, 20_000),
+                                  "paper_single_core": {"value": 2 ** 20 / 13.78, "unit": UNIT,
+                                                        "source": "Table 2: 2^20 rays and faces, one "
+                                                                  "iteration with the tree in 13.78 s"},
                                   "sample": f"{args.cpu_sample_rays:,} seeded rays of the workload "
                                             f"(oracle median-split tree, image sources, RIR): {q:,} queries",
                                   "cpu": host_cpu()}
