@@ -26,3 +26,18 @@ def test_batched_rooms_workload():
     again = scenes.batched_rooms(n_rooms=3)
     for a, b in zip(again, rooms[:3]):
         assert np.array_equal(a.vertices, b.vertices) and np.array_equal(a.sources, b.sources)
+
+
+def test_directional_copy_normalises_and_broadcasts():
+    """scenes.directional: one axis for all sources or one per source, unit
+    length, one pattern per source; the scene it copies is left as it was."""
+    import numpy as np
+    import scenes
+    sc = scenes.shoebox(n_rays=100, n_bounces=2)
+    d = scenes.directional(sc, [0.0, 3.0, 4.0], 0.25)
+    assert sc.src_axis is None and sc.src_pattern is None
+    assert d.src_axis.shape == (len(sc.sources), 3) and d.src_pattern.shape == (len(sc.sources),)
+    assert np.allclose(d.src_axis[0], [0.0, 0.6, 0.8], atol=0, rtol=1e-15)
+    assert abs(np.sum(d.src_axis[0] ** 2) - 1.0) < 1e-15
+    assert np.all(d.src_pattern == 0.25)
+    assert d.tris is sc.tris and d.vertices is sc.vertices
