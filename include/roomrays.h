@@ -82,8 +82,9 @@ typedef struct {
  * directions have density (1 - a + a cos theta) / (4 pi (1 - a)) about its
  * unit axis, a = pattern[k] in [0, 1/2] (NULL: 0) -- the uniform rule's z
  * mapped through the inverse cumulative of that density and turned to the
- * axis (roomrays reference: the FP64 steps in rt_trace.cu's directional_dir).
- * Axes must be unit vectors within 1e-9 (RT_ERR_INVALID_ARG otherwise). */
+ * axis; the exact FP64 steps are those of directional_dir in csrc/rt_trace.cu.
+ * Axes must be unit vectors within 1e-9 and patterns lie in [0, 1/2]
+ * (RT_ERR_INVALID_ARG otherwise).  The arrays are read during the call. */
 typedef struct {
     const double* pos;           /* [n][3] */
     int32_t n;
