@@ -28,7 +28,7 @@ cpu_baseline  the FP64 oracle (oracle/, C + numpy) on a bounded sample of the
            same workload on this host's cores; beside it the oracle's trace
            on one thread and the paper's single-core rate (Table 2).
 
---impl reference runs that oracle as the reference arm (see DESIGN.md).
+--impl reference runs that oracle as the reference arm.
 Under torchrun each rank traces its own ray shard of a world_size x 1M-ray
 job (weak scaling, no collective on the data path).
 """

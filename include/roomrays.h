@@ -255,7 +255,13 @@ void rt_response_free(rt_response* rir);
  * Its sort scratch is one static device array of RT_RIR_STATIC_SCRATCH_BYTES
  * that every GPU loading the library holds until exit; all calls share it,
  * so calls whose GPU work overlaps race (serialise them).  The first call on
- * a device looks up the array's address; make it before any stream capture.
+ * a device looks up the array's address, which loads the library's device
+ * code on that device if nothing has loaded it yet: that first call may make
+ * the driver allocate and may block, so a real-time caller makes one warm-up
+ * call (any n, e.g. 0) before its deadline loop and before any stream
+ * capture.  The address is kept for the life of the process: after
+ * cudaDeviceReset (or a release of the device's primary context) later calls
+ * are invalid.
  * Errors: RT_ERR_INVALID_ARG (n > RT_RIR_STATIC_MAX_SOURCES, bad sizes or
  * null arrays), RT_ERR_CUDA. */
 #define RT_RIR_STATIC_MAX_SOURCES 524288

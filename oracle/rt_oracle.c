@@ -22,7 +22,7 @@
  *   - binary tree: mother box, split along the largest dimension at
  *     the median until one element per leaf                          Sec. 2.2
  *
- * Readings where the paper is silent (all also listed in the design doc):
+ * Readings where the paper is silent:
  *   - Fibonacci rule: z_i = 1-(2i+1)/N, rho = sqrt(1-z^2),
  *     phi_i = 2 pi frac(i g), g = (3 - sqrt 5)/2; each direction
  *     component is rounded to float32 and promoted back.

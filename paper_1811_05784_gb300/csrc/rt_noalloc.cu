@@ -19,8 +19,15 @@
 //   - nothing in it needs to start at zero: every launch writes what it
 //     later reads;
 //   - the first call on a device looks up the array's device address
-//     (cudaGetSymbolAddress) once for that device; make that first call
-//     before capturing the stream into a CUDA graph.
+//     (cudaGetSymbolAddress) once for that device.  With lazy module loading
+//     (the default) that lookup is what loads this library's device code on
+//     the device, so the first call may make the driver allocate and may
+//     block: real-time callers make one warm-up call (n = 0 is enough)
+//     before their deadline loop, and before capturing the stream into a
+//     CUDA graph;
+//   - the address is cached for the life of the process; cudaDeviceReset
+//     (or a release of the primary context) unloads the module, after which
+//     the cached address is stale and later calls are invalid.
 #include "rt_internal.cuh"
 
 #include <mutex>

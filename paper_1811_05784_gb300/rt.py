@@ -538,13 +538,23 @@ RT_RIR_STATIC_MAX_SOURCES = 524288
 
 def rt_rir_static(image_sources: ImageSources, fs, duration, out=None, stream=None):
     """Histograms of image sources without any device allocation inside the
-    library (static scratch; see roomrays.h).  `out` is a CUDA float32 tensor
-    [n_rcv, 8, ceil(duration * fs)], allocated here by torch if not given."""
-    import torch
+    library (static scratch; see roomrays.h).  `out` is a contiguous CUDA
+    float32 tensor [n_rcv, 8, ceil(duration * fs)] that the call zero-fills
+    and sums into; if not given, torch allocates it here (outside the
+    library).  A wrong `out` raises ValueError before anything is launched."""
     n_bins = int(np.ceil(duration * fs))
     n_rcv = max(image_sources_n_rcv(image_sources), 1)
+    if n_bins < 1:
+        raise ValueError("rt_rir_static: duration * fs must give at least one bin")
+    shape = (n_rcv, N_BANDS, n_bins)
     if out is None:
-        out = torch.empty((n_rcv, N_BANDS, n_bins), dtype=torch.float32, device="cuda")
+        import torch
+        out = torch.empty(shape, dtype=torch.float32, device="cuda")
+    elif not (_is_cuda_tensor(out) and str(out.dtype) == "torch.float32" and out.is_contiguous()
+              and tuple(out.shape) == shape):
+        raise ValueError(f"rt_rir_static: out must be a contiguous CUDA float32 tensor of shape {shape}, got "
+                         f"{tuple(getattr(out, 'shape', ()))} {getattr(out, 'dtype', type(out))} on "
+                         f"{getattr(out, 'device', 'host')}")
     v = image_sources.view
     _check(lib().rt_rir_static(P(v.time), P(v.rcv), P(v.energy), int(v.n), int(n_rcv), float(fs), int(n_bins),
                                P(out.data_ptr()), _stream_ptr(stream)))

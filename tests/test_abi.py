@@ -88,3 +88,26 @@ def test_binding_structs_match_the_header(tmp_path):
         assert int(value) == want, (name, field, int(value), want)
         seen += 1
     assert seen == sum(1 + len(getattr(rt, n)._fields_) for n in STRUCTS)
+
+
+def test_static_histogram_binding_rejects_a_wrong_output_before_any_call():
+    """rt.rt_rir_static checks a caller-supplied output (device, dtype,
+    contiguity, shape) before it reaches the library: a wrong buffer would
+    otherwise be written past its end on the device."""
+    import numpy as np
+    from paper_1811_05784_gb300 import rt
+
+    class _Fake:          # only n_rcv is read before the output check
+        n_rcv = 2
+
+        @property
+        def view(self):
+            raise AssertionError("the library was reached")
+
+    for bad in (np.zeros((2, 8, 100), np.float32), [[0.0]], np.zeros(3)):
+        with pytest.raises(ValueError):
+            rt.rt_rir_static(_Fake(), 100.0, 1.0, out=bad)
+    torch = pytest.importorskip("torch")
+    for bad in (torch.zeros((2, 8, 100)), torch.zeros((2, 8, 99)), torch.zeros((2, 8, 100), dtype=torch.float64)):
+        with pytest.raises(ValueError):
+            rt.rt_rir_static(_Fake(), 100.0, 1.0, out=bad)

@@ -40,22 +40,70 @@ def _case(sc, duration):
     return isrc, ref
 
 
+def _expected_launches(n, n_rcv, n_bins):
+    """Kernels of one rt_rir_static call: bin keys, the radix sort's digit
+    count and one scatter per 8 key bits, the FP64 bin sums."""
+    if n == 0:
+        return 0
+    bits = max(int(n_rcv * n_bins).bit_length(), 1)
+    return 3 + (bits + 7) // 8 if n > 1 else 2
+
+
 def test_static_histograms_match_rt_rir_on_two_calls():
     cases = [(scenes.theatre(n_rays=200_000), 1.0), (scenes.shoebox(n_rays=50_000, n_bounces=40), 0.5)]
-    # while these calls run, any allocation through the library's allocator fails
     prepared = [(sc, dur) + _case(sc, dur) for sc, dur in cases]
+    outs = []
+    for sc, dur, isrc, ref in prepared:
+        n_rcv = len(sc.rcv_center)
+        n_bins = int(math.ceil(dur * sc.fs))
+        outs.append(torch.full((n_rcv, 8, n_bins), float("nan"), dtype=torch.float32, device="cuda"))
+    # the first call on the device looks up the static array (and may load
+    # the library's device code): done here, before the checked calls
+    assert _static(prepared[1][2], 1, prepared[1][0].fs, 8, outs[1][:, :, :8].contiguous()) == rt.RT_OK
+    torch.cuda.synchronize()
+    # while the checked calls run, any allocation through the library's
+    # allocator fails, device free memory must not drop, and the library
+    # launches exactly the kernels of the binning step
     rt.rt_set_allocator(lambda nbytes, stream, ctx: None, lambda p, s, c: None)
     try:
-        for sc, dur, isrc, ref in prepared:
-            n_rcv = len(sc.rcv_center)
-            n_bins = int(math.ceil(dur * sc.fs))
-            out = torch.full((n_rcv, 8, n_bins), float("nan"), dtype=torch.float32, device="cuda")
-            assert _static(isrc, n_rcv, sc.fs, n_bins, out) == rt.RT_OK, rt.rt_last_error()
-            assert isrc.n > 0 and torch.isfinite(out).all()
-            err = float(torch.linalg.norm((out - ref).double()) / torch.linalg.norm(ref.double()))
-            assert err < TOL_RIR, err
+        for rnd in range(2):
+            launches0 = rt.rt_launch_count()
+            want = 0
+            for (sc, dur, isrc, ref), out in zip(prepared, outs):
+                n_rcv = len(sc.rcv_center)
+                n_bins = int(math.ceil(dur * sc.fs))
+                out.fill_(float("nan"))
+                torch.cuda.synchronize()
+                free0 = torch.cuda.mem_get_info()[0]
+                assert _static(isrc, n_rcv, sc.fs, n_bins, out) == rt.RT_OK, rt.rt_last_error()
+                assert torch.cuda.mem_get_info()[0] >= free0, "device free memory dropped during the call"
+                want += _expected_launches(isrc.n, n_rcv, n_bins)
+                assert isrc.n > 0 and torch.isfinite(out).all()
+                err = float(torch.linalg.norm((out - ref).double()) / torch.linalg.norm(ref.double()))
+                assert err < TOL_RIR, (rnd, err)
+            assert rt.rt_launch_count() - launches0 == want
     finally:
         rt.rt_set_allocator(None, None)
+
+
+def test_static_histograms_through_the_binding():
+    """rt.rt_rir_static with and without a caller-supplied output, and a
+    wrong output rejected before any launch."""
+    sc = scenes.shoebox(n_rays=20_000, n_bounces=30)
+    isrc, ref = _case(sc, 0.5)
+    a = rt.rt_rir_static(isrc, sc.fs, 0.5)
+    out = torch.empty_like(ref)
+    b = rt.rt_rir_static(isrc, sc.fs, 0.5, out=out)
+    assert b is out
+    for h in (a, b):
+        err = float(torch.linalg.norm((h - ref).double()) / torch.linalg.norm(ref.double()))
+        assert err < TOL_RIR, err
+    launches0 = rt.rt_launch_count()
+    for bad in (torch.empty_like(ref)[:, :, :-1], torch.empty_like(ref, dtype=torch.float64), ref.cpu(),
+                torch.empty((ref.shape[2], 8, 1), device="cuda").transpose(0, 2)):
+        with pytest.raises(ValueError):
+            rt.rt_rir_static(isrc, sc.fs, 0.5, out=bad)
+    assert rt.rt_launch_count() == launches0
 
 
 def test_static_histograms_reject_sizes_beyond_the_limit():
