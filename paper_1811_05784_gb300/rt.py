@@ -503,11 +503,11 @@ class Workspace:
 
 def rt_trace_batch(rooms, n_rays, n_bounces, ray_begin=0, ray_count=0, max_distance=0.0, air_beta=None, c=343.2,
                    block_size=0, max_node_visits=0, tail_rays=0, stream=None, workspace=None,
-                   replay=None) -> ImageSources:
+                   replay=None, debug_t=None, debug_state=None, debug_cost=None) -> ImageSources:
     """Trace many rooms in one persistent launch.  `rooms` is a list of dicts
     with keys tree, sources, rcv_center, rcv_radius, rcv_source,
     band_absorption (and optionally src_axis, src_pattern).  Receivers are
-    numbered room after room.  replay: see rt_trace."""
+    numbered room after room.  replay and the debug outputs: see rt_trace."""
     keep, arr = [], (rt_room * len(rooms))()
     n_rcv = 0
     for k, r in enumerate(rooms):
@@ -525,7 +525,10 @@ def rt_trace_batch(rooms, n_rays, n_bounces, ray_begin=0, ray_count=0, max_dista
         be, pbe = None, None
     prm = rt_trace_params(int(n_rays), int(ray_begin), int(ray_count), int(n_bounces), float(max_distance), pbe,
                           float(c), int(block_size), int(max_node_visits), int(tail_rays), _stream_ptr(stream),
-                          None, None, None, workspace._h if workspace is not None else None, _replay_ptr(replay))
+                          P(debug_t.data_ptr()) if debug_t is not None else None,
+                          P(debug_state.data_ptr()) if debug_state is not None else None,
+                          P(debug_cost.data_ptr()) if debug_cost is not None else None,
+                          workspace._h if workspace is not None else None, _replay_ptr(replay))
     out = P()
     _check(lib().rt_trace_batch(arr, len(rooms), C.byref(prm), C.byref(out)))
     res = ImageSources(out)

@@ -111,21 +111,37 @@ def _check_lockstep(sc, osc, ds, dt, hist, pick=None):
     return bq, amb
 
 
-def _check_free_running(sc, hist, ids, tr):
+def _check_free_running(sc, hist, ids, tr, isrc=None):
     """Free-running float32 vs FP64 trajectories: the reflection sequences
     (surface ids) agree up to each ray's first ambiguous bounce.  Triangle
     ids inside one surface may differ once the trajectories have drifted by
-    more than the near-edge band; those are counted, not failed."""
+    more than the near-edge band; those are counted, not failed.  With the
+    GPU result `isrc`, the rays whose whole triangle sequence equals the
+    oracle's (no ambiguity) must also carry the oracle's band energies
+    (1e-4) and path lengths (1e-5)."""
     surf = np.append(sc.surface_id, -1)            # index -1 -> -1
     agree = tri_diff = 0
+    same = np.zeros(len(ids), bool)
     for k, q in enumerate(ids):
         upto = tr.first_amb[k]
         g, o = hist[:upto, q], tr.hist[k, :upto]
         assert np.array_equal(surf[g], surf[o]), (q, g, o)
         tri_diff += int((g != o).any())
         agree += upto
+        same[k] = upto == tr.B and np.array_equal(hist[:, q], tr.hist[k])
     assert agree > 0.5 * len(ids) * tr.B
     assert tri_diff <= 0.01 * len(ids), tri_diff
+    if isrc is not None:
+        assert same.mean() > 0.5, same.mean()
+        q = np.asarray(ids)[same]
+        E = isrc.ray_energy.cpu().numpy().astype(np.float64)[q]
+        L = isrc.ray_length.cpu().numpy().astype(np.float64)[q]
+        nh = isrc.ray_hits.cpu().numpy()[q]
+        assert np.array_equal(nh, tr.n_hits[same])
+        assert np.abs(E / tr.E[same] - 1).max() < TOL_E
+        pos = tr.L[same] > 0
+        assert np.abs(L[pos] / tr.L[same][pos] - 1).max() < TOL_T
+        assert np.all(L[~pos] == 0)
     return tri_diff
 
 
@@ -270,7 +286,7 @@ def test_lroom_subset_against_oracle_tree():
     # free running on a seeded 4096-ray subset: reflection (surface) sequences
     ids = np.sort(rng.choice(N, 4096, replace=False))
     tr = oracle.trace(osc, ray_ids=ids, eps_edge_rel=EPS_FREE)
-    _check_free_running(sc, hist, ids, tr)
+    _check_free_running(sc, hist, ids, tr, isrc)
 
 
 @pytest.mark.parametrize("level", [5, 9])
@@ -372,9 +388,9 @@ def test_theatre_lockstep_and_free_running():
     assert len(perf) == isrc.queries
     pick = perf[rng.choice(len(perf), 20_000, replace=False)]
     _check_lockstep(sc, osc, ds_t.cpu().numpy(), dt_t.cpu().numpy(), hist, pick)
-    ids = np.sort(rng.choice(N, 1024, replace=False))
+    ids = np.sort(rng.choice(N, 4096, replace=False))
     tr = oracle.trace(osc, ray_ids=ids, eps_edge_rel=EPS_FREE)
-    _check_free_running(sc, hist, ids, tr)
+    _check_free_running(sc, hist, ids, tr, isrc)
 
 
 def test_deterministic():
