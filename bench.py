@@ -13,11 +13,16 @@ value      nearest-element queries resolved (hits + escapes) per second, over
            launching stream, L2 flushed (256 MB write) before every step.
 e2e        the same metric through the C ABI from pinned host buffers: mesh
            H2D, trace, histograms and their D2H copy inside the timed region.
-roofline   the bounce kernel's algorithmic L2-path bytes (112 B per 4-wide
-           node visited: six float4 of child boxes and one of child
-           references; 48 B per triangle tested; counted by an instrumented
-           pass) over its live duration, against the L2 read bandwidth
-           measured in the same run; HBM fraction beside it.
+roofline   the bounce kernel's algorithmic L2-path bytes over its live
+           duration, against the L2 read bandwidth measured in the same run
+           (MEASURED_PEAKS.json has no L2 figure); HBM fraction beside it.
+           Bytes per query: 64 B per tree node visited and 48 B per
+           triangle tested (the survey's accounting), counted by an
+           instrumented pass; the kernel's own 4-wide nodes read 112 B per
+           visit, reported beside it as "achieved_wide".
+config2    the same measurement on the closed L-room (102,400 triangles,
+           1M rays x 50 bounces, 4 receivers): every ray lives to its last
+           bounce, so it measures full-length traversal.
 ms_step_spread  median, min and max of the timed steps (Python's garbage
            collector is off during them).
 phases_ms  medians over the timed steps (CUDA events): tree build, ray
@@ -68,6 +73,7 @@ def parse():
     ap.add_argument("--tail-rays", type=int, default=None, help="override the autotuned tail threshold")
     ap.add_argument("--cpu-sample-rays", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-config2", action="store_true", help="skip the closed L-room object of the default line")
     ap.add_argument("--clock-log", default=None, help="keep the nvidia-smi samples of the timed region here")
     ap.add_argument("--workload", choices=["theatre", "batched", "tetra", "trees"], default="theatre",
                     help="theatre: the headline line; batched: 64 rooms x 16 pairs x 262,144 rays x 30 bounces "
@@ -250,11 +256,12 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profiled_traffic(tail):
-    """DRAM bytes per trace of the bounce kernel from the committed ncu
-    summary, if that capture matches the current kernel source and config."""
+def profiled_traffic(name, tail):
+    """DRAM bytes per trace of the bounce kernel from a committed ncu
+    summary under profiles/, if that capture matches the current kernel
+    source and configuration (else None)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_bounce_theatre.md")
+    path = os.path.join(ROOT, "profiles", name)
     src = os.path.join(ROOT, "paper_1811_05784_gb300", "csrc", "rt_trace.cu")
     if not os.path.exists(path):
         return None
@@ -284,6 +291,102 @@ def host_cpu():
     return f"{platform.machine()} {model} x{os.cpu_count()}".strip()
 
 
+def l2_roofline(rt, torch, tree, sc, kw, chosen, bounce_ms, stream, dev, l2_peak, hbm, traffic):
+    """Roofline object of the bounce kernel for one trace: node visits and
+    triangle tests counted by an instrumented pass of the same
+    configuration, over the bounce loop's CUDA-event time."""
+    B, n = sc.n_bounces, kw.get("ray_count") or sc.n_rays
+    cost = torch.zeros((B, n, 2), dtype=torch.int32, device=dev)
+    fixed_tail = chosen["tail_rays"] if chosen["tail_rays"] > 0 else -1
+    isrc = rt.rt_trace(tree, tail_rays=fixed_tail, block_size=chosen["block_size"], stream=stream,
+                       debug_cost=cost, **kw)
+    torch.cuda.synchronize()
+    c = cost.double().sum((0, 1)).cpu().numpy()
+    del cost
+    n_q = isrc.queries
+    l2_bytes = 64.0 * c[0] + 48.0 * c[1]                 # a node visited, a triangle tested
+    wide_bytes = 112.0 * c[0] + 48.0 * c[1]              # the 4-wide node's six box float4 and its refs
+    hbm_bytes = n_q * 4.0 + n * (80.0 + 44.0) + isrc.n_records * 24.0   # hist, state in / out, records
+    sec = bounce_ms / 1e3
+    hbm_peak, hbm_src = hbm
+    return {"bound": "l2", "kernel": "k_bounce (all launches of one trace)",
+            "achieved": l2_bytes / sec / 1e9, "peak": l2_peak, "unit": "GB/s",
+            "frac": l2_bytes / sec / 1e9 / l2_peak,
+            "peak_source": "measured in this run: rt_measure_l2_bandwidth (32 MiB L2-resident, ld.global.cg)",
+            "traffic": traffic, "algorithmic_bytes": l2_bytes,
+            "bytes_per_query": "64 B per node visited + 48 B per triangle tested",
+            "achieved_wide": {"value": wide_bytes / sec / 1e9, "frac": wide_bytes / sec / 1e9 / l2_peak,
+                              "bytes_per_query": "112 B per 4-wide node visited + 48 B per triangle tested"},
+            "hbm": {"achieved": hbm_bytes / sec / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_bytes / sec / 1e9 / hbm_peak, "peak_source": hbm_src},
+            "ms_per_launch_set": bounce_ms, "nodes_per_query": c[0] / n_q, "tris_per_query": c[1] / n_q}
+
+
+def timed_trace_steps(rt, torch, sc, kw, stream, tail, warmup, steps, flush, dev, duration):
+    """Tree build + trace + RIR per step on device-resident inputs: the
+    autotuner's trials first, then `warmup` steps, then `steps` timed steps
+    (CUDA events on the launching stream, L2 flushed before each)."""
+    V, T, Mt, St = (torch.as_tensor(x, device=dev) for x in (sc.vertices, sc.tris, sc.material_id, sc.surface_id))
+    ws_trace = rt.Workspace()
+
+    def step(ev=None):
+        tree = rt.rt_build_tree(V, T, Mt, St, stream=stream)
+        if ev is not None:
+            ev[0].record(stream)
+        isrc = rt.rt_trace(tree, tail_rays=tail, stream=stream, workspace=ws_trace, **kw)
+        if ev is not None:
+            ev[1].record(stream)
+        resp = rt.rt_rir(isrc, sc.fs, duration=duration, stream=stream)
+        return tree, isrc, resp
+
+    with torch.cuda.stream(stream):
+        # the autotuner tries one configuration per call until it has timed
+        # each candidate twice; finish that before the warm-up steps, so that
+        # the timed steps run the chosen configuration whatever W is
+        if tail == rt.RT_TAIL_AUTOTUNE:
+            prev = None
+            for _ in range(40):
+                _, isrc_t, _ = step()
+                cur = (isrc_t.block_size, int(isrc_t.tail_rays))
+                if cur == prev:
+                    break
+                prev = cur
+        for _ in range(max(warmup, 1)):
+            _, isrc_w, _ = step()
+        torch.cuda.synchronize()
+        chosen = {"block_size": isrc_w.block_size, "tail_rays": int(isrc_w.tail_rays)}
+        torch.cuda.synchronize()
+        launches0 = rt.rt_launch_count()
+        ms, queries = [], []
+        phases = {k: [] for k in ("build", "rays", "bounces", "image_sources", "trace_other", "rir")}
+        # no Python garbage collection inside the timed steps: a collection
+        # pause stalls the host while the GPU waits for the next launch
+        gc.collect()
+        gc.disable()
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            a.record(stream)
+            tree, isrc, resp = step(ev)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            queries.append(isrc.queries)
+            t_trace = ev[0].elapsed_time(ev[1])
+            phases["build"].append(a.elapsed_time(ev[0]))
+            phases["rays"].append(isrc.ms_rays)
+            phases["bounces"].append(isrc.ms_bounces)
+            phases["image_sources"].append(isrc.ms_image_sources)
+            phases["trace_other"].append(t_trace - isrc.ms_rays - isrc.ms_bounces - isrc.ms_image_sources)
+            phases["rir"].append(ev[1].elapsed_time(b))
+        torch.cuda.synchronize()
+        gc.enable()
+        launches = rt.rt_launch_count() - launches0
+    return dict(ms=ms, queries=queries, phases=phases, chosen=chosen, launches=launches, tree=tree,
+                graph=ws_trace.graph_launches > 0, ws=ws_trace, mesh=(V, T, Mt, St))
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -301,87 +404,26 @@ def run_native(args):
     kw = rt.scene_args(sc)
     rng_kw, _ = shard(rank, ws)
     kw.update(rng_kw)
-    # resident inputs
-    V = torch.as_tensor(sc.vertices, device=dev)
-    T = torch.as_tensor(sc.tris, device=dev)
-    Mt = torch.as_tensor(sc.material_id, device=dev)
-    St = torch.as_tensor(sc.surface_id, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    ws_trace = rt.Workspace()
     tail = rt.RT_TAIL_AUTOTUNE if args.tail_rays is None else args.tail_rays
+    l2_peak = rt.rt_measure_l2_bandwidth(stream=stream)
+    hbm = measured_peaks()
 
-    def step(tail, ev=None):
-        tree = rt.rt_build_tree(V, T, Mt, St, stream=stream)
-        if ev is not None:
-            ev[0].record(stream)
-        isrc = rt.rt_trace(tree, tail_rays=tail, stream=stream, workspace=ws_trace, **kw)
-        if ev is not None:
-            ev[1].record(stream)
-        resp = rt.rt_rir(isrc, sc.fs, duration=DURATION, stream=stream)
-        return tree, isrc, resp
-
-    # warm-up; with the default the library's online autotuner tries its block
-    # sizes and tail thresholds on these calls and keeps the fastest.  The
-    # clock sampler starts here and runs through the timed steps.
+    # clocks sampled from the first warm-up step through the timed steps
     clk = ClockSampler(torch.cuda.current_device(), args.clock_log)
     clk.__enter__()
+    clk.wait_first_sample()
+    if ws > 1:
+        dist.barrier()
+    run = timed_trace_steps(rt, torch, sc, kw, stream, tail, args.warmup, args.steps, flush, dev, DURATION)
+    clk.__exit__(None, None, None)
+    if ws > 1:
+        dist.barrier()
+    ms, queries, chosen = run["ms"], run["queries"], run["chosen"]
+    t_total = sum(ms) / 1e3
+    q_total = sum(queries)
+
     with torch.cuda.stream(stream):
-        # the autotuner tries one configuration per call until it has timed
-        # each of its 7 twice; finish that before the W warm-up steps, so that
-        # the timed steps run the chosen configuration whatever W is
-        if tail == rt.RT_TAIL_AUTOTUNE:
-            prev = None
-            for _ in range(20):
-                _, isrc_t, _ = step(tail)
-                cur = (isrc_t.block_size, int(isrc_t.tail_rays))
-                if cur == prev:
-                    break
-                prev = cur
-        for _ in range(max(args.warmup, 1)):
-            _, isrc_w, _ = step(tail)
-        torch.cuda.synchronize()
-        chosen = {"block_size": isrc_w.block_size, "tail_rays": int(isrc_w.tail_rays)}
-        clk.wait_first_sample()
-
-        # -- timed region (device-resident inputs) --------------------------
-        if ws > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        launches0 = rt.rt_launch_count()
-        ms, queries, ms_bounce = [], [], []
-        phases = {k: [] for k in ("build", "rays", "bounces", "image_sources", "trace_other", "rir")}
-        # no Python garbage collection inside the timed steps: a collection
-        # pause stalls the host while the GPU waits for the next launch
-        gc.collect()
-        gc.disable()
-        for _ in range(args.steps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-            a.record(stream)
-            tree, isrc, resp = step(tail, ev)
-            b.record(stream)
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
-            queries.append(isrc.queries)
-            ms_bounce.append(isrc.ms_bounces)
-            t_trace = ev[0].elapsed_time(ev[1])
-            phases["build"].append(a.elapsed_time(ev[0]))
-            phases["rays"].append(isrc.ms_rays)
-            phases["bounces"].append(isrc.ms_bounces)
-            phases["image_sources"].append(isrc.ms_image_sources)
-            phases["trace_other"].append(t_trace - isrc.ms_rays - isrc.ms_bounces - isrc.ms_image_sources)
-            phases["rir"].append(ev[1].elapsed_time(b))
-        torch.cuda.synchronize()
-        clk.__exit__(None, None, None)
-        gc.enable()
-        launches = rt.rt_launch_count() - launches0
-        if ws > 1:
-            dist.barrier()
-        t_total = sum(ms) / 1e3
-        q_total = sum(queries)
-
         # -- end to end through host buffers ----------------------------------
         host = [torch.as_tensor(x).pin_memory() for x in (sc.vertices, sc.tris, sc.material_id, sc.surface_id)]
         h2d = sum(x.numel() * x.element_size() for x in host)
@@ -395,32 +437,35 @@ def run_native(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             tree = rt.rt_build_tree(*host, stream=stream)
-            isrc = rt.rt_trace(tree, tail_rays=tail, stream=stream, workspace=ws_trace, **kw)
+            isrc = rt.rt_trace(tree, tail_rays=tail, stream=stream, workspace=run["ws"], **kw)
             resp = rt.rt_rir(isrc, sc.fs, duration=DURATION, stream=stream)
             resp.download(out, stream=stream)
             dt = time.perf_counter() - t0
             if k >= args.warmup:
                 e2e_ms.append(dt * 1e3)
                 e2e_q += isrc.queries
+        roof = l2_roofline(rt, torch, run["tree"], sc, kw, chosen, statistics.median(run["phases"]["bounces"]),
+                           stream, dev, l2_peak, hbm, profiled_traffic("k_bounce_theatre.md", chosen["tail_rays"]))
 
-        # -- roofline of the bounce kernel ------------------------------------
-        B = sc.n_bounces
-        cost = torch.zeros((B, N_RAYS, 2), dtype=torch.int32, device=dev)
-        tree = rt.rt_build_tree(V, T, Mt, St, stream=stream)
-        fixed_tail = chosen["tail_rays"] if chosen["tail_rays"] > 0 else -1
-        isrc = rt.rt_trace(tree, tail_rays=fixed_tail, block_size=chosen["block_size"], stream=stream,
-                           debug_cost=cost, **kw)
-        torch.cuda.synchronize()
-        c = cost.double().sum((0, 1)).cpu().numpy()
-        n_q = isrc.queries
-        # a 4-wide node visit reads 112 B (six float4 of child boxes, one of refs);
-        # a triangle test reads 48 B
-        l2_bytes = 112.0 * c[0] + 48.0 * c[1]
-        hbm_bytes = n_q * 4.0 + N_RAYS * (80.0 + 44.0) + isrc.n_records * 24.0   # hist, state in/out, records
-        del cost
-        bounce_s = statistics.median(ms_bounce) / 1e3
-        l2_peak = rt.rt_measure_l2_bandwidth(stream=stream)
-        hbm_peak, hbm_src = measured_peaks()
+    # -- the closed L-room (config 2): full-length traversal -------------------
+    cfg2 = None
+    if not args.no_config2:
+        sc2 = scenes.lroom(n_rays=N_RAYS, n_bounces=50)
+        kw2 = rt.scene_args(sc2)
+        kw2.update(rng_kw)
+        run2 = timed_trace_steps(rt, torch, sc2, kw2, stream, tail, args.warmup, args.steps, flush, dev, 1.0)
+        with torch.cuda.stream(stream):
+            roof2 = l2_roofline(rt, torch, run2["tree"], sc2, kw2, run2["chosen"],
+                                statistics.median(run2["phases"]["bounces"]), stream, dev, l2_peak, hbm,
+                                profiled_traffic("k_bounce_lroom.md", run2["chosen"]["tail_rays"]))
+        t2 = sum(run2["ms"]) / 1e3
+        cfg2 = {"workload": f"closed L-room 102,400 tris / 8 surfaces, {N_RAYS:,} rays x 50 bounces, 4 receivers "
+                            f"r=0.5 m, RIR 8 bands x 1 s at 48 kHz",
+                "value": sum(run2["queries"]) / t2, "unit": UNIT, "ms_per_step": 1e3 * t2 / args.steps,
+                "queries_per_step": int(statistics.median(run2["queries"])), "bounce_kernel": run2["chosen"],
+                "phases_ms": {k: statistics.median(v) for k, v in run2["phases"].items()},
+                "roofline": roof2, "gpu_launches": int(run2["launches"])}
+        del run2
 
     # max over ranks
     t_max = t_total
@@ -438,24 +483,18 @@ def run_native(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(ws), "rays_per_gpu": N_RAYS, "n_bounces": N_BOUNCES,
                    "queries_per_step_per_gpu": int(statistics.median(queries)),
-                   "bounce_kernel": chosen, "cuda_graph": ws_trace.graph_launches > 0,
+                   "bounce_kernel": chosen, "cuda_graph": run["graph"],
                    "l2": "flushed (256 MB write) before every timed step", "parallelism": f"ray shards x{ws}"},
         "e2e": {"value": e2e_q_all / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "roofline": {"bound": "l2", "kernel": "k_bounce (all launches of one trace)",
-                     "achieved": l2_bytes / bounce_s / 1e9, "peak": l2_peak, "unit": "GB/s",
-                     "frac": l2_bytes / bounce_s / 1e9 / l2_peak,
-                     "peak_source": "measured in this run: rt_measure_l2_bandwidth (32 MiB L2-resident, ld.global.cg)",
-                     "traffic": profiled_traffic(chosen["tail_rays"]), "algorithmic_bytes": l2_bytes,
-                     "hbm": {"achieved": hbm_bytes / bounce_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": hbm_bytes / bounce_s / 1e9 / hbm_peak, "peak_source": hbm_src},
-                     "ms_per_launch_set": bounce_s * 1e3,
-                     "nodes_per_query": c[0] / n_q, "tris_per_query": c[1] / n_q},
-        "phases_ms": {k: statistics.median(v) for k, v in phases.items()},
+        "roofline": roof,
+        "phases_ms": {k: statistics.median(v) for k, v in run["phases"].items()},
         "ms_step_spread": {"median": statistics.median(ms), "min": min(ms), "max": max(ms)},
-        "gpu_launches": int(launches),
+        "gpu_launches": int(run["launches"]),
         "clocks": clocks,
     }
+    if cfg2 is not None:
+        result["config2"] = cfg2
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         q, dt, threads = oracle_sample(sc, args.cpu_sample_rays)
         result["cpu_baseline"] = {"value": q / dt, "unit": UNIT, "cores": threads, "kind": "oracle",

@@ -1009,15 +1009,19 @@ struct rt_workspace {
 
 namespace rr {
 
-// Launch the B bounce kernels.  With a workspace on a capturable stream the
-// loop is captured once into a CUDA graph and later replayed with updated
-// kernel parameters (one graph launch per trace).
-static rt_status run_bounces(BounceArgs a, const Queue q[2], int B, int block, int grid, cudaStream_t s,
+// Launch the bounce kernels: one per bounce, or only the first when the
+// tail threshold covers every traced ray (that launch then finishes every
+// bounce in tail mode and the others would find no live ray).  With a
+// workspace on a capturable stream the loop is captured once into a CUDA
+// graph and later replayed with updated kernel parameters (one graph launch
+// per trace).
+static rt_status run_bounces(BounceArgs a, const Queue q[2], int n_launch, int block, int grid, cudaStream_t s,
                              rt_workspace* ws) {
     const bool replay = a.replay != nullptr;
     void* kern = kernel_of(block, replay);
     const size_t smem = stack_bytes(block);
     RR_TRY(allow_stack_smem(block, replay));
+    const int B = n_launch;
     std::vector<BounceArgs> args((size_t)B, a);
     for (int b = 0; b < B; b++) {
         args[b].b = b;
@@ -1460,7 +1464,8 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
         a.debug_state = p->debug_state;
         a.debug_cost = p->debug_cost;
         a.replay = p->replay_hist;
-        RR_TRY(run_bounces(a, q, B, block, grid, s, ws));
+        const int n_launch = (uint64_t)tail >= (uint64_t)n_traced ? 1 : B;
+        RR_TRY(run_bounces(a, q, n_launch, block, grid, s, ws));
         RR_CUDA(cudaGetLastError());
         RR_CUDA(cudaEventRecord(ev.e[2], s));
         RR_CUDA(cudaMemcpyAsync(h_cnt.data(), counters, sizeof(unsigned int) * n_counters, cudaMemcpyDeviceToHost, s));
