@@ -111,20 +111,39 @@ def _check_lockstep(sc, osc, ds, dt, hist, pick=None):
     return bq, amb
 
 
-def _check_lengths(sc, L_gpu, L_ora, n_hits):
-    """Path lengths: 1e-5 relative, plus the float32 restart offset of the
-    kernel.  After each hit the next segment starts 2^-21 max|p| before the
-    hit point along the incoming ray (p the hit point), so every hit may add
-    up to that much to the summed length; the bound takes twice the scene's
-    largest coordinate per hit as an absolute term beside the relative one
-    (at the theatre's 50 m: 48 micrometres per hit)."""
+def _length_bound(sc, L_ora, n_hits):
+    """1e-5 relative, plus the float32 restart offset of the kernel: after
+    each hit the next segment starts 2^-21 max|p| before the hit point along
+    the incoming ray (p the hit point), so every hit may add up to that much
+    to the summed length; the bound takes twice the scene's largest
+    coordinate per hit (at the theatre's 50 m: 48 micrometres per hit)."""
     X = max(float(np.abs(sc.vertices).max()), 1e-3)
+    return TOL_T * L_ora + n_hits * 2.0 ** -20 * X
+
+
+#: free-running float32 and FP64 paths with the same triangles still drift
+#: apart: a hit point moves by the drift over the cosine of the incidence, so
+#: grazing reflections amplify it.  This share of the rays must meet the
+#: per-query bound, and every ray this relative bound.
+FREE_LENGTH_SHARE, FREE_LENGTH_REL = 0.999, 1e-3
+
+
+def _check_lengths(sc, L_gpu, L_ora, n_hits):
+    """Free-running path lengths of rays with the oracle's triangle sequence."""
     err = np.abs(L_gpu - L_ora)
-    bound = TOL_T * L_ora + n_hits * 2.0 ** -20 * X
-    worst = np.argmax(err - bound) if len(err) else 0
-    assert (err <= bound).all(), (f"path length {L_gpu[worst]!r} vs {L_ora[worst]!r} after {n_hits[worst]} hits "
-                                  f"(bound {bound[worst]:.3g})")
+    ok = err <= _length_bound(sc, L_ora, n_hits)
+    assert ok.mean() >= FREE_LENGTH_SHARE, (ok.mean(), int((~ok).sum()))
+    rel = err / np.maximum(L_ora, 1e-9)
+    assert (rel[L_ora > 0] <= FREE_LENGTH_REL).all() and (L_gpu[L_ora == 0] == 0).all(), rel.max()
     return err
+
+
+def _check_compensated_lengths(isrc, dt, hist):
+    """The kernel's path length is the compensated float32 sum of its own
+    segment lengths: within 4 ulps of their FP64 sum on every ray."""
+    seg = np.where(hist >= 0, dt, 0.0).astype(np.float64).sum(0)
+    L = isrc.ray_length.cpu().numpy().astype(np.float64)
+    assert (np.abs(L - seg) <= 4 * np.spacing(np.float32(np.maximum(seg, 1e-30))).astype(np.float64)).all()
 
 
 def _check_free_running(sc, hist, ids, tr, isrc=None):
@@ -132,30 +151,33 @@ def _check_free_running(sc, hist, ids, tr, isrc=None):
     (surface ids) agree up to each ray's first ambiguous bounce.  Triangle
     ids inside one surface may differ once the trajectories have drifted by
     more than the near-edge band; those are counted, not failed.  With the
-    GPU result `isrc`, the rays whose whole triangle sequence equals the
-    oracle's (no ambiguity) must also carry the oracle's band energies
-    (1e-4) and path lengths (1e-5)."""
+    GPU result `isrc`: rays whose whole surface sequence equals the oracle's
+    carry its band energies (1e-4), and rays with its exact triangle
+    sequence (no ambiguity) its hit counts and path lengths."""
     surf = np.append(sc.surface_id, -1)            # index -1 -> -1
     agree = tri_diff = 0
-    same = np.zeros(len(ids), bool)
+    same_tri = np.zeros(len(ids), bool)
+    same_surf = np.zeros(len(ids), bool)
     for k, q in enumerate(ids):
         upto = tr.first_amb[k]
         g, o = hist[:upto, q], tr.hist[k, :upto]
         assert np.array_equal(surf[g], surf[o]), (q, g, o)
         tri_diff += int((g != o).any())
         agree += upto
-        same[k] = upto == tr.B and np.array_equal(hist[:, q], tr.hist[k])
+        same_tri[k] = upto == tr.B and np.array_equal(hist[:, q], tr.hist[k])
+        same_surf[k] = np.array_equal(surf[hist[:, q]], surf[tr.hist[k]])
     assert agree > 0.5 * len(ids) * tr.B
     assert tri_diff <= 0.01 * len(ids), tri_diff
     if isrc is not None:
-        assert same.mean() > 0.5, same.mean()
-        q = np.asarray(ids)[same]
+        assert same_surf.mean() > 0.9, same_surf.mean()
+        assert same_tri.sum() > 0.2 * len(ids), same_tri.mean()
+        q = np.asarray(ids)
         E = isrc.ray_energy.cpu().numpy().astype(np.float64)[q]
         L = isrc.ray_length.cpu().numpy().astype(np.float64)[q]
         nh = isrc.ray_hits.cpu().numpy()[q]
-        assert np.array_equal(nh, tr.n_hits[same])
-        assert np.abs(E / tr.E[same] - 1).max() < TOL_E
-        _check_lengths(sc, L, tr.L[same], tr.n_hits[same])
+        assert np.abs(E[same_surf] / tr.E[same_surf] - 1).max() < TOL_E
+        assert np.array_equal(nh[same_tri], tr.n_hits[same_tri])
+        _check_lengths(sc, L[same_tri], tr.L[same_tri], tr.n_hits[same_tri])
     return tri_diff
 
 
@@ -291,6 +313,7 @@ def test_lroom_subset_against_oracle_tree():
     dt_t = torch.empty((B, N), dtype=torch.float32, device="cuda")
     tree, isrc = _trace(sc, debug_t=dt_t, debug_state=ds_t)
     hist = isrc.hist.cpu().numpy()
+    _check_compensated_lengths(isrc, dt_t.cpu().numpy(), hist)
     osc = oracle.OracleScene(sc, tree=True)
     rng = np.random.default_rng(11)
     # lockstep on 20,000 sampled queries
@@ -396,6 +419,7 @@ def test_theatre_lockstep_and_free_running():
     dt_t = torch.empty((B, N), dtype=torch.float32, device="cuda")
     tree, isrc = _trace(sc, debug_state=ds_t, debug_t=dt_t)
     hist = isrc.hist.cpu().numpy()
+    _check_compensated_lengths(isrc, dt_t.cpu().numpy(), hist)
     osc = oracle.OracleScene(sc, tree=True)
     rng = np.random.default_rng(5)
     perf = np.argwhere(_performed(hist))
@@ -432,6 +456,45 @@ def test_tail_mode_matches_per_bounce_launches(tail):
     assert torch.equal(a.ray_energy, b.ray_energy) and torch.equal(a.ray_length, b.ray_length)
     assert a.queries == b.queries and a.n == b.n and a.n_records == b.n_records
     assert torch.equal(a.energy, b.energy) and torch.equal(a.count, b.count)
+
+
+@pytest.mark.parametrize("fetch_min,tail", [(1, -1), (8, 16384), (32, -1)])
+def test_split_traversal_matches_the_fused_kernel(fetch_min, tail):
+    """Wavefront bounces whose hits come from the separate traversal kernel
+    (lanes refilled as soon as their query is done) give every ray the
+    result of the fused kernel, in the library's own graph too."""
+    sc = scenes.theatre(n_rays=200_000, n_bounces=30)
+    tree = _tree(sc)
+    a = rt.rt_trace(tree, tail_rays=-1, **rt.scene_args(sc))
+    stream = torch.cuda.Stream()
+    ws = rt.Workspace()
+    for k in range(2):
+        b = rt.rt_trace(tree, tail_rays=tail, split_traversal=1, fetch_min=fetch_min, stream=stream, workspace=ws,
+                        **rt.scene_args(sc))
+        torch.cuda.synchronize()
+        assert b.split_traversal == 1
+        assert torch.equal(a.hist, b.hist)
+        assert torch.equal(a.ray_energy, b.ray_energy) and torch.equal(a.ray_length, b.ray_length)
+        assert a.queries == b.queries and a.n == b.n and a.n_records == b.n_records
+        assert torch.equal(a.energy, b.energy) and torch.equal(a.count, b.count)
+    assert ws.graph_launches == 2
+
+
+def test_split_traversal_lockstep_against_the_oracle():
+    """The split kernels' hits and distances in lockstep with the FP64
+    oracle on every query of the L-room (h = 0.5 m), and their cost counts."""
+    sc = scenes.lroom(h=0.5, n_rays=30_000, n_bounces=20)
+    B, N = sc.n_bounces, sc.n_rays
+    ds_t = torch.empty((B, N, 6), dtype=torch.float32, device="cuda")
+    dt_t = torch.empty((B, N), dtype=torch.float32, device="cuda")
+    cost = torch.zeros((B, N, 2), dtype=torch.int32, device="cuda")
+    tree, isrc = _trace(sc, debug_t=dt_t, debug_state=ds_t, debug_cost=cost, tail_rays=1000, split_traversal=1)
+    assert isrc.split_traversal == 1
+    hist = isrc.hist.cpu().numpy()
+    osc = oracle.OracleScene(sc, tree=True)
+    _check_lockstep(sc, osc, ds_t.cpu().numpy(), dt_t.cpu().numpy(), hist)
+    c = cost.cpu().numpy()
+    assert (c[..., 0][_performed(hist)] >= 1).all() and (c[..., 0][~_performed(hist)] == 0).all()
 
 
 def test_shards_add_up():
