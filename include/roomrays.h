@@ -138,14 +138,6 @@ typedef struct {
                                 receivers gives.  A recorded id outside the mesh is reported
                                 (RT_ERR_INTERNAL); a history of other rays gives other
                                 (meaningless) paths. */
-    int32_t split_traversal; /* 1: each wavefront bounce (live rays above the tail threshold)
-                                finds its nearest hits in a separate traversal kernel whose
-                                lanes take a new query as soon as theirs is done, then shades
-                                (spheres, records, reflection, compaction) in the bounce
-                                kernel; 0: one fused kernel.  Results do not depend on it;
-                                RT_TAIL_AUTOTUNE chooses it too.  Ignored for replays. */
-    int32_t fetch_min;       /* split traversal: idle lanes of a warp that trigger a refill
-                                (1..32; 0 = 8) */
 } rt_trace_params;
 
 #define RT_TAIL_AUTOTUNE (-2)
@@ -191,7 +183,6 @@ typedef struct {
     float ms_bounces;          /* device time of all bounce launches */
     float ms_image_sources;    /* device time of dedup + FP64 reconstruction */
     int32_t n_rcv;             /* receivers of the trace (all rooms of a batch) */
-    int32_t split_traversal;   /* 1 if wavefront bounces ran the separate traversal kernel */
 } rt_is_view;
 
 typedef struct {

@@ -104,7 +104,6 @@ struct BounceArgs {
     float* debug_state;
     int32_t* debug_cost;
     const int32_t* __restrict__ replay;  // [B][n_traced] hits of an earlier trace of the same rays, or null
-    const int2* __restrict__ hit;        // [slot] nearest hits of the in-queue found by k_traverse, or null
 };
 
 // ---------------------------------------------------------------------------
@@ -469,7 +468,7 @@ __device__ __forceinline__ void load_ray(const Queue& q, unsigned int slot, RayS
 // it; lanes without a ray pass active = false.  Returns true if the ray goes on.
 template <int BT, bool REPLAY>
 __device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool active, int bb, RayState& s,
-                                         int* __restrict__ stack, bool pre = false, int2 pre_hit = int2{}) {
+                                         int* __restrict__ stack) {
     const int q = (int)s.m.x;
     const int src = active ? (int)(q / a.per_src) : 0;
     const RoomDev& rm = a.rooms[active ? a.room_of_src[src] : 0];
@@ -480,14 +479,10 @@ __device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool act
     RayPre rp = ray_pre(make_float3(o4.x, o4.y, o4.z), make_float3(d4.x, d4.y, d4.z));
     int n_nodes = 0, n_tests = 0;
     if (active) {
-        if (REPLAY) {  // the query re-tests the triangle an earlier trace recorded
+        if (REPLAY)  // the query re-tests the triangle an earlier trace recorded
             replay_hit(a, rm, rp, (int)s.m.y, bb, q, best_t, hit, err, n_tests);
-        } else if (pre) {  // found by k_traverse for this queue slot
-            hit = pre_hit.x;
-            best_t = __int_as_float(pre_hit.y);
-        } else {
+        else
             nearest_hit<BT>(a, rm, rp, (int)s.m.y, best_t, hit, err, n_nodes, n_tests, stack);
-        }
     }
     if (err) atomicOr(a.status, err);
     const unsigned int amask = __ballot_sync(0xffffffffu, active);
@@ -534,7 +529,7 @@ __device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool act
     const int64_t hb = (int64_t)bb * a.n_traced + q;
     a.hist[hb] = hit;
     if (a.debug_t) a.debug_t[hb] = seg;
-    if (a.debug_cost && !pre) {  // k_traverse wrote the cost of precomputed hits
+    if (a.debug_cost) {
         a.debug_cost[2 * hb] = n_nodes;
         a.debug_cost[2 * hb + 1] = n_tests;
     }
@@ -621,13 +616,7 @@ __global__ void __launch_bounds__(BT) k_bounce(BounceArgs a) {
             s.e0 = s.e1 = s.o;
             s.m = make_uint4(0, 0xFFFFFFFFu, 0, 0);
             if (active) load_ray(a.in, slot, s);
-            bool survive;
-            if (a.hit) {  // hits found by k_traverse: no traversal here
-                const int2 h = active ? a.hit[slot] : make_int2(-1, 0);
-                survive = step_ray<BT, REPLAY>(a, lane, active, b, s, stack, true, h);
-            } else {
-                survive = step_ray<BT, REPLAY>(a, lane, active, b, s, stack);
-            }
+            const bool survive = step_ray<BT, REPLAY>(a, lane, active, b, s, stack);
             const unsigned int mask = __ballot_sync(0xffffffffu, survive);
             if (mask) {
                 unsigned int obase = 0;
@@ -680,173 +669,6 @@ __global__ void __launch_bounds__(BT) k_bounce(BounceArgs a) {
                 has = false;
         }
     }
-}
-
-// ---------------------------------------------------------------------------
-// k_traverse: the nearest-hit queries of one wavefront bounce alone.
-//
-// The fused kernel above keeps a ray's whole state (energies, hash, path
-// length) in registers during its traversal, and a warp moves to its next
-// queries only when its slowest lane has finished (a query costs from a few
-// to a few hundred node visits).  This kernel holds only what the traversal
-// reads (origin, reciprocal direction, shear constants, the surface just left)
-// and refills each lane as soon as its query is done: lanes whose query has
-// finished publish (triangle, distance) for their queue slot, and once at
-// least fetch_min lanes of the warp are idle they take the next slots with
-// one atomic per warp (dynamic fetch, Aila & Laine 2009).  k_bounce then
-// reads these hits for the spheres, records, reflection and compaction of the
-// same bounce.  The traversal itself (slab test, child order, postponed
-// leaves, watertight triangle test, bounds and visit caps) is that of
-// nearest_hit, so the hits are the same.
-// ---------------------------------------------------------------------------
-struct TravArgs {
-    const RoomDev* __restrict__ rooms;
-    const int32_t* __restrict__ room_of_src;
-    const float4* __restrict__ o;    // in-queue origins
-    const float4* __restrict__ d;    // in-queue directions
-    const uint4* __restrict__ m;     // in-queue (ray, last surface, hash)
-    int2* __restrict__ hit;          // [slot] (triangle id or -1, distance bits)
-    const unsigned int* live;        // [B+1]
-    unsigned int* fetch;             // [B] slot counter of this kernel (separate from k_bounce's)
-    unsigned int* status;
-    int64_t per_src;
-    int64_t n_traced;
-    int b;
-    unsigned int tail_threshold;
-    int step_cap;
-    int fetch_min;
-    int32_t* debug_cost;
-};
-
-template <int BT, int STACK>
-__global__ void __launch_bounds__(BT) k_traverse(TravArgs a) {
-    extern __shared__ int s_trav[];  // STACK * BT entries
-    int* stack = s_trav + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    const unsigned int n_live = a.live[a.b];
-    if (n_live == 0 || n_live <= a.tail_threshold) return;  // k_bounce finishes these in tail mode
-    const int SENTINEL = 0x7FFFFFFF;
-    RayPre r;
-    r.o = r.d = r.inv = make_float3(0.f, 0.f, 1.f);
-    r.kx = 0, r.ky = 1, r.kz = 2;
-    r.Sx = r.Sy = 0.f, r.Sz = 1.f;
-    const float4* nodes = nullptr;
-    const float4* tris = nullptr;
-    int64_t n_nodes = 0, n_tris = 0;
-    int exclude = -1;
-    unsigned int slot = 0;
-    bool has = false, exhausted = false;
-    int node = SENTINEL, leaf = 0, sp = 0, steps = 0, cn = 0, ct = 0;
-    float best_t = INFINITY;
-    int best_id = 0x7FFFFFFF;
-    unsigned int err = 0;
-    for (;;) {
-        if (has && node == SENTINEL && leaf == 0) {  // query done: publish its hit
-            a.hit[slot] = make_int2(best_id == 0x7FFFFFFF ? -1 : best_id, __float_as_int(best_t));
-            if (a.debug_cost) {
-                const int64_t hb = (int64_t)a.b * a.n_traced + (int64_t)__ldg(&a.m[slot].x);
-                a.debug_cost[2 * hb] = cn;
-                a.debug_cost[2 * hb + 1] = ct;
-            }
-            has = false;
-        }
-        const unsigned int idle = __ballot_sync(0xffffffffu, !has);
-        if (idle && !exhausted && (__popc(idle) >= a.fetch_min || idle == 0xffffffffu)) {
-            const int leader = __ffs(idle) - 1;
-            unsigned int base = 0;
-            if (lane == leader) base = atomicAdd(&a.fetch[a.b], (unsigned int)__popc(idle));
-            base = __shfl_sync(0xffffffffu, base, leader);
-            if (!has) {
-                const unsigned int my = base + __popc(idle & ((1u << lane) - 1u));
-                if (my < n_live) {
-                    slot = my;
-                    const float4 o4 = a.o[slot], d4 = a.d[slot];
-                    const uint4 m4 = a.m[slot];
-                    r = ray_pre(make_float3(o4.x, o4.y, o4.z), make_float3(d4.x, d4.y, d4.z));
-                    exclude = (int)m4.y;
-                    const RoomDev* rm = a.rooms + a.room_of_src[(int64_t)m4.x / a.per_src];
-                    nodes = rm->nodes;
-                    tris = rm->tris;
-                    n_nodes = rm->n_nodes;
-                    n_tris = rm->n_tris;
-                    node = 0, leaf = 0, sp = 0, steps = 0, cn = 0, ct = 0;
-                    best_t = INFINITY;
-                    best_id = 0x7FFFFFFF;
-                    has = true;
-                }
-            }
-            exhausted = base + __popc(idle) >= n_live;
-        }
-        if (__ballot_sync(0xffffffffu, has) == 0) {
-            if (exhausted) break;
-            continue;
-        }
-        // descend until every lane with a query holds a postponed leaf (or is done)
-        while ((unsigned)node < (unsigned)SENTINEL) {
-            if (++steps > a.step_cap) {
-                err |= ST_STEPS;
-                node = SENTINEL, leaf = 0;
-                break;
-            }
-            if ((int64_t)node >= n_nodes) {  // never read outside the node array
-                err |= ST_BOUNDS;
-                node = SENTINEL, leaf = 0;
-                break;
-            }
-            const float4* np = nodes + 8 * (int64_t)node;
-            const float4 lx = __ldg(np), ly = __ldg(np + 1), lz = __ldg(np + 2);
-            const float4 hx = __ldg(np + 3), hy = __ldg(np + 4), hz = __ldg(np + 5);
-            const int4 ref = __ldg(reinterpret_cast<const int4*>(np + 6));
-            cn++;
-            float t0 = slab(r, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x, best_t);
-            float t1 = slab(r, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, best_t);
-            float t2 = slab(r, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z, best_t);
-            float t3 = slab(r, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w, best_t);
-            int r0 = ref.x, r1 = ref.y, r2 = ref.z, r3 = ref.w;
-            cswap(t0, r0, t1, r1);
-            cswap(t2, r2, t3, r3);
-            cswap(t0, r0, t2, r2);
-            cswap(t1, r1, t3, r3);
-            cswap(t1, r1, t2, r2);
-            if (!(t0 < INFINITY)) {
-                node = sp > 0 ? stack[--sp * BT] : SENTINEL;
-            } else {
-                node = r0;
-                const int push = (t1 < INFINITY) + (t2 < INFINITY) + (t3 < INFINITY);
-                if (sp + push > STACK) {
-                    err |= ST_STACK;
-                    node = SENTINEL, leaf = 0;
-                    break;
-                }
-                if (t3 < INFINITY) stack[sp++ * BT] = r3;
-                if (t2 < INFINITY) stack[sp++ * BT] = r2;
-                if (t1 < INFINITY) stack[sp++ * BT] = r1;
-            }
-            if (node < 0 && leaf == 0) {  // postpone the leaf, keep descending
-                leaf = node;
-                node = sp > 0 ? stack[--sp * BT] : SENTINEL;
-            }
-            if (__all_sync(__activemask(), leaf != 0)) break;
-        }
-        // test the postponed leaves (and leaves popped right after them)
-        while (leaf != 0) {
-            const int code = ~leaf;
-            const int first = code >> 3, cnt = code & 7;
-            if ((int64_t)first + cnt > n_tris) {
-                err |= ST_BOUNDS;
-                node = SENTINEL, leaf = 0;
-                break;
-            }
-            for (int k = 0; k < cnt; k++) tri_test(r, tris + 3 * (int64_t)(first + k), exclude, best_t, best_id);
-            ct += cnt;
-            leaf = 0;
-            if (node < 0) {  // a leaf popped from the stack
-                leaf = node;
-                node = sp > 0 ? stack[--sp * BT] : SENTINEL;
-            }
-        }
-    }
-    if (err) atomicOr(a.status, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -1031,18 +853,11 @@ static rt_status alloc_queue(Arena& ar, Queue& q, int64_t n) {
 // each run the next candidate, every candidate twice (the faster time counts,
 // which keeps one noisy call from deciding), and then the fastest is kept
 // (optionally persisted in the file named by RT_AUTOTUNE_CACHE).
-// A configuration also chooses how wavefront bounces find their hits: inside
-// k_bounce, or in k_traverse (dynamic fetch, fetch_min idle lanes per refill)
-// followed by k_bounce for the rest of the bounce.
 struct Config {
     int block;
-    int tail_mode;  // 0 never, 1 resident threads, 2 every ray, 3 SPLIT_TAIL_RAYS
-    int split;      // 1: k_traverse + k_bounce per wavefront bounce
-    int fetch_min;
+    int tail_mode;  // 0 never, 1 resident threads, 2 every ray
 };
-static constexpr unsigned int SPLIT_TAIL_RAYS = 16384;
-static const Config CANDIDATES[] = {{128, 2, 0, 0}, {256, 2, 0, 0}, {128, 1, 0, 0}, {128, 0, 0, 0},
-                                    {128, 1, 1, 8},  {256, 1, 1, 8}, {128, 3, 1, 8}, {128, 3, 1, 16}};
+static const Config CANDIDATES[] = {{128, 2}, {128, 1}, {64, 2}, {256, 2}, {128, 0}, {64, 1}, {256, 1}};
 static constexpr int N_CANDIDATES = sizeof(CANDIDATES) / sizeof(CANDIDATES[0]);
 static constexpr int TUNE_ROUNDS = 2;
 
@@ -1158,27 +973,6 @@ static int grid_of_block(int block) {
     }
 }
 
-// the traversal kernel: its stack, kernel pointer and persistent grid
-static constexpr int TRAV_STACK = 64;
-static size_t trav_stack_bytes(int block) { return sizeof(int) * (size_t)TRAV_STACK * (size_t)block; }
-
-static void* trav_kernel_of(int block) {
-    switch (block) {
-        case 64: return (void*)k_traverse<64, TRAV_STACK>;
-        case 256: return (void*)k_traverse<256, TRAV_STACK>;
-        default: return (void*)k_traverse<128, TRAV_STACK>;
-    }
-}
-
-static rt_status trav_grid(int block, int* grid) {
-    void* k = trav_kernel_of(block);
-    RR_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trav_stack_bytes(block)));
-    int occ = 0;
-    RR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, block, trav_stack_bytes(block)));
-    *grid = device_sm_count() * std::max(occ, 1);
-    return RT_OK;
-}
-
 }  // namespace rr
 
 // -- workspace: reusable scratch and the graph of the bounce loop ------------
@@ -1193,9 +987,8 @@ struct rt_workspace {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     std::vector<cudaGraphNode_t> nodes;
-    int g_b = 0, g_grid = 0, g_block = 0, g_tgrid = 0;
+    int g_b = 0, g_grid = 0, g_block = 0;
     bool g_replay = false;
-    int2* hit = nullptr;  // [cap_rays] hits of k_traverse
     long long graph_launches = 0;
     unsigned long long last_records = 0;  // capacity hint for the next trace
 
@@ -1216,103 +1009,82 @@ struct rt_workspace {
 
 namespace rr {
 
-// Launch the bounce kernels: per bounce k_bounce, preceded by k_traverse
-// when `ta` is given; or only the first k_bounce when the tail threshold
-// covers every traced ray (that launch then finishes every bounce in tail
-// mode and the others would find no live ray).  With a workspace on a
-// capturable stream the launches are captured once into a CUDA graph and
-// later replayed with updated kernel parameters (one graph launch per trace).
-static rt_status run_bounces(BounceArgs a, const Queue q[2], int n_launch, int block, int grid, const TravArgs* ta,
-                             int tgrid, cudaStream_t s, rt_workspace* ws) {
+// Launch the bounce kernels: one per bounce, or only the first when the
+// tail threshold covers every traced ray (that launch then finishes every
+// bounce in tail mode and the others would find no live ray).  With a
+// workspace on a capturable stream the loop is captured once into a CUDA
+// graph and later replayed with updated kernel parameters (one graph launch
+// per trace).
+static rt_status run_bounces(BounceArgs a, const Queue q[2], int n_launch, int block, int grid, cudaStream_t s,
+                             rt_workspace* ws) {
     const bool replay = a.replay != nullptr;
     void* kern = kernel_of(block, replay);
     const size_t smem = stack_bytes(block);
     RR_TRY(allow_stack_smem(block, replay));
     const int B = n_launch;
     std::vector<BounceArgs> args((size_t)B, a);
-    std::vector<TravArgs> targs(ta ? (size_t)B : 0);
-    struct Launch {
-        void* func;
-        int grid;
-        size_t smem;
-        void* arg;
-    };
-    std::vector<Launch> L;
     for (int b = 0; b < B; b++) {
         args[b].b = b;
         args[b].in = q[b & 1];
         args[b].out = q[(b + 1) & 1];
-        if (ta) {
-            targs[b] = *ta;
-            targs[b].b = b;
-            targs[b].o = q[b & 1].o;
-            targs[b].d = q[b & 1].d;
-            targs[b].m = q[b & 1].m;
-            L.push_back({trav_kernel_of(block), tgrid, trav_stack_bytes(block), &targs[b]});
-        }
-        L.push_back({kern, grid, smem, &args[b]});
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     const bool can_graph = ws && s != nullptr && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
                            cs == cudaStreamCaptureStatusNone;
     cudaGetLastError();
-    const int n = (int)L.size();
     if (!can_graph) {
-        for (auto& l : L) {
-            void* params[] = {l.arg};
-            RR_CUDA(cudaLaunchKernel(l.func, dim3(l.grid), dim3(block), params, l.smem, s));
+        for (int b = 0; b < B; b++) {
+            void* params[] = {&args[b]};
+            RR_CUDA(cudaLaunchKernel(kern, dim3(grid), dim3(block), params, smem, s));
             note_launch();
         }
         return RT_OK;
     }
-    const int tg = ta ? tgrid : 0;
-    if (!ws->exec || ws->g_b != n || ws->g_grid != grid || ws->g_block != block || ws->g_replay != replay ||
-        ws->g_tgrid != tg) {
+    if (!ws->exec || ws->g_b != B || ws->g_grid != grid || ws->g_block != block || ws->g_replay != replay) {
         ws->release_graph();
         RR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        for (auto& l : L) {
-            void* params[] = {l.arg};
-            cudaLaunchKernel(l.func, dim3(l.grid), dim3(block), params, l.smem, s);
+        for (int b = 0; b < B; b++) {
+            void* params[] = {&args[b]};
+            cudaLaunchKernel(kern, dim3(grid), dim3(block), params, smem, s);
         }
         cudaGraph_t g = nullptr;
         RR_CUDA(cudaStreamEndCapture(s, &g));
         ws->graph = g;
         RR_CUDA(cudaGraphInstantiate(&ws->exec, g, 0));
         // the captured launches form a chain: walk it from the root
-        size_t nr = 1;
+        size_t n = 1;
         cudaGraphNode_t node;
-        RR_CUDA(cudaGraphGetRootNodes(g, &node, &nr));
+        RR_CUDA(cudaGraphGetRootNodes(g, &node, &n));
         ws->nodes.clear();
-        for (int k = 0; k < n; k++) {
+        for (int b = 0; b < B; b++) {
             ws->nodes.push_back(node);
             size_t nd = 1;
             cudaGraphNode_t next = nullptr;
-            if (k + 1 < n) {
+            if (b + 1 < B) {
                 RR_CUDA(cudaGraphNodeGetDependentNodes(node, &next, nullptr, &nd));
                 node = next;
             }
         }
-        ws->g_b = n;
+        ws->g_b = B;
         ws->g_grid = grid;
-        ws->g_tgrid = tg;
         ws->g_block = block;
         ws->g_replay = replay;
     } else {
-        for (int k = 0; k < n; k++) {
+        for (int b = 0; b < B; b++) {
             cudaKernelNodeParams kp{};
-            void* params[] = {L[k].arg};
-            kp.func = L[k].func;
-            kp.gridDim = dim3(L[k].grid);
+            void* params[] = {&args[b]};
+            kp.func = kern;
+            kp.gridDim = dim3(grid);
             kp.blockDim = dim3(block);
-            kp.sharedMemBytes = (unsigned int)L[k].smem;
+            kp.sharedMemBytes = (unsigned int)smem;
             kp.kernelParams = params;
             kp.extra = nullptr;
-            RR_CUDA(cudaGraphExecKernelNodeSetParams(ws->exec, ws->nodes[k], &kp));
+            RR_CUDA(cudaGraphExecKernelNodeSetParams(ws->exec, ws->nodes[b], &kp));
         }
     }
     RR_CUDA(cudaGraphLaunch(ws->exec, s));
     ws->graph_launches++;
-    for (int k = 0; k < n; k++) note_launch();
+    for (int b = 0; b < B; b++) note_launch();
     return RT_OK;
 }
 
@@ -1549,9 +1321,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     Queue q[2];
     unsigned int* counters;
     unsigned long long* n2d;
-    // live[B+1], k_bounce's fetch[B], status, two spare words, k_traverse's fetch[B]
-    const int n_counters = 3 * B + 4;
-    int2* hit_buf;
+    const int n_counters = 2 * B + 4;
     if (ws) {
         if (ws->cap_rays < n_traced || ws->cap_b < B) {
             ws->release_graph();
@@ -1562,7 +1332,6 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
             RR_TRY(alloc_queue(war, ws->q[1], n_traced));
             RR_TRY(war.alloc(&ws->counters, n_counters));
             RR_TRY(war.alloc(&ws->n2, 2));
-            RR_TRY(war.alloc(&ws->hit, n_traced));
             ws->owned = war.release();
             ws->cap_rays = n_traced;
             ws->cap_b = B;
@@ -1571,13 +1340,11 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
         q[1] = ws->q[1];
         counters = ws->counters;
         n2d = ws->n2;
-        hit_buf = ws->hit;
     } else {
         RR_TRY(alloc_queue(tmp, q[0], n_traced));
         RR_TRY(alloc_queue(tmp, q[1], n_traced));
         RR_TRY(tmp.alloc(&counters, n_counters));
         RR_TRY(tmp.alloc(&n2d, 2));
-        RR_TRY(tmp.alloc(&hit_buf, n_traced));
     }
     // primary rays first, so that the GPU works while the host prepares the rest
     struct Events {
@@ -1623,26 +1390,17 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     int cand = -1;
     int block = p->block_size > 0 ? p->block_size : 128;
     int tail_mode = p->tail_rays < 0 ? 0 : 1;
-    int split = p->split_traversal > 0 ? 1 : 0;
-    int fetch_min = p->fetch_min > 0 ? std::min(p->fetch_min, 32) : 8;
     if (autotune) {
         key = tune_key(h.total_tris, n_traced, B, n_rooms) + (p->replay_hist ? "_replay" : "");
         cand = tune_pick(key);
         block = CANDIDATES[cand].block;
         tail_mode = CANDIDATES[cand].tail_mode;
-        split = CANDIDATES[cand].split;
-        fetch_min = std::max(CANDIDATES[cand].fetch_min, 1);
     }
-    if (p->replay_hist) split = 0;  // a replay re-tests one recorded triangle per query
     const int grid = grid_of_block(block);
-    int tgrid = 0;
-    if (split) RR_TRY(trav_grid(block, &tgrid));
     unsigned int tail = 0;
     if (autotune) {
-        tail = tail_mode == 0   ? 0u
-               : tail_mode == 1 ? (unsigned int)grid * (unsigned int)block
-               : tail_mode == 3 ? SPLIT_TAIL_RAYS
-                                : (unsigned int)std::min<int64_t>(n_traced, UINT32_MAX);
+        tail = tail_mode == 0 ? 0u : (tail_mode == 1 ? (unsigned int)grid * (unsigned int)block
+                                                    : (unsigned int)std::min<int64_t>(n_traced, UINT32_MAX));
     } else if (p->tail_rays > 0) {
         tail = (unsigned int)p->tail_rays;
     } else if (p->tail_rays == 0) {
@@ -1707,24 +1465,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
         a.debug_cost = p->debug_cost;
         a.replay = p->replay_hist;
         const int n_launch = (uint64_t)tail >= (uint64_t)n_traced ? 1 : B;
-        TravArgs ta{};
-        const bool use_split = split && n_launch > 1;
-        if (use_split) {
-            a.hit = hit_buf;
-            ta.rooms = d_rooms;
-            ta.room_of_src = d_room_of_src;
-            ta.hit = hit_buf;
-            ta.live = a.live;
-            ta.fetch = counters + (2 * B + 4);
-            ta.status = a.status;
-            ta.per_src = per_src;
-            ta.n_traced = n_traced;
-            ta.tail_threshold = tail;
-            ta.step_cap = a_step_cap;
-            ta.fetch_min = fetch_min;
-            ta.debug_cost = p->debug_cost;
-        }
-        RR_TRY(run_bounces(a, q, n_launch, block, grid, use_split ? &ta : nullptr, tgrid, s, ws));
+        RR_TRY(run_bounces(a, q, n_launch, block, grid, s, ws));
         RR_CUDA(cudaGetLastError());
         RR_CUDA(cudaEventRecord(ev.e[2], s));
         RR_CUDA(cudaMemcpyAsync(h_cnt.data(), counters, sizeof(unsigned int) * n_counters, cudaMemcpyDeviceToHost, s));
@@ -1879,7 +1620,6 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     v.hash_collisions = (int64_t)collisions;
     v.block_size = block;
     v.tail_rays = (int64_t)tail;
-    v.split_traversal = split && !((uint64_t)tail >= (uint64_t)n_traced);
     cudaEventElapsedTime(&v.ms_rays, ev.e[0], ev.e[1]);
     v.ms_bounces = ms_bounce;
     if (nr > 0) cudaEventElapsedTime(&v.ms_image_sources, ev.e[2], ev.e[3]);

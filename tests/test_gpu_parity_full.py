@@ -22,7 +22,8 @@ pytestmark = pytest.mark.gpu
 
 from paper_1811_05784_gb300 import rt  # noqa: E402
 from test_gpu_trace import (EPS_FREE, TOL_E, TOL_POS, TOL_RIR, TOL_T, _check_free_running,  # noqa: E402
-                            _check_compensated_lengths, _check_lengths, _check_lockstep, _gpu_as_oracle_trace, _moved_listeners, _performed)
+                            _check_compensated_lengths, _check_lengths, _check_lockstep, _gpu_as_oracle_trace,
+                            _moved_listeners, _performed)
 
 #: crossings whose FP64 margin (r - distance) / r lies within this band of
 #: the sphere are decided by rounding (float32 vs FP64 trajectories)
@@ -120,10 +121,8 @@ def test_theatre_end_to_end_against_the_free_running_oracle():
     ds_t = torch.empty((B, N, 6), dtype=torch.float32, device="cuda")
     dt_t = torch.empty((B, N), dtype=torch.float32, device="cuda")
     tree = rt.rt_build_tree(sc.vertices, sc.tris, sc.material_id, sc.surface_id)
-    # wavefront bounces in the split kernels down to 16,384 live rays, then tail mode
-    isrc = rt.rt_trace(tree, debug_state=ds_t, debug_t=dt_t, tail_rays=16384, split_traversal=1,
-                       **rt.scene_args(sc))
-    assert isrc.split_traversal == 1
+    # wavefront bounces down to 16,384 live rays, then tail mode
+    isrc = rt.rt_trace(tree, debug_state=ds_t, debug_t=dt_t, tail_rays=16384, **rt.scene_args(sc))
     dur = 2.0
     H = rt.rt_rir(isrc, sc.fs, duration=dur).download().astype(np.float64)
     hist = isrc.hist.cpu().numpy()

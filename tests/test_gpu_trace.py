@@ -458,45 +458,6 @@ def test_tail_mode_matches_per_bounce_launches(tail):
     assert torch.equal(a.energy, b.energy) and torch.equal(a.count, b.count)
 
 
-@pytest.mark.parametrize("fetch_min,tail", [(1, -1), (8, 16384), (32, -1)])
-def test_split_traversal_matches_the_fused_kernel(fetch_min, tail):
-    """Wavefront bounces whose hits come from the separate traversal kernel
-    (lanes refilled as soon as their query is done) give every ray the
-    result of the fused kernel, in the library's own graph too."""
-    sc = scenes.theatre(n_rays=200_000, n_bounces=30)
-    tree = _tree(sc)
-    a = rt.rt_trace(tree, tail_rays=-1, **rt.scene_args(sc))
-    stream = torch.cuda.Stream()
-    ws = rt.Workspace()
-    for k in range(2):
-        b = rt.rt_trace(tree, tail_rays=tail, split_traversal=1, fetch_min=fetch_min, stream=stream, workspace=ws,
-                        **rt.scene_args(sc))
-        torch.cuda.synchronize()
-        assert b.split_traversal == 1
-        assert torch.equal(a.hist, b.hist)
-        assert torch.equal(a.ray_energy, b.ray_energy) and torch.equal(a.ray_length, b.ray_length)
-        assert a.queries == b.queries and a.n == b.n and a.n_records == b.n_records
-        assert torch.equal(a.energy, b.energy) and torch.equal(a.count, b.count)
-    assert ws.graph_launches == 2
-
-
-def test_split_traversal_lockstep_against_the_oracle():
-    """The split kernels' hits and distances in lockstep with the FP64
-    oracle on every query of the L-room (h = 0.5 m), and their cost counts."""
-    sc = scenes.lroom(h=0.5, n_rays=30_000, n_bounces=20)
-    B, N = sc.n_bounces, sc.n_rays
-    ds_t = torch.empty((B, N, 6), dtype=torch.float32, device="cuda")
-    dt_t = torch.empty((B, N), dtype=torch.float32, device="cuda")
-    cost = torch.zeros((B, N, 2), dtype=torch.int32, device="cuda")
-    tree, isrc = _trace(sc, debug_t=dt_t, debug_state=ds_t, debug_cost=cost, tail_rays=1000, split_traversal=1)
-    assert isrc.split_traversal == 1
-    hist = isrc.hist.cpu().numpy()
-    osc = oracle.OracleScene(sc, tree=True)
-    _check_lockstep(sc, osc, ds_t.cpu().numpy(), dt_t.cpu().numpy(), hist)
-    c = cost.cpu().numpy()
-    assert (c[..., 0][_performed(hist)] >= 1).all() and (c[..., 0][~_performed(hist)] == 0).all()
-
-
 def test_shards_add_up():
     sc = scenes.shoebox(n_rays=30_000, n_bounces=20)
     tree = _tree(sc)
