@@ -33,6 +33,7 @@
 #ifndef ROOMRAYS_H
 #define ROOMRAYS_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -333,6 +334,129 @@ rt_status rt_mlp_set_step(rt_mlp* net, int64_t step);
  * n_bins > 0, dt > 0, t0 >= 0 are checked (RT_ERR_INVALID_ARG). */
 rt_status rt_tail_prior(const float* rates, const float* air, const float* level, int32_t n, int32_t n_nodes,
                         float t0, float dt, int32_t n_bins, float* out, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Surrogate-tail mode (no counterpart in the paper: the learned late
+ * reverberation of a room, with the method as fallback and judge).  A room is
+ * traced twice with few rays -- 0-50 ms in 1 ms bins ("early") and a 2 s tail
+ * probe in 10 ms bins -- and an ensemble of rt_mlp networks predicts its
+ * 8-band tail (50 ms - 2 s in 10 ms bins) from those traces, the room's
+ * descriptors and the specular tail prior (rt_tail_prior).  A gate sends the
+ * room to full tracing when its descriptors leave the training range or the
+ * prediction disagrees with its traces.  Every room of these calls is an
+ * rt_room with one source and one receiver (receiver 0 listens to source 0);
+ * volume[k] is room k's volume in m^3 (given, not derived: the mesh may be open
+ * or inconsistently oriented).  All arrays are device float, row-major, owned
+ * by the caller unless stated:
+ *   desc  [n][RT_SUR_N_DESC]   log10 V, log10 S, area-weighted mean alpha [8],
+ *         log10 (share of S whose normal is closest to x, y, z + 1e-6) [3],
+ *         log10 (c A_k a_kf / (2 V) + 1e-6) [3][8] (A_k the area of axis group
+ *         k, a_kf its area-weighted -ln(1 - alpha_f)), c beta [8], log10 r,
+ *         log10 (V / bounding-box volume)
+ *   early [n][8][RT_SUR_N_EARLY]  energy per 1 ms bin, 0-50 ms
+ *   probe [n][8][RT_SUR_N_TAIL]   energy per 10 ms bin, 50 ms - 2 s, of the probe
+ *   *_db  [n][8][RT_SUR_N_TAIL]   tail decay curve: 10 log10 (energy arriving
+ *         from each 10 ms bin start to 2 s + 1e-30)
+ *   X     [n][RT_SUR_N_FEAT]      network features: desc, 10 log10 (early +
+ *         1e-10), and the probe's minus the prior's decay at 63 bins per band
+ *         (each curve as its first value, then its decay relative to it
+ *         clamped at -50 dB)
+ *   env   [n][8][RT_SUR_N_ENV]    energy per 10 ms bin, 0-2 s
+ * ------------------------------------------------------------------------- */
+#define RT_SUR_N_DESC 47
+#define RT_SUR_N_EARLY 50
+#define RT_SUR_N_TAIL 195
+#define RT_SUR_N_ENV 200
+#define RT_SUR_N_FEAT 951
+
+typedef struct rt_surrogate rt_surrogate;
+
+typedef struct {
+    int32_t early_rays;       /* rays of the 0-50 ms trace (0 = 65,536) */
+    int32_t probe_rays;       /* rays of the 2 s tail probe (0 = 16,384) */
+    int32_t full_rays;        /* rays of a full 2 s trace: fallback and reference (0 = 1,000,000) */
+    int32_t rooms_per_launch; /* rooms traced together in one batched trace (0 = 16) */
+    const float* air_beta;    /* [8] host, 1/m energy (eq. 19); NULL = none */
+    double c;                 /* sound speed, 0 = 343.2 m/s */
+    void* stream;
+    rt_workspace* workspace;  /* NULL or a workspace for the batched traces */
+} rt_surrogate_trace_params;
+
+/* What the surrogate reads of n rooms: descriptors, the early trace, the
+ * probe, the prior's decay curve, the base curve the networks correct (the
+ * probe's level and decay over the first 200 ms of the tail, then the prior's
+ * decay joined without a step) and the features.  Any output may be NULL.
+ * Errors: RT_ERR_INVALID_ARG (n < 1, a room without exactly one receiver, a
+ * volume <= 0), and those of rt_trace_batch. */
+rt_status rt_surrogate_inputs(const rt_room* rooms, const double* volume, int32_t n,
+                              const rt_surrogate_trace_params* p, float* desc, float* early, float* probe,
+                              float* prior_db, float* base_db, float* X);
+/* Full traces of n rooms (p->full_rays rays, 2 s of path, 10 ms bins): the
+ * envelope env and its tail decay curve tail_db (either may be NULL). */
+rt_status rt_surrogate_reference(const rt_room* rooms, int32_t n, const rt_surrogate_trace_params* p, float* env,
+                                 float* tail_db);
+
+typedef struct {
+    int32_t n_nets;           /* ensemble members (0 = 4) */
+    int32_t steps;            /* AdamW steps per member (0 = 6000), cosine learning-rate schedule */
+    int32_t batch;            /* rooms per step (0 = 1024) */
+    float lr;                 /* peak learning rate (0 = 1e-3) */
+    float weight_decay;       /* decoupled weight decay (< 0: none; 0 = 1e-4) */
+    float input_noise;        /* Gaussian noise on the normalised features, in standard deviations (< 0: none; 0 = 0.1) */
+    float val_frac;           /* share of the rooms held out for validation (0 = 0.05) */
+    int32_t log_every;        /* validation every this many steps; each member keeps its best weights (0 = 250) */
+    uint64_t seed;
+    void* stream;
+} rt_surrogate_train_params;
+
+/* Train the networks on n rooms: features X, target tail decay curves
+ * tail_db (from rt_surrogate_reference), desc, base_db and prior_db (from
+ * rt_surrogate_inputs).  The networks learn the difference between the
+ * target and the base curve in the target form, normalised per column
+ * (output columns scaled so that the level at 50 ms weighs 9 and the first
+ * 300 ms 4 in the squared error).  The training range is the descriptors'
+ * span over the training rooms; the gate's tolerances are the 99th
+ * percentiles (at least 3 dB) of the join and probe gaps (rt_surrogate_gate)
+ * on up to 4096 training rooms.  Synchronises; n >= 64. */
+rt_status rt_surrogate_train(const float* X, const float* tail_db, const float* desc, const float* base_db,
+                             const float* prior_db, int32_t n, const rt_surrogate_train_params* p,
+                             rt_surrogate** out);
+void rt_surrogate_free(rt_surrogate* model);
+/* Ensemble size, gate tolerances (dB) and validation history
+ * (n_history x (member, step, loss), copied when history is not NULL). */
+rt_status rt_surrogate_info(const rt_surrogate* model, int32_t* n_nets, float* join_db, float* probe_db,
+                            int32_t* n_history, float* history);
+/* Serialise a model into host memory: with buf NULL only *bytes is set. */
+rt_status rt_surrogate_save(const rt_surrogate* model, void* buf, size_t cap, size_t* bytes);
+rt_status rt_surrogate_load(const void* buf, size_t bytes, void* stream, rt_surrogate** out);
+
+/* Predicted tail decay curves pred_db of n rooms from their features and
+ * base curves (ensemble mean in the target form, plus the base curve). */
+rt_status rt_surrogate_predict(const rt_surrogate* model, const float* X, const float* base_db, int32_t n,
+                               float* pred_db, void* stream);
+/* Gate of n rooms: pass (host [n]) = descriptors within the training range
+ * widened by 2 % of its span, join gap <= join_db and probe gap <= probe_db.
+ * Join gap: the largest over the bands with traced energy in 40-50 ms of
+ * |predicted 50-60 ms energy - traced 40-50 ms energy| in dB (+inf when no
+ * band has any); probe gap: the largest over bands of the RMS difference (dB)
+ * between the predicted and the probe's decay, both relative to the prior, at
+ * the features' probe bins.  gaps (host [n][2], nullable) receives both.
+ * Synchronises. */
+rt_status rt_surrogate_gate(const rt_surrogate* model, const float* desc, const float* X, const float* pred_db,
+                            const float* prior_db, int32_t n, int32_t* pass, float* gaps, void* stream);
+/* Envelope env of n rooms: the early trace summed into 10 ms bins, then the
+ * tail: per-bin energies (tail_is_db = 0) or a decay curve turned into
+ * per-bin energies (made non-increasing first). */
+rt_status rt_surrogate_envelope(const float* early, const float* tail, int32_t tail_is_db, int32_t n, float* env,
+                                void* stream);
+
+/* The surrogate-tail response of n rooms: rt_surrogate_inputs, prediction,
+ * gate, and a full trace (p->full_rays) for every room that fails the gate.
+ * *out: [n][8][RT_SUR_N_ENV] energies at fs = 100 Hz (rt_response_get; its
+ * n_rcv is n); used_fallback (host [n], nullable): 1 where the room was traced
+ * in full.  Synchronises. */
+rt_status rt_rir_surrogate(const rt_room* rooms, const double* volume, int32_t n, const rt_surrogate* model,
+                           const rt_surrogate_trace_params* p, rt_response** out, int32_t* used_fallback);
 
 /* ---------------------------------------------------------------------------
  * What the impulse responses feed (Sec. 1.4 and the perceptive factors of

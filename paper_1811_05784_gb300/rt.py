@@ -34,7 +34,10 @@ EXPORTED = ["rt_build_tree", "rt_build_tree_median", "rt_tree_free", "rt_tree_in
             "rt_last_error", "rt_api_version", "rt_launch_count", "rt_measure_l2_bandwidth", "rt_set_allocator",
             "rt_mlp_create", "rt_mlp_free", "rt_mlp_info", "rt_mlp_forward", "rt_mlp_gradients", "rt_mlp_train_step",
             "rt_mlp_copy", "rt_mlp_set_weight_decay", "rt_mlp_get_step", "rt_mlp_set_step", "rt_tail_prior",
-            "rt_room_parameters", "rt_pressure_rir"]
+            "rt_room_parameters", "rt_pressure_rir",
+            "rt_surrogate_inputs", "rt_surrogate_reference", "rt_surrogate_train", "rt_surrogate_free",
+            "rt_surrogate_info", "rt_surrogate_save", "rt_surrogate_load", "rt_surrogate_predict",
+            "rt_surrogate_gate", "rt_surrogate_envelope", "rt_rir_surrogate"]
 
 
 class RtError(RuntimeError):
@@ -115,6 +118,18 @@ class rt_response_view(C.Structure):
     _fields_ = [("n_rcv", C.c_int32), ("n_bins", C.c_int64), ("fs", C.c_double), ("data", P)]
 
 
+class rt_surrogate_trace_params(C.Structure):
+    _fields_ = [("early_rays", C.c_int32), ("probe_rays", C.c_int32), ("full_rays", C.c_int32),
+                ("rooms_per_launch", C.c_int32), ("air_beta", P), ("c", C.c_double), ("stream", P),
+                ("workspace", P)]
+
+
+class rt_surrogate_train_params(C.Structure):
+    _fields_ = [("n_nets", C.c_int32), ("steps", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float),
+                ("weight_decay", C.c_float), ("input_noise", C.c_float), ("val_frac", C.c_float),
+                ("log_every", C.c_int32), ("seed", C.c_uint64), ("stream", P)]
+
+
 ALLOC_FN = C.CFUNCTYPE(P, C.c_size_t, P, P)
 FREE_FN = C.CFUNCTYPE(None, P, P, P)
 
@@ -193,6 +208,23 @@ def lib():
             L.rt_pressure_rir.argtypes = [P, C.c_double, C.c_int64, C.c_int32, P, P]
             L.rt_tail_prior.restype = st
             L.rt_tail_prior.argtypes = [P, P, P, C.c_int32, C.c_int32, C.c_float, C.c_float, C.c_int32, P, P]
+            for name, args in (
+                    ("rt_surrogate_inputs", [P, P, C.c_int32, C.POINTER(rt_surrogate_trace_params), P, P, P, P, P, P]),
+                    ("rt_surrogate_reference", [P, C.c_int32, C.POINTER(rt_surrogate_trace_params), P, P]),
+                    ("rt_surrogate_train", [P, P, P, P, P, C.c_int32, C.POINTER(rt_surrogate_train_params),
+                                            C.POINTER(P)]),
+                    ("rt_surrogate_info", [P, C.POINTER(C.c_int32), C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                           C.POINTER(C.c_int32), P]),
+                    ("rt_surrogate_save", [P, P, C.c_size_t, C.POINTER(C.c_size_t)]),
+                    ("rt_surrogate_load", [P, C.c_size_t, P, C.POINTER(P)]),
+                    ("rt_surrogate_predict", [P, P, P, C.c_int32, P, P]),
+                    ("rt_surrogate_gate", [P, P, P, P, P, C.c_int32, P, P, P]),
+                    ("rt_surrogate_envelope", [P, P, C.c_int32, C.c_int32, P, P]),
+                    ("rt_rir_surrogate", [P, P, C.c_int32, P, C.POINTER(rt_surrogate_trace_params), C.POINTER(P),
+                                          P])):
+                getattr(L, name).restype = st
+                getattr(L, name).argtypes = args
+            L.rt_surrogate_free.argtypes = [P]
             L.rt_set_allocator.restype = st
             L.rt_set_allocator.argtypes = [ALLOC_FN, FREE_FN, P]
             _lib = L
@@ -501,13 +533,10 @@ class Workspace:
         self.free()
 
 
-def rt_trace_batch(rooms, n_rays, n_bounces, ray_begin=0, ray_count=0, max_distance=0.0, air_beta=None, c=343.2,
-                   block_size=0, max_node_visits=0, tail_rays=0, stream=None, workspace=None,
-                   replay=None, debug_t=None, debug_state=None, debug_cost=None) -> ImageSources:
-    """Trace many rooms in one persistent launch.  `rooms` is a list of dicts
-    with keys tree, sources, rcv_center, rcv_radius, rcv_source,
-    band_absorption (and optionally src_axis, src_pattern).  Receivers are
-    numbered room after room.  replay and the debug outputs: see rt_trace."""
+def _rooms(rooms):
+    """rt_room array over host copies of a list of room dicts (keys tree,
+    sources, rcv_center, rcv_radius, rcv_source, band_absorption, optionally
+    src_axis, src_pattern); returns (array, kept copies, receiver count)."""
     keep, arr = [], (rt_room * len(rooms))()
     n_rcv = 0
     for k, r in enumerate(rooms):
@@ -519,6 +548,17 @@ def rt_trace_batch(rooms, n_rays, n_bounces, ray_begin=0, ray_count=0, max_dista
         keep += keep_src + [rc, rr, rs, al]
         arr[k] = rt_room(r["tree"]._h, S, rt_receivers(prc, prr, prs, len(rc)), pal, len(al))
         n_rcv += len(rc)
+    return arr, keep, n_rcv
+
+
+def rt_trace_batch(rooms, n_rays, n_bounces, ray_begin=0, ray_count=0, max_distance=0.0, air_beta=None, c=343.2,
+                   block_size=0, max_node_visits=0, tail_rays=0, stream=None, workspace=None,
+                   replay=None, debug_t=None, debug_state=None, debug_cost=None) -> ImageSources:
+    """Trace many rooms in one persistent launch.  `rooms` is a list of dicts
+    with keys tree, sources, rcv_center, rcv_radius, rcv_source,
+    band_absorption (and optionally src_axis, src_pattern).  Receivers are
+    numbered room after room.  replay and the debug outputs: see rt_trace."""
+    arr, keep, n_rcv = _rooms(rooms)
     if air_beta is not None:
         be, pbe = _host(np.asarray(air_beta, np.float32).reshape(N_BANDS), np.float32)
     else:
@@ -659,3 +699,174 @@ class MLP:
 
     def __del__(self):
         self.free()
+
+
+# ----------------------------------------------------------------------------
+# surrogate-tail mode (see roomrays.h): every room one source, one receiver
+# ----------------------------------------------------------------------------
+SUR_N_DESC, SUR_N_EARLY, SUR_N_TAIL, SUR_N_ENV, SUR_N_FEAT = 47, 50, 195, 200, 951
+
+
+def _sur_params(early_rays=0, probe_rays=0, full_rays=0, rooms_per_launch=0, air_beta=None, c=0.0, stream=None,
+                workspace=None):
+    be, pbe = (None, None) if air_beta is None else _host(np.asarray(air_beta, np.float32).reshape(N_BANDS),
+                                                            np.float32)
+    prm = rt_surrogate_trace_params(int(early_rays), int(probe_rays), int(full_rays), int(rooms_per_launch), pbe,
+                                    float(c), _stream_ptr(stream), workspace._h if workspace is not None else None)
+    return prm, be
+
+
+def _dev(shape):
+    import torch
+    return torch.empty(shape, dtype=torch.float32, device="cuda")
+
+
+def _ptr(t):
+    return P(t.data_ptr()) if t is not None else None
+
+
+def _f32(t, shape, name):
+    if not (_is_cuda_tensor(t) and str(t.dtype) == "torch.float32" and t.is_contiguous() and tuple(t.shape) == shape):
+        raise ValueError(f"{name}: a contiguous CUDA float32 tensor of shape {shape}")
+    return t
+
+
+def rt_surrogate_inputs(rooms, volume, **kw):
+    """desc, early, probe, prior_db, base_db and X (CUDA tensors) of one-
+    receiver rooms; kw: early_rays, probe_rays, rooms_per_launch, air_beta, c,
+    stream, workspace."""
+    n = len(rooms)
+    arr, keep, _ = _rooms(rooms)
+    vol, pvol = _host(np.asarray(volume, np.float64).reshape(-1), np.float64)
+    if len(vol) != n:
+        raise ValueError("rt_surrogate_inputs: one volume per room")
+    prm, kb = _sur_params(**kw)
+    out = {"desc": _dev((n, SUR_N_DESC)), "early": _dev((n, N_BANDS, SUR_N_EARLY)),
+           "probe": _dev((n, N_BANDS, SUR_N_TAIL)), "prior_db": _dev((n, N_BANDS, SUR_N_TAIL)),
+           "base_db": _dev((n, N_BANDS, SUR_N_TAIL)), "X": _dev((n, SUR_N_FEAT))}
+    _check(lib().rt_surrogate_inputs(arr, pvol, n, C.byref(prm), *(_ptr(out[k]) for k in
+                                     ("desc", "early", "probe", "prior_db", "base_db", "X"))))
+    return out
+
+
+def rt_surrogate_reference(rooms, **kw):
+    """Full traces of one-receiver rooms: (env [n][8][200], tail_db [n][8][195])
+    CUDA tensors; kw: full_rays, rooms_per_launch, air_beta, c, stream, workspace."""
+    n = len(rooms)
+    arr, keep, _ = _rooms(rooms)
+    prm, kb = _sur_params(**kw)
+    env, tdb = _dev((n, N_BANDS, SUR_N_ENV)), _dev((n, N_BANDS, SUR_N_TAIL))
+    _check(lib().rt_surrogate_reference(arr, n, C.byref(prm), _ptr(env), _ptr(tdb)))
+    return env, tdb
+
+
+class SurrogateModel:
+    """rt_surrogate handle: the trained tail networks, their normalisation,
+    training range and gate tolerances."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    def info(self):
+        nn, nh = C.c_int32(), C.c_int32()
+        j, pr = C.c_float(), C.c_float()
+        _check(lib().rt_surrogate_info(self._h, C.byref(nn), C.byref(j), C.byref(pr), C.byref(nh), None))
+        hist = np.zeros(3 * nh.value, np.float32)
+        _check(lib().rt_surrogate_info(self._h, None, None, None, None, P(hist.ctypes.data)))
+        return {"n_nets": nn.value, "join_db": j.value, "probe_db": pr.value, "history": hist.reshape(-1, 3)}
+
+    def to_bytes(self) -> bytes:
+        n = C.c_size_t()
+        _check(lib().rt_surrogate_save(self._h, None, 0, C.byref(n)))
+        buf = (C.c_ubyte * n.value)()
+        _check(lib().rt_surrogate_save(self._h, buf, n.value, C.byref(n)))
+        return bytes(buf)
+
+    def save(self, path):
+        with open(path, "wb") as f:
+            f.write(self.to_bytes())
+
+    @staticmethod
+    def from_bytes(data: bytes, stream=None):
+        buf = (C.c_ubyte * len(data)).from_buffer_copy(data)
+        h = P()
+        _check(lib().rt_surrogate_load(buf, len(data), _stream_ptr(stream), C.byref(h)))
+        return SurrogateModel(h)
+
+    @staticmethod
+    def load(path, stream=None):
+        with open(path, "rb") as f:
+            return SurrogateModel.from_bytes(f.read(), stream)
+
+    def predict(self, X, base_db, stream=None):
+        n = int(X.shape[0])
+        _f32(X, (n, SUR_N_FEAT), "X")
+        _f32(base_db, (n, N_BANDS, SUR_N_TAIL), "base_db")
+        out = _dev((n, N_BANDS, SUR_N_TAIL))
+        _check(lib().rt_surrogate_predict(self._h, _ptr(X), _ptr(base_db), n, _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def gate(self, desc, X, pred_db, prior_db, stream=None):
+        """(pass [n] bool, gaps [n][2] = join, probe in dB) as numpy arrays."""
+        n = int(X.shape[0])
+        _f32(desc, (n, SUR_N_DESC), "desc")
+        _f32(X, (n, SUR_N_FEAT), "X")
+        for t, name in ((pred_db, "pred_db"), (prior_db, "prior_db")):
+            _f32(t, (n, N_BANDS, SUR_N_TAIL), name)
+        ok = np.zeros(n, np.int32)
+        gaps = np.zeros((n, 2), np.float32)
+        _check(lib().rt_surrogate_gate(self._h, _ptr(desc), _ptr(X), _ptr(pred_db), _ptr(prior_db), n,
+                                       P(ok.ctypes.data), P(gaps.ctypes.data), _stream_ptr(stream)))
+        return ok.astype(bool), gaps
+
+    def free(self):
+        if getattr(self, "_h", None):
+            lib().rt_surrogate_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.free()
+
+
+def rt_surrogate_train(X, tail_db, desc, base_db, prior_db, n_nets=0, steps=0, batch=0, lr=0.0, weight_decay=0.0,
+                       input_noise=0.0, val_frac=0.0, log_every=0, seed=0, stream=None) -> SurrogateModel:
+    n = int(X.shape[0])
+    _f32(X, (n, SUR_N_FEAT), "X")
+    _f32(desc, (n, SUR_N_DESC), "desc")
+    for t, name in ((tail_db, "tail_db"), (base_db, "base_db"), (prior_db, "prior_db")):
+        _f32(t, (n, N_BANDS, SUR_N_TAIL), name)
+    prm = rt_surrogate_train_params(int(n_nets), int(steps), int(batch), float(lr), float(weight_decay),
+                                    float(input_noise), float(val_frac), int(log_every), int(seed),
+                                    _stream_ptr(stream))
+    h = P()
+    _check(lib().rt_surrogate_train(_ptr(X), _ptr(tail_db), _ptr(desc), _ptr(base_db), _ptr(prior_db), n,
+                                    C.byref(prm), C.byref(h)))
+    return SurrogateModel(h)
+
+
+def rt_surrogate_envelope(early, tail, tail_is_db, stream=None):
+    """Envelopes [n][8][200] (CUDA): early [n][8][50] + a tail [n][8][195]
+    given as per-bin energies or as a decay curve in dB."""
+    n = int(early.shape[0])
+    _f32(early, (n, N_BANDS, SUR_N_EARLY), "early")
+    _f32(tail, (n, N_BANDS, SUR_N_TAIL), "tail")
+    env = _dev((n, N_BANDS, SUR_N_ENV))
+    _check(lib().rt_surrogate_envelope(_ptr(early), _ptr(tail), int(bool(tail_is_db)), n, _ptr(env),
+                                       _stream_ptr(stream)))
+    return env
+
+
+def rt_rir_surrogate(rooms, volume, model: SurrogateModel, **kw):
+    """Surrogate-tail responses of one-receiver rooms: (Response [n][8][200]
+    at 100 Hz, used_fallback numpy bool [n]); kw: early_rays, probe_rays,
+    full_rays, rooms_per_launch, air_beta, c, stream, workspace."""
+    n = len(rooms)
+    arr, keep, _ = _rooms(rooms)
+    vol, pvol = _host(np.asarray(volume, np.float64).reshape(-1), np.float64)
+    if len(vol) != n:
+        raise ValueError("rt_rir_surrogate: one volume per room")
+    prm, kb = _sur_params(**kw)
+    fb = np.zeros(n, np.int32)
+    h = P()
+    _check(lib().rt_rir_surrogate(arr, pvol, n, model._h, C.byref(prm), C.byref(h), P(fb.ctypes.data)))
+    return Response(h), fb.astype(bool)

@@ -2,21 +2,22 @@
 
     python -m paper_1811_05784_gb300.train_surrogate --out DIR [--train-rooms 20000] [--test-rooms 500]
 
-1. data: seeded rooms (scenes.surrogate_room), each traced in batched
-   launches: a short trace (64k rays, 50 ms, 1 ms bins) and a tail probe
-   (16k rays, 2 s, 10 ms bins) for the network input, and a full trace
-   (--target-rays, 2 s, 10 ms bins) for the target;
-2. training on the GPU (rt_mlp: BF16 tensor-core forward / backward, AdamW),
-   the network predicting the correction to the specular tail prior;
-3. judging on held-out rooms against full 1M-ray traces: per-band EDT and T30
-   of the surrogate response (traced 0-50 ms + predicted tail) versus the
-   full trace; the same for the method without the network: the early trace
-   joined to the probe's tail (same cost), the prior alone, Eyring's
-   exponential and the early decay continued; rooms failing the gate fall
-   back to the full trace (its cost is charged);
+1. data: seeded rooms (scenes.surrogate_room), traced in batched launches by
+   rt_surrogate_inputs (64k-ray 0-50 ms trace, 16k-ray 2 s tail probe,
+   descriptors, prior, features, base curve) and rt_surrogate_reference
+   (--target-rays full traces to 2 s: the targets);
+2. training: rt_surrogate_train (BF16 tensor-core networks, AdamW);
+3. judging on held-out rooms against full 1M-ray traces (rt_surrogate_reference):
+   per-band EDT and T30 (rt_room_parameters on 10 ms envelopes) of the
+   surrogate response (rt_rir_surrogate: traced 0-50 ms + predicted tail,
+   full tracing where the gate fails; that cost is charged), and of the
+   method without the network: the early trace joined to the probe's own
+   tail (same rays), to the prior alone, and to Eyring's exponential;
+   a defined reference value with an undefined estimate counts as a 100 %
+   error (and is counted);
 4. RIRs/s of the surrogate pipeline versus plain full tracing, same GPU.
-Writes DIR/surrogate_report.json and the checkpoint (--model-out, default
-DIR/surrogate_model.npz); the traced data set goes to --data-dir (default DIR).
+Writes DIR/surrogate_report.json and the model (--model-out, default
+DIR/surrogate_tail.rtsur, rt_surrogate_save format).
 """
 from __future__ import annotations
 
@@ -38,6 +39,7 @@ from . import rt  # noqa: E402
 from . import surrogate as S  # noqa: E402
 
 TEST_SEED0 = 1_000_000
+KEYS = ("desc", "early", "probe", "prior_db", "base_db", "X")
 
 
 def make_rooms(seeds):
@@ -45,31 +47,45 @@ def make_rooms(seeds):
 
 
 def dataset(seeds, early_rays, probe_rays, target_rays, per_batch, stream, ws, log=print):
-    """descriptors [n][47], early energies [n][8][50], probe and target tail
-    energies [n][8][195]."""
-    desc, E, Pr, T = [], [], [], []
-    queries, t0 = 0, time.perf_counter()
+    """Host arrays of every input of the rooms plus their target tail curves."""
+    import torch
+    parts = {k: [] for k in KEYS + ("tail_db",)}
+    t0 = time.perf_counter()
     for k in range(0, len(seeds), per_batch):
         rooms = make_rooms(seeds[k:k + per_batch])
-        sh = S.short_traces(rooms, early_rays, probe_rays, stream=stream, workspace=ws)
-        f, q = S.full_histograms(rooms, target_rays, stream=stream, workspace=ws, trees=sh["trees"])
-        desc.append(sh["desc"])
-        E.append(sh["early"])
-        Pr.append(sh["probe"])
-        T.append(S._np(f)[:, :, S.FIRST_TAIL:])
-        queries += sh["queries"] + q
-        if (k // per_batch) % 100 == 0:
-            log(f"  rooms {k + len(rooms)}/{len(seeds)}  {time.perf_counter() - t0:.1f} s  {queries:.3e} queries")
-    return (np.concatenate(desc), np.concatenate(E), np.concatenate(Pr), np.concatenate(T), queries,
-            time.perf_counter() - t0)
+        d = S.inputs(rooms, early_rays=early_rays, probe_rays=probe_rays, stream=stream, workspace=ws)
+        _, tail_db = S.reference(rooms, d["trees"], full_rays=target_rays, stream=stream, workspace=ws)
+        for key in KEYS:
+            parts[key].append(d[key].cpu().numpy())
+        parts["tail_db"].append(tail_db.cpu().numpy())
+        if (k // per_batch) % 50 == 0:
+            log(f"  rooms {k + len(rooms)}/{len(seeds)}  {time.perf_counter() - t0:.1f} s")
+    torch.cuda.synchronize()
+    return {k: np.concatenate(v) for k, v in parts.items()}, time.perf_counter() - t0
 
 
-def errors(env, ref):
-    """relative EDT / T30 errors per room and band (NaN where undefined)."""
+def eyring_tail(desc, early):
+    """Judging baseline, the method without the network in statistical form:
+    an exponential tail at Eyring's rate c S (-ln(1 - alpha_f)) / (4 V) per
+    band (+ air), joined to the traced 40-50 ms energy.  [n][8][195] per-bin energy."""
+    V, Sa = 10 ** desc[:, 0], 10 ** desc[:, 1]
+    a = np.clip(desc[:, 2:10], 1e-6, 0.999)
+    rate = S.C_SOUND * Sa[:, None] * (-np.log(1 - a)) / (4 * V[:, None]) + desc[:, 37:45]
+    e45 = early[:, :, 40:50].sum(-1)
+    t = (np.arange(5, 200) + 0.5) / S.TAIL_FS
+    return e45[:, :, None] * np.exp(-rate[:, :, None] * (t[None, None, :] - 0.045))
+
+
+def errors(est, ref):
+    """Relative EDT / T30 errors [n][8] of (EDT, T30) pairs; a defined
+    reference with an undefined estimate is a 100 % error; an undefined
+    reference leaves NaN (excluded, counted)."""
     out = {}
-    for name, fn in (("EDT", S.edt), ("T30", S.t30)):
-        a, b = fn(env), fn(ref)
-        out[name] = np.abs(a - b) / b
+    for k, name in enumerate(("EDT", "T30")):
+        a, b = est[k], ref[k]
+        e = np.abs(a - b) / b
+        e = np.where(np.isfinite(b) & ~np.isfinite(a), 1.0, e)
+        out[name] = e
     return out
 
 
@@ -77,10 +93,47 @@ def summary(err, mask=None):
     res = {}
     for name, e in err.items():
         e = e if mask is None else e[mask]
-        per_band = [float(np.nanmean(e[:, f])) for f in range(8)]
         res[name] = {"mean_rel_error": float(np.nanmean(e)), "median_rel_error": float(np.nanmedian(e)),
-                     "per_band_mean": per_band, "defined": int(np.isfinite(e).sum())}
+                     "per_band_mean": [float(np.nanmean(e[:, f])) for f in range(8)],
+                     "worst_band_mean": float(np.nanmax(np.nanmean(e, axis=0))),
+                     "estimate_undefined": int(np.sum(e == 1.0)), "reference_undefined": int(np.isnan(e).sum())}
     return res
+
+
+def judge(model, seeds, early_rays, probe_rays, ref_rays, per_batch, stream, ws, log=print):
+    """Held-out rooms: surrogate vs plain full tracing (errors, RIRs/s)."""
+    out = {k: [] for k in ("sur", "ref", "probe", "prior", "eyring", "fallback", "kind")}
+    t_sur = t_plain = 0.0
+    for k in range(0, len(seeds), per_batch):
+        rooms = make_rooms(seeds[k:k + per_batch])
+        (env, fb), dt_s = S.timed(lambda: S.respond(rooms, model, full_rays=ref_rays, early_rays=early_rays,
+                                                    probe_rays=probe_rays, stream=stream, workspace=ws))
+        (ref, _), dt_p = S.timed(lambda: S.reference(rooms, full_rays=ref_rays, stream=stream, workspace=ws))
+        t_sur += dt_s
+        t_plain += dt_p
+        d = S.inputs(rooms, early_rays=early_rays, probe_rays=probe_rays, stream=stream, workspace=ws)
+        out["sur"].append(S.decay_times(env, stream))
+        out["ref"].append(S.decay_times(ref, stream))
+        out["probe"].append(S.decay_times(rt.rt_surrogate_envelope(d["early"], d["probe"], False, stream), stream))
+        out["prior"].append(S.decay_times(rt.rt_surrogate_envelope(d["early"], d["prior_db"], True, stream), stream))
+        import torch
+        ey = torch.tensor(eyring_tail(d["desc"].cpu().numpy().astype(np.float64),
+                                      d["early"].cpu().numpy().astype(np.float64)), dtype=torch.float32,
+                          device="cuda").contiguous()
+        out["eyring"].append(S.decay_times(rt.rt_surrogate_envelope(d["early"], ey, False, stream), stream))
+        out["fallback"].append(fb)
+        out["kind"].append(np.array([r.meta["kind"] == "shoebox" for r in rooms]))
+    cat = lambda key: tuple(np.concatenate([x[i] for x in out[key]]) for i in range(2))
+    ref = cat("ref")
+    box = np.concatenate(out["kind"])
+    fb = np.concatenate(out["fallback"])
+    judged = {"rooms": int(len(box)), "fallback_rooms": int(fb.sum()), "rirs_per_s_surrogate": len(box) / t_sur,
+              "rirs_per_s_plain": len(box) / t_plain, "speedup": t_plain / t_sur}
+    for name in ("sur", "probe", "prior", "eyring"):
+        err = errors(cat(name), ref)
+        judged[name] = {"all": summary(err), "shoebox": summary(err, box), "lroom": summary(err, ~box)}
+    judged["sur_gated_rooms_only"] = summary(errors(cat("sur"), ref), ~fb)
+    return judged
 
 
 def main(argv=None):
@@ -88,18 +141,17 @@ def main(argv=None):
     ap.add_argument("--out", required=True)
     ap.add_argument("--train-rooms", type=int, default=20_000)
     ap.add_argument("--test-rooms", type=int, default=500)
-    ap.add_argument("--early-rays", type=int, default=65_536)
+    ap.add_argument("--early-rays", type=int, default=S.EARLY_RAYS)
     ap.add_argument("--probe-rays", type=int, default=S.PROBE_RAYS)
-    ap.add_argument("--target-rays", type=int, default=131_072)
+    ap.add_argument("--target-rays", type=int, default=262_144)
     ap.add_argument("--ref-rays", type=int, default=1_000_000)
-    ap.add_argument("--per-batch", type=int, default=16)
+    ap.add_argument("--per-batch", type=int, default=64)
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--batch", type=int, default=1024)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--nets", type=int, default=4, help="ensemble members")
-    ap.add_argument("--reuse-data", action="store_true")
-    ap.add_argument("--data-dir", default=None, help="where the traced data set is cached (default: --out)")
-    ap.add_argument("--model-out", default=None, help="checkpoint path (default: DIR/surrogate_model.npz)")
+    ap.add_argument("--data", default=None, help="cache of the traced data set (.npz; reused when present)")
+    ap.add_argument("--model-out", default=None, help="model path (default: DIR/surrogate_tail.rtsur)")
     a = ap.parse_args(argv)
     import torch
     os.makedirs(a.out, exist_ok=True)
@@ -107,97 +159,36 @@ def main(argv=None):
     ws = rt.Workspace()
     report = {"config": vars(a)}
     log = lambda m: print(m, flush=True)
-    os.makedirs(a.data_dir or a.out, exist_ok=True)
-    data_path = os.path.join(a.data_dir or a.out, "surrogate_data.npz")
     with torch.cuda.stream(stream):
-        if a.reuse_data and os.path.exists(data_path):
-            d = np.load(data_path)
-            desc, E, Pr, T = d["desc"], d["early"], d["probe"], d["tail"]
+        if a.data and os.path.exists(a.data):
+            host = dict(np.load(a.data))
         else:
             log(f"tracing {a.train_rooms} training rooms")
-            desc, E, Pr, T, q, dt = dataset(np.arange(a.train_rooms), a.early_rays, a.probe_rays, a.target_rays,
-                                            a.per_batch, stream, ws, log)
-            np.savez(data_path, desc=desc, early=E, probe=Pr, tail=T)
-            report["data"] = {"rooms": a.train_rooms, "queries": q, "seconds": dt}
-        prior = S.tail_prior_edc_db(desc, stream=stream)
-        base = S.base_db(Pr, prior)
-        X, Y = S.features(desc, E, Pr, prior), S.tail_edc_db(T)
+            host, dt = dataset(np.arange(a.train_rooms), a.early_rays, a.probe_rays, a.target_rays, a.per_batch,
+                               stream, ws, log)
+            report["data"] = {"rooms": a.train_rooms, "seconds": dt}
+            if a.data:
+                np.savez(a.data, **host)
+        dev = {k: torch.tensor(v, dtype=torch.float32, device="cuda").contiguous() for k, v in host.items()}
         log("training")
-        t0 = time.perf_counter()
-        sur = S.Surrogate.fit(X, Y, desc, base, prior, n_nets=a.nets, steps=a.steps, batch=a.batch, lr=a.lr,
-                              stream=stream)
-        torch.cuda.synchronize()
-        report["training"] = {"seconds": time.perf_counter() - t0, "validation_loss": sur.history,
-                              "join_db": sur.join_db, "probe_db": sur.probe_db}
-        sur.save(a.model_out or os.path.join(a.out, "surrogate_model.npz"))
-        # fit on training rooms (their 10 ms response rebuilt from the stored energies)
-        k = np.random.default_rng(2).choice(len(X), min(256, len(X)), replace=False)
-        ref_tr = np.concatenate([E[k].reshape(len(k), 8, S.FIRST_TAIL, -1).sum(-1), T[k]], axis=2)
-        env_tr = S.combine(E[k], S.edc_to_energy(sur.predict_db(X[k], base[k], stream=stream)))
-        report["training"]["fit_on_training_rooms"] = summary(errors(env_tr, ref_tr))
-        f = report["training"]["fit_on_training_rooms"]
-        log(f"  training rooms: T30 {f['T30']['mean_rel_error']:.4f} EDT {f['EDT']['mean_rel_error']:.4f} (mean)")
-
-        # -- held-out rooms -----------------------------------------------------
+        model, dt = S.timed(lambda: S.train(dev, n_nets=a.nets, steps=a.steps, batch=a.batch, lr=a.lr, stream=stream))
+        info = model.info()
+        report["training"] = {"seconds": dt, "join_db": info["join_db"], "probe_db": info["probe_db"],
+                              "validation_loss": info["history"].tolist()}
+        model.save(a.model_out or os.path.join(a.out, "surrogate_tail.rtsur"))
         log(f"judging on {a.test_rooms} held-out rooms")
-        seeds = np.arange(TEST_SEED0, TEST_SEED0 + a.test_rooms)
-        out = {k: [] for k in ("sur", "ref", "probe", "prior", "eyring", "extra", "gate", "outside", "kind")}
-        t_sur = t_plain = 0.0
-        n_fallback = 0
-        for k in range(0, len(seeds), a.per_batch):
-            rooms = make_rooms(seeds[k:k + a.per_batch])
-
-            def surrogate_pipeline():
-                sh = S.short_traces(rooms, a.early_rays, a.probe_rays, stream=stream, workspace=ws)
-                pred = sur.predict_db(sh["X"], sh["base"], stream=stream)
-                return sh, pred, sur.gate(sh["desc"], sh["X"], pred, sh["prior"])
-
-            (sh, pred, ok), dt_s = S.timed(surrogate_pipeline)
-
-            def plain_pipeline():
-                trees = [rt.rt_build_tree(r.vertices, r.tris, r.material_id, r.surface_id, stream=stream)
-                         for r in rooms]
-                return S.full_histograms(rooms, a.ref_rays, stream=stream, workspace=ws, trees=trees)
-
-            (f, _), dt_p = S.timed(plain_pipeline)
-            t_sur += dt_s
-            t_plain += dt_p
-            env = S.combine(sh["early"], S.edc_to_energy(pred))
-            ref = S._np(f)
-            bad = ~ok          # fallback: rooms failing the gate take the full trace (its cost is charged)
-            if bad.any():
-                env[bad] = ref[bad]
-                n_fallback += int(bad.sum())
-                t_sur += dt_p * bad.sum() / len(rooms)
-            e, Xb, d = sh["early"], sh["X"], sh["desc"]
-            out["sur"].append(env)
-            out["ref"].append(ref)
-            out["probe"].append(S.combine(e, sh["probe"]))
-            out["prior"].append(S.combine(e, S.edc_to_energy(sh["prior"])))
-            out["eyring"].append(S.combine(e, S.eyring_tail_energy(d, Xb)))
-            out["extra"].append(S.combine(e, 10 ** (S.extrapolated_tail_db(Xb) / 10.0)))
-            out["gate"].append(ok)
-            out["outside"].append(~sur.in_range(d))
-            out["kind"].append(np.array([r.meta["kind"] == "shoebox" for r in rooms]))
-        o = {k: np.concatenate(v) for k, v in out.items()}
-        ref, box = o["ref"], o["kind"]
-        judged = {"rooms": int(len(ref)), "fallback_rooms": n_fallback, "outside_training_range": int(o["outside"].sum()),
-                  "rirs_per_s_surrogate": len(ref) / t_sur, "rirs_per_s_plain": len(ref) / t_plain,
-                  "speedup": t_plain / t_sur}
-        for name in ("sur", "probe", "prior", "eyring", "extra"):
-            err = errors(o[name], ref)
-            judged[name] = {"all": summary(err), "shoebox": summary(err, box), "lroom": summary(err, ~box)}
-        judged["sur_gated_rooms_only"] = summary(errors(o["sur"], ref), o["gate"])
-        report["judged"] = judged
-    path = os.path.join(a.out, "surrogate_report.json")
-    with open(path, "w") as fh:
+        report["judged"] = judge(model, np.arange(TEST_SEED0, TEST_SEED0 + a.test_rooms), a.early_rays,
+                                 a.probe_rays, a.ref_rays, 16, stream, ws, log)
+    with open(os.path.join(a.out, "surrogate_report.json"), "w") as fh:
         json.dump(report, fh, indent=1)
     j = report["judged"]
     line = {"speedup": j["speedup"], "rirs_per_s_surrogate": j["rirs_per_s_surrogate"],
-            "rirs_per_s_plain": j["rirs_per_s_plain"], "fallback_rooms": j["fallback_rooms"]}
-    for name in ("sur", "probe", "prior", "eyring", "extra"):
+            "rirs_per_s_plain": j["rirs_per_s_plain"], "fallback_rooms": j["fallback_rooms"],
+            "join_db": info["join_db"], "probe_db": info["probe_db"]}
+    for name in ("sur", "probe", "prior", "eyring"):
         for m in ("T30", "EDT"):
             line[f"{m}_{name}"] = round(j[name]["all"][m]["mean_rel_error"], 4)
+            line[f"{m}_{name}_worst_band"] = round(j[name]["all"][m]["worst_band_mean"], 4)
     log(json.dumps(line))
     return report
 

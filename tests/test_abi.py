@@ -54,7 +54,7 @@ def test_oracle_and_cuda_path_share_no_code():
 
 
 STRUCTS = ("rt_mesh", "rt_sources", "rt_receivers", "rt_trace_params", "rt_room", "rt_is_view",
-           "rt_response_view")
+           "rt_response_view", "rt_surrogate_trace_params", "rt_surrogate_train_params")
 
 
 def test_binding_structs_match_the_header(tmp_path):

@@ -84,85 +84,3 @@ def test_gpu_training_reduces_loss():
     assert net.step == 300
     final = net.gradients(x[:1024], t[:1024])
     assert final < 0.3 * first, (first, final)
-
-
-def test_package_decay_metrics_on_exponentials():
-    from paper_1811_05784_gb300 import surrogate as S
-    fs = 100.0
-    n = np.arange(200)
-    T = np.array([0.4, 0.9, 1.7])
-    env = np.exp(-6 * np.log(10) * n[None, :] / (fs * T[:, None]))   # 60 dB per T seconds
-    assert np.allclose(S.edt(env, fs), T, rtol=2e-2)
-    got = S.t30(env, fs)
-    assert np.allclose(got[:2], T[:2], rtol=2e-2)
-    assert np.isnan(got[2]) or abs(got[2] / T[2] - 1) < 2e-2      # 2 s may not reach -35 dB
-
-
-def test_surrogate_feature_layout():
-    from paper_1811_05784_gb300 import surrogate as S
-    assert S.N_FEAT == S.N_DESC + 400 + 8 * len(S.PROBE_BINS) and S.N_IN >= S.N_FEAT and S.N_IN % 32 == 0
-    assert S.PROBE_BINS.max() < S.N_TAIL and np.all(np.diff(S.PROBE_BINS) > 0)
-    assert S.X_EARLY.start == S.N_DESC and S.X_PROBE.start == S.X_EARLY.stop and S.X_PROBE.stop == S.N_FEAT
-    assert len(S.BASIC_COLS) == 410 and S.BASIC_COLS[10] == S.N_DESC
-    assert S.N_OUT_RAW == 8 * 195 and S.N_OUT >= S.N_OUT_RAW and S.N_OUT % 32 == 0
-    import scenes
-    d = S.descriptors(scenes.surrogate_room(2))
-    assert d.shape == (S.N_DESC,) and 0.02 <= d[2:10].min() and d[2:10].max() <= 0.6
-
-
-def test_axis_descriptors_closed_form():
-    """In a 10 x 7 x 3 m box of uniform absorption 0.1 the walls normal to
-    axis k hold 2 V / L_k of area and decay a ray's energy at c a / L_k per
-    unit |d_k| (a = -ln 0.9); half their sum is Eyring's rate c S a / (4 V)."""
-    from paper_1811_05784_gb300 import surrogate as S
-    import scenes
-    sc = scenes.shoebox()
-    L = np.array([10.0, 7.0, 3.0])
-    V, Sa = L.prod(), 2 * (L[0] * L[1] + L[1] * L[2] + L[0] * L[2])
-    sc.meta["V"] = V
-    d = S.descriptors(sc)
-    a = -np.log(0.9)
-    assert np.isclose(10 ** d[0], V) and np.isclose(10 ** d[1], Sa)
-    assert np.allclose(10 ** d[S.D_AXIS_SHARE], 2 * V / L / Sa, rtol=1e-5)
-    rate = (10 ** d[S.D_AXIS_RATE]).reshape(3, 8)
-    assert np.allclose(rate, (S.C_SOUND * a / L)[:, None], rtol=1e-5)
-    assert np.allclose(rate.sum(0) / 2, S.C_SOUND * Sa * a / (4 * V), rtol=1e-5)
-    assert np.all(d[S.D_AIR] == 0)
-
-
-def test_tail_targets_round_trip():
-    from paper_1811_05784_gb300 import surrogate as S
-    g = np.random.default_rng(0)
-    rate = g.uniform(5, 200, (3, 8, 1))
-    t = (np.arange(S.N_TAIL) + 0.5) / S.TAIL_FS
-    energy = g.uniform(1e-4, 1e-2, (3, 8, 1)) * np.exp(-rate * t)
-    edc = S.tail_edc_db(energy)
-    y = S.edc_to_targets(edc)
-    back = S.targets_to_edc_db(y).reshape(3, 8, -1)
-    e3 = edc.reshape(3, 8, -1)
-    keep = e3 >= e3[:, :, :1] - S.REL_FLOOR_DB
-    assert np.allclose(back[keep], e3[keep], atol=1e-9)
-    assert np.all(back[~keep] >= e3[~keep])                       # clamped, never below the floor
-    assert np.allclose(back - back[:, :, :1], np.maximum(e3 - e3[:, :, :1], -S.REL_FLOOR_DB))
-
-
-def test_base_curve_follows_probe_then_prior():
-    from paper_1811_05784_gb300 import surrogate as S
-    g = np.random.default_rng(5)
-    n = 3
-    t = (np.arange(S.N_TAIL) + 0.5) / S.TAIL_FS
-    probe = g.uniform(1e-5, 1e-3, (n, 8, 1)) * np.exp(-g.uniform(5, 40, (n, 8, 1)) * t) * g.uniform(0.5, 1.5, (n, 8, S.N_TAIL))
-    prior_e = g.uniform(1e-5, 1e-3, (n, 8, 1)) * np.exp(-g.uniform(5, 40, (n, 8, 1)) * t)
-    prior = S.tail_edc_db(prior_e)
-    base = S.edc_to_targets(S.base_db(probe, prior)).reshape(n, 8, -1)
-    a = S.edc_to_targets(S.tail_edc_db(probe)).reshape(n, 8, -1)
-    b = S.edc_to_targets(prior).reshape(n, 8, -1)
-    k = S.BASE_PROBE_BINS
-    keep = a[:, :, :k] >= -S.REL_FLOOR_DB
-    assert np.allclose(base[:, :, :k][keep], a[:, :, :k][keep])            # level and first bins: the probe
-    step_base = np.diff(base[:, :, k - 1:], axis=2)
-    step_prior = np.diff(b[:, :, k - 1:], axis=2)
-    lo = -S.REL_FLOOR_DB + 1e-6                                           # off the clamp
-    free = (base[:, :, k:] > lo) & (base[:, :, k - 1:-1] > lo)
-    assert np.allclose(step_base[free], step_prior[free])                 # then the prior's decay, no step
-    assert base[:, :, 1:].min() >= -S.REL_FLOOR_DB - 1e-9
