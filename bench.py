@@ -80,7 +80,8 @@ def parse():
                          "in batched launches; tetra: the N = M scaling sweep of one iteration on the refined "
                          "tetrahedron; trees: the LBVH against the paper's median-split tree "
                          "(each its own line, one GPU)")
-    ap.add_argument("--batch-chunk", type=int, default=65_536, help="rays per pair per batched launch")
+    ap.add_argument("--batch-chunk", type=int, default=262_144,
+                    help="rays per pair per batched trace (default: all of them, one trace per step)")
     return ap.parse_args()
 
 
@@ -299,6 +300,7 @@ def l2_roofline(rt, torch, tree, sc, kw, chosen, bounce_ms, stream, dev, l2_peak
     cost = torch.zeros((B, n, 2), dtype=torch.int32, device=dev)
     fixed_tail = chosen["tail_rays"] if chosen["tail_rays"] > 0 else -1
     isrc = rt.rt_trace(tree, tail_rays=fixed_tail, block_size=chosen["block_size"], stream=stream,
+                       compaction_period=chosen["compaction_period"], stack_entries=chosen["stack_entries"],
                        debug_cost=cost, **kw)
     torch.cuda.synchronize()
     c = cost.double().sum((0, 1)).cpu().numpy()
@@ -347,14 +349,15 @@ def timed_trace_steps(rt, torch, sc, kw, stream, tail, warmup, steps, flush, dev
             prev = None
             for _ in range(40):
                 _, isrc_t, _ = step()
-                cur = (isrc_t.block_size, int(isrc_t.tail_rays))
+                cur = (isrc_t.block_size, int(isrc_t.tail_rays), isrc_t.compaction_period, isrc_t.stack_entries)
                 if cur == prev:
                     break
                 prev = cur
         for _ in range(max(warmup, 1)):
             _, isrc_w, _ = step()
         torch.cuda.synchronize()
-        chosen = {"block_size": isrc_w.block_size, "tail_rays": int(isrc_w.tail_rays)}
+        chosen = {"block_size": isrc_w.block_size, "tail_rays": int(isrc_w.tail_rays),
+                  "compaction_period": isrc_w.compaction_period, "stack_entries": isrc_w.stack_entries}
         torch.cuda.synchronize()
         launches0 = rt.rt_launch_count()
         ms, queries = [], []
@@ -514,8 +517,10 @@ def run_native(args):
 def run_batched(args):
     """64 seeded rooms of 12 to 182,400 triangles, 16 source / receiver pairs
     each, 262,144 rays per pair, 30 bounces: every step builds the 64 trees and
-    traces all rooms together in batched launches of --batch-chunk rays per
-    pair (the shards add up exactly), each followed by its 8-band RIRs."""
+    traces all 268M rays of all rooms in one batched trace (its bounce loop one
+    CUDA graph of persistent launches, configuration autotuned), followed by
+    the 8-band RIRs of all 1,024 receivers.  --batch-chunk splits the rays of
+    each pair into several traces instead (the shards add up exactly)."""
     import torch
     from paper_1811_05784_gb300 import rt
     torch.cuda.set_device(0)
@@ -532,14 +537,17 @@ def run_batched(args):
         trees = [rt.rt_build_tree(*m, stream=stream) for m in mesh]
         rooms = [dict(tree=t, sources=r.sources, rcv_center=r.rcv_center, rcv_radius=r.rcv_radius,
                       rcv_source=r.rcv_source, band_absorption=r.alpha) for t, r in zip(trees, rooms_sc)]
-        q = 0
+        q, cfg = 0, None
         for begin in range(0, n_rays, chunk):
             isrc = rt.rt_trace_batch(rooms, n_rays, B, ray_begin=begin, ray_count=min(chunk, n_rays - begin),
                                      tail_rays=rt.RT_TAIL_AUTOTUNE, stream=stream, workspace=ws_trace)
             rt.rt_rir(isrc, 48_000.0, duration=1.0, stream=stream)
             q += isrc.queries
+            cfg = {"block_size": isrc.block_size, "tail_rays": int(isrc.tail_rays),
+                   "compaction_period": isrc.compaction_period, "stack_entries": isrc.stack_entries,
+                   "ms_bounces": isrc.ms_bounces}
             del isrc
-        return q
+        return q, cfg
 
     with torch.cuda.stream(stream):
         # finish the autotuner's trials (one configuration per call) first,
@@ -548,10 +556,10 @@ def run_batched(args):
         rooms = [dict(tree=t, sources=r.sources, rcv_center=r.rcv_center, rcv_radius=r.rcv_radius,
                       rcv_source=r.rcv_source, band_absorption=r.alpha) for t, r in zip(trees, rooms_sc)]
         prev = None
-        for _ in range(20):
+        for _ in range(40):
             isrc = rt.rt_trace_batch(rooms, n_rays, B, ray_begin=0, ray_count=chunk, tail_rays=rt.RT_TAIL_AUTOTUNE,
                                      stream=stream, workspace=ws_trace)
-            cur = (isrc.block_size, int(isrc.tail_rays))
+            cur = (isrc.block_size, int(isrc.tail_rays), isrc.compaction_period, isrc.stack_entries)
             del isrc
             if cur == prev:
                 break
@@ -566,7 +574,8 @@ def run_batched(args):
             for _ in range(args.steps):
                 a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 a.record(stream)
-                queries.append(step())
+                q, cfg = step()
+                queries.append(q)
                 b.record(stream)
                 b.synchronize()
                 ms.append(a.elapsed_time(b))
@@ -579,7 +588,8 @@ def run_batched(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{len(rooms_sc)} rooms ({min(tris)}-{max(tris)} tris, {sum(tris)} in total) x "
                                f"{len(rooms_sc[0].sources)} pairs x {n_rays} rays x {B} bounces, receivers r=0.5 m",
-                   "rays_per_launch_per_pair": chunk, "queries_per_step": statistics.mean(queries),
+                   "rays_per_trace_per_pair": chunk, "traces_per_step": -(-n_rays // chunk),
+                   "bounce_kernel": cfg, "queries_per_step": statistics.mean(queries),
                    "step": "64 tree builds + batched traces + RIRs", "l2": "inputs larger than L2"},
         "gpu_launches": launches, "clocks": clk.summary()}))
 

@@ -117,9 +117,9 @@ typedef struct {
                               launch finishes all their remaining bounces (0 = the number
                               of resident threads, -1 = never: one launch per bounce,
                               RT_TAIL_AUTOTUNE = the library times each of its candidate
-                              block sizes and thresholds twice on the first calls of each
-                              workload class and keeps the fastest; results do not depend
-                              on it) */
+                              configurations (block size, threshold, compaction period,
+                              stack depth) twice on the first calls of each workload class
+                              and keeps the fastest; results do not depend on it) */
     void* stream;          /* cudaStream_t */
     /* optional device outputs for parity checks (NULL = off) */
     float* debug_t;        /* [n_bounces][n_traced] hit distance, +inf on escape */
@@ -139,6 +139,12 @@ typedef struct {
                                 receivers gives.  A recorded id outside the mesh is reported
                                 (RT_ERR_INTERNAL); a history of other rays gives other
                                 (meaningless) paths. */
+    int32_t compaction_period; /* while more rays live than the tail threshold, each bounce
+                                launch steps its rays this many bounces (refilling a lane as
+                                soon as its ray dies) before it compacts the survivors into
+                                the next queue (0 = 1: one bounce per launch) */
+    int32_t stack_entries;   /* traversal stack per thread: 0 or 64, or 48 (used only when
+                                every tree has binary depth <= 32, else 64) */
 } rt_trace_params;
 
 #define RT_TAIL_AUTOTUNE (-2)
@@ -184,6 +190,8 @@ typedef struct {
     float ms_bounces;          /* device time of all bounce launches */
     float ms_image_sources;    /* device time of dedup + FP64 reconstruction */
     int32_t n_rcv;             /* receivers of the trace (all rooms of a batch) */
+    int32_t compaction_period; /* bounce-kernel configuration used (with block_size, tail_rays) */
+    int32_t stack_entries;
 } rt_is_view;
 
 typedef struct {

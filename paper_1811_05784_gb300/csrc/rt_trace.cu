@@ -95,7 +95,8 @@ struct BounceArgs {
     unsigned int* status;
     int64_t n_traced;
     int64_t per_src;                     // rays per source traced
-    int b, B;
+    int b, B;                            // first bounce of this launch, bounces of the trace
+    int launch, b_end;                   // counter index of this launch; its survivors are compacted at b_end
     unsigned int tail_threshold;         // live rays at or below which one launch finishes the trace
     unsigned long long* n_queries;
     int step_cap;                        // node visits per query
@@ -328,7 +329,11 @@ __device__ __forceinline__ void tri_test(const RayPre& r, const float4* __restri
 // 4-wide node pushes at most 3 entries, so a tree of binary depth D needs at
 // most 3 ceil(D / 2) <= 64 entries for D <= 42; deeper trees can overflow,
 // which the kernel reports (ST_STACK) instead of writing past the stack.
+// A 48-entry variant serves trees of binary depth <= 32 (3 * 16 = 48): it
+// leaves more of the SM's unified shared memory / L1 to the cache.
 static constexpr int STACK_SMEM = 64;
+static constexpr int STACK_SHORT = 48;
+static constexpr int STACK_SHORT_MAX_DEPTH = 32;
 
 // compare-exchange of (t, ref) pairs, nearer first
 __device__ __forceinline__ void cswap(float& ta, int& ra, float& tb, int& rb) {
@@ -348,7 +353,7 @@ __device__ __forceinline__ void cswap(float& ta, int& ra, float& tb, int& rb) {
 // tested, sorted by entry distance (a 5-exchange network; misses sort last),
 // the nearest is visited next and the other hits are pushed far-to-near.
 // Child references: >= 0 internal node, < 0 leaf ~(first_triangle << 3 | count).
-template <int BT>
+template <int BT, int STACK>
 __device__ __forceinline__ void nearest_hit(const BounceArgs& a, const RoomDev& rm, const RayPre& r, int exclude,
                                             float& best_t, int& best_id, unsigned int& err, int& n_nodes,
                                             int& n_tests, int* __restrict__ stack) {
@@ -393,7 +398,7 @@ __device__ __forceinline__ void nearest_hit(const BounceArgs& a, const RoomDev& 
             } else {
                 node = r0;
                 const int push = (t1 < INFINITY) + (t2 < INFINITY) + (t3 < INFINITY);
-                if (sp + push > STACK_SMEM) {
+                if (sp + push > STACK) {
                     err |= ST_STACK;
                     node = SENTINEL;
                     leaf = 0;
@@ -466,7 +471,7 @@ __device__ __forceinline__ void load_ray(const Queue& q, unsigned int slot, RayS
 
 // One bounce of the ray in s (bounce index bb).  Every lane of the warp calls
 // it; lanes without a ray pass active = false.  Returns true if the ray goes on.
-template <int BT, bool REPLAY>
+template <int BT, bool REPLAY, int STACK>
 __device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool active, int bb, RayState& s,
                                          int* __restrict__ stack) {
     const int q = (int)s.m.x;
@@ -482,7 +487,7 @@ __device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool act
         if (REPLAY)  // the query re-tests the triangle an earlier trace recorded
             replay_hit(a, rm, rp, (int)s.m.y, bb, q, best_t, hit, err, n_tests);
         else
-            nearest_hit<BT>(a, rm, rp, (int)s.m.y, best_t, hit, err, n_nodes, n_tests, stack);
+            nearest_hit<BT, STACK>(a, rm, rp, (int)s.m.y, best_t, hit, err, n_nodes, n_tests, stack);
     }
     if (err) atomicOr(a.status, err);
     const unsigned int amask = __ballot_sync(0xffffffffu, active);
@@ -586,26 +591,32 @@ __device__ __forceinline__ bool step_ray(const BounceArgs& a, int lane, bool act
 }
 
 // ---------------------------------------------------------------------------
-// the bounce kernel
-//   wavefront mode (live rays > tail threshold): one bounce per ray, survivors
-//   compacted into the next queue with one atomic per warp;
+// the bounce kernel: launch k steps the rays of its input queue from bounce
+// a.b (= k P for a compaction period P) and compacts the survivors at a.b_end
+//   wavefront mode (P = 1, live rays > tail threshold): one bounce per ray,
+//   survivors compacted into the next queue with one atomic per warp;
+//   period mode (P > 1, live rays > tail threshold): each lane steps its ray
+//   up to b_end and takes a new one as soon as its ray dies or is written
+//   to the next queue (compaction every P bounces);
 //   tail mode (few live rays): this launch finishes every remaining bounce,
 //   lanes whose ray dies fetch the next one, so the last bounces do not each
 //   wait for their slowest ray.  It writes no survivors, so the later
 //   launches of the same trace find no live rays and return at once.
 // ---------------------------------------------------------------------------
-template <int BT, bool REPLAY>
+template <int BT, bool REPLAY, int STACK>
 __global__ void __launch_bounds__(BT) k_bounce(BounceArgs a) {
-    extern __shared__ int s_stack[];  // STACK_SMEM * BT entries (stack_bytes)
+    extern __shared__ int s_stack[];  // STACK * BT entries (stack_bytes)
     int* stack = s_stack + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    const unsigned int n_live = a.live[a.b];
+    const int k = a.launch;
+    const unsigned int n_live = a.live[k];
     const int b = a.b;
     if (n_live == 0) return;
-    if (n_live > a.tail_threshold) {
+    const bool tail = n_live <= a.tail_threshold;
+    if (!tail && a.b_end == b + 1) {
         for (;;) {
             unsigned int base = 0;
-            if (lane == 0) base = atomicAdd(&a.fetch[b], 32u);
+            if (lane == 0) base = atomicAdd(&a.fetch[k], 32u);
             base = __shfl_sync(0xffffffffu, base, 0);
             if (base >= n_live) break;
             const unsigned int slot = base + lane;
@@ -616,12 +627,12 @@ __global__ void __launch_bounds__(BT) k_bounce(BounceArgs a) {
             s.e0 = s.e1 = s.o;
             s.m = make_uint4(0, 0xFFFFFFFFu, 0, 0);
             if (active) load_ray(a.in, slot, s);
-            const bool survive = step_ray<BT, REPLAY>(a, lane, active, b, s, stack);
+            const bool survive = step_ray<BT, REPLAY, STACK>(a, lane, active, b, s, stack);
             const unsigned int mask = __ballot_sync(0xffffffffu, survive);
             if (mask) {
                 unsigned int obase = 0;
                 const int leader = __ffs(mask) - 1;
-                if (lane == leader) obase = atomicAdd(&a.live[b + 1], (unsigned int)__popc(mask));
+                if (lane == leader) obase = atomicAdd(&a.live[k + 1], (unsigned int)__popc(mask));
                 obase = __shfl_sync(0xffffffffu, obase, leader);
                 if (survive) {
                     unsigned int p = obase + __popc(mask & ((1u << lane) - 1u));
@@ -635,7 +646,8 @@ __global__ void __launch_bounds__(BT) k_bounce(BounceArgs a) {
         }
         return;
     }
-    // tail mode
+    // period mode and tail mode: per-lane refill
+    const int end = tail ? a.B : a.b_end;
     RayState s;
     s.o = make_float4(0, 0, 0, 0);
     s.d = make_float4(0, 0, 1, 0);
@@ -648,7 +660,7 @@ __global__ void __launch_bounds__(BT) k_bounce(BounceArgs a) {
         if (need && !exhausted) {
             unsigned int base = 0;
             const int leader = __ffs(need) - 1;
-            if (lane == leader) base = atomicAdd(&a.fetch[b], (unsigned int)__popc(need));
+            if (lane == leader) base = atomicAdd(&a.fetch[k], (unsigned int)__popc(need));
             base = __shfl_sync(0xffffffffu, base, leader);
             if (!has) {
                 const unsigned int slot = base + __popc(need & ((1u << lane) - 1u));
@@ -661,12 +673,31 @@ __global__ void __launch_bounds__(BT) k_bounce(BounceArgs a) {
             exhausted = base + __popc(need) >= n_live;
         }
         if (__ballot_sync(0xffffffffu, has) == 0) break;
-        const bool survive = step_ray<BT, REPLAY>(a, lane, has, bb, s, stack);
+        const bool survive = step_ray<BT, REPLAY, STACK>(a, lane, has, bb, s, stack);
+        bool write = false;
         if (has) {
-            if (survive)
+            if (survive) {
                 bb++;
-            else
+                write = bb == end;  // end < B here: a ray alive at B has no next bounce
+            } else {
                 has = false;
+            }
+        }
+        const unsigned int wmask = __ballot_sync(0xffffffffu, write);
+        if (wmask) {  // survivors of this launch's bounce range: compact into the next queue
+            unsigned int obase = 0;
+            const int leader = __ffs(wmask) - 1;
+            if (lane == leader) obase = atomicAdd(&a.live[k + 1], (unsigned int)__popc(wmask));
+            obase = __shfl_sync(0xffffffffu, obase, leader);
+            if (write) {
+                const unsigned int p = obase + __popc(wmask & ((1u << lane) - 1u));
+                a.out.o[p] = s.o;
+                a.out.d[p] = s.d;
+                a.out.e0[p] = s.e0;
+                a.out.e1[p] = s.e1;
+                a.out.m[p] = s.m;
+                has = false;
+            }
         }
     }
 }
@@ -847,8 +878,11 @@ static rt_status alloc_queue(Arena& ar, Queue& q, int64_t n) {
 }
 
 // -- bounce-kernel configurations and the online autotuner -------------------
-// A configuration is a block size and a tail threshold (never / resident
-// threads / every ray).  Every configuration gives identical results per ray,
+// A configuration is a block size, a tail threshold (never / resident
+// threads / every ray), a compaction period (bounces each launch runs before
+// it compacts the survivors) and a traversal stack depth (64 entries, or 48
+// for trees of binary depth <= 32; a deeper tree runs the 48-entry
+// candidates with 64).  Every configuration gives identical results per ray,
 // so the autotuner times the real calls: the first calls of a workload class
 // each run the next candidate, every candidate twice (the faster time counts,
 // which keeps one noisy call from deciding), and then the fastest is kept
@@ -856,8 +890,12 @@ static rt_status alloc_queue(Arena& ar, Queue& q, int64_t n) {
 struct Config {
     int block;
     int tail_mode;  // 0 never, 1 resident threads, 2 every ray
+    int period;     // compaction period: bounces per launch above the tail threshold
+    int stack;      // traversal stack entries (STACK_SHORT only for trees it provably fits)
 };
-static const Config CANDIDATES[] = {{128, 2}, {128, 1}, {64, 2}, {256, 2}, {128, 0}, {64, 1}, {256, 1}};
+static const Config CANDIDATES[] = {{128, 2, 1, STACK_SMEM},  {256, 2, 1, STACK_SMEM}, {128, 2, 1, STACK_SHORT},
+                                    {256, 2, 1, STACK_SHORT}, {128, 1, 1, STACK_SMEM}, {128, 1, 4, STACK_SMEM},
+                                    {128, 0, 1, STACK_SMEM},  {128, 0, 4, STACK_SMEM}, {256, 0, 8, STACK_SHORT}};
 static constexpr int N_CANDIDATES = sizeof(CANDIDATES) / sizeof(CANDIDATES[0]);
 static constexpr int TUNE_ROUNDS = 2;
 
@@ -938,39 +976,40 @@ static void tune_report(const std::string& key, int cand, float ms) {
 }
 
 // dynamic shared memory of a bounce launch: the traversal stacks
-static size_t stack_bytes(int block) { return sizeof(int) * (size_t)STACK_SMEM * (size_t)block; }
+static size_t stack_bytes(int block, int stack = STACK_SMEM) {
+    return sizeof(int) * (size_t)stack * (size_t)block;
+}
 
-static void* kernel_of(int block, bool replay = false) {
+template <int BT>
+static void* kernel_bt(bool replay, int stack) {
+    if (stack == STACK_SHORT) return replay ? (void*)k_bounce<BT, true, STACK_SHORT> : (void*)k_bounce<BT, false, STACK_SHORT>;
+    return replay ? (void*)k_bounce<BT, true, STACK_SMEM> : (void*)k_bounce<BT, false, STACK_SMEM>;
+}
+
+static void* kernel_of(int block, bool replay = false, int stack = STACK_SMEM) {
     switch (block) {
-        case 64: return replay ? (void*)k_bounce<64, true> : (void*)k_bounce<64, false>;
-        case 256: return replay ? (void*)k_bounce<256, true> : (void*)k_bounce<256, false>;
-        default: return replay ? (void*)k_bounce<128, true> : (void*)k_bounce<128, false>;
+        case 64: return kernel_bt<64>(replay, stack);
+        case 256: return kernel_bt<256>(replay, stack);
+        default: return kernel_bt<128>(replay, stack);
     }
 }
 
 // allow the stacks above the 48 KB default (the 256-thread block needs 64 KB);
 // a function attribute of the current device, set before any launch or capture
-static rt_status allow_stack_smem(int block, bool replay = false) {
-    RR_CUDA(cudaFuncSetAttribute(kernel_of(block, replay), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)stack_bytes(block)));
+static rt_status allow_stack_smem(int block, bool replay = false, int stack = STACK_SMEM) {
+    RR_CUDA(cudaFuncSetAttribute(kernel_of(block, replay, stack), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)stack_bytes(block, stack)));
     return RT_OK;
 }
 
-template <int BT>
-static int occupancy_grid() {
+// persistent grid: resident blocks per SM x SMs
+static int grid_of_block(int block, int stack = STACK_SMEM) {
     int occ = 0;
-    if (allow_stack_smem(BT) == RT_OK)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bounce<BT, false>, BT, stack_bytes(BT));
+    if (allow_stack_smem(block, false, stack) == RT_OK)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel_of(block, false, stack), block,
+                                                      stack_bytes(block, stack));
     cudaGetLastError();
     return device_sm_count() * (occ > 0 ? occ : 1);
-}
-
-static int grid_of_block(int block) {
-    switch (block) {
-        case 64: return occupancy_grid<64>();
-        case 256: return occupancy_grid<256>();
-        default: return occupancy_grid<128>();
-    }
 }
 
 }  // namespace rr
@@ -987,7 +1026,7 @@ struct rt_workspace {
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
     std::vector<cudaGraphNode_t> nodes;
-    int g_b = 0, g_grid = 0, g_block = 0;
+    int g_b = 0, g_grid = 0, g_block = 0, g_stack = 0;
     bool g_replay = false;
     long long graph_launches = 0;
     unsigned long long last_records = 0;  // capacity hint for the next trace
@@ -1015,16 +1054,18 @@ namespace rr {
 // workspace on a capturable stream the loop is captured once into a CUDA
 // graph and later replayed with updated kernel parameters (one graph launch
 // per trace).
-static rt_status run_bounces(BounceArgs a, const Queue q[2], int n_launch, int block, int grid, cudaStream_t s,
-                             rt_workspace* ws) {
+static rt_status run_bounces(BounceArgs a, const Queue q[2], int n_launch, int period, int stack, int block,
+                             int grid, cudaStream_t s, rt_workspace* ws) {
     const bool replay = a.replay != nullptr;
-    void* kern = kernel_of(block, replay);
-    const size_t smem = stack_bytes(block);
-    RR_TRY(allow_stack_smem(block, replay));
+    void* kern = kernel_of(block, replay, stack);
+    const size_t smem = stack_bytes(block, stack);
+    RR_TRY(allow_stack_smem(block, replay, stack));
     const int B = n_launch;
     std::vector<BounceArgs> args((size_t)B, a);
     for (int b = 0; b < B; b++) {
-        args[b].b = b;
+        args[b].launch = b;
+        args[b].b = b * period;
+        args[b].b_end = std::min(a.B, (b + 1) * period);
         args[b].in = q[b & 1];
         args[b].out = q[(b + 1) & 1];
     }
@@ -1040,7 +1081,8 @@ static rt_status run_bounces(BounceArgs a, const Queue q[2], int n_launch, int b
         }
         return RT_OK;
     }
-    if (!ws->exec || ws->g_b != B || ws->g_grid != grid || ws->g_block != block || ws->g_replay != replay) {
+    if (!ws->exec || ws->g_b != B || ws->g_grid != grid || ws->g_block != block || ws->g_replay != replay ||
+        ws->g_stack != stack) {
         ws->release_graph();
         RR_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         for (int b = 0; b < B; b++) {
@@ -1069,6 +1111,7 @@ static rt_status run_bounces(BounceArgs a, const Queue q[2], int n_launch, int b
         ws->g_grid = grid;
         ws->g_block = block;
         ws->g_replay = replay;
+        ws->g_stack = stack;
     } else {
         for (int b = 0; b < B; b++) {
             cudaKernelNodeParams kp{};
@@ -1390,13 +1433,22 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     int cand = -1;
     int block = p->block_size > 0 ? p->block_size : 128;
     int tail_mode = p->tail_rays < 0 ? 0 : 1;
+    int period = 1, stack = STACK_SMEM;
     if (autotune) {
         key = tune_key(h.total_tris, n_traced, B, n_rooms) + (p->replay_hist ? "_replay" : "");
         cand = tune_pick(key);
         block = CANDIDATES[cand].block;
         tail_mode = CANDIDATES[cand].tail_mode;
+        period = CANDIDATES[cand].period;
+        stack = CANDIDATES[cand].stack;
     }
-    const int grid = grid_of_block(block);
+    if (p->compaction_period > 0) period = p->compaction_period;
+    if (p->stack_entries > 0) stack = p->stack_entries <= STACK_SHORT ? STACK_SHORT : STACK_SMEM;
+    int max_depth = 0;
+    for (int r = 0; r < n_rooms; r++) max_depth = std::max(max_depth, (int)rooms[r].tree->depth);
+    if (max_depth > STACK_SHORT_MAX_DEPTH) stack = STACK_SMEM;  // the short stack could overflow
+    period = std::min(std::max(period, 1), B);
+    const int grid = grid_of_block(block, stack);
     unsigned int tail = 0;
     if (autotune) {
         tail = tail_mode == 0 ? 0u : (tail_mode == 1 ? (unsigned int)grid * (unsigned int)block
@@ -1464,8 +1516,8 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
         a.debug_state = p->debug_state;
         a.debug_cost = p->debug_cost;
         a.replay = p->replay_hist;
-        const int n_launch = (uint64_t)tail >= (uint64_t)n_traced ? 1 : B;
-        RR_TRY(run_bounces(a, q, n_launch, block, grid, s, ws));
+        const int n_launch = (uint64_t)tail >= (uint64_t)n_traced ? 1 : (B + period - 1) / period;
+        RR_TRY(run_bounces(a, q, n_launch, period, stack, block, grid, s, ws));
         RR_CUDA(cudaGetLastError());
         RR_CUDA(cudaEventRecord(ev.e[2], s));
         RR_CUDA(cudaMemcpyAsync(h_cnt.data(), counters, sizeof(unsigned int) * n_counters, cudaMemcpyDeviceToHost, s));
@@ -1475,7 +1527,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
         unsigned int st = h_cnt[2 * B + 1];
         if (st & ST_STACK) {
             set_error("rt_trace: traversal stack overflow (more than %d entries; a tree of binary depth <= 42 "
-                      "always fits)", STACK_SMEM);
+                      "always fits)", stack);
             return RT_ERR_STACK;
         }
         if (st & ST_BOUNDS) {
@@ -1620,6 +1672,8 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     v.hash_collisions = (int64_t)collisions;
     v.block_size = block;
     v.tail_rays = (int64_t)tail;
+    v.compaction_period = period;
+    v.stack_entries = stack;
     cudaEventElapsedTime(&v.ms_rays, ev.e[0], ev.e[1]);
     v.ms_bounces = ms_bounce;
     if (nr > 0) cudaEventElapsedTime(&v.ms_image_sources, ev.e[2], ev.e[3]);
