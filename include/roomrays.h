@@ -217,6 +217,30 @@ void rt_tree_free(rt_tree* tree);
  * rt_build_tree. */
 rt_status rt_build_tree_median(const rt_mesh* mesh, void* stream, rt_tree** out);
 
+/* Nearest-element queries of n given rays (one ray-tracing iteration, Sec.
+ * 2.1-2.2), for comparing the two ways through the tree:
+ *   RT_NEAREST_STACK   each ray alone, front to back with a stack (the
+ *                      traversal of rt_trace's bounce kernel);
+ *   RT_NEAREST_LEVELS  the paper's distribution of rays through the tree
+ *                      level by level (Sec. 2.2): every (ray, box) pair of a
+ *                      level tests the box's daughters with the slab test and
+ *                      the ray goes on into each daughter it meets; leaf
+ *                      elements are intersected when reached; boxes beyond a
+ *                      ray's nearest hit so far are not entered.
+ * Both give the same hits: the nearest triangle with an inclusive watertight
+ * test, ties to the lowest id, the surface exclude_surface[i] (NULL: none)
+ * skipped.  origins, directions: device [n][3]; hit (device [n], -1 = none),
+ * t (device [n], +inf = none).  stats (host [2], nullable): node visits
+ * (4-wide nodes opened) and triangle tests.  Synchronises (the level method
+ * once per level).  Errors: RT_ERR_INVALID_ARG, RT_ERR_CAPACITY (a single
+ * ray meets more than 2^26 boxes of one level), RT_ERR_STEP_LIMIT,
+ * RT_ERR_STACK, RT_ERR_INTERNAL. */
+#define RT_NEAREST_STACK 0
+#define RT_NEAREST_LEVELS 1
+rt_status rt_nearest_hits(const rt_tree* tree, const float* origins, const float* directions,
+                          const int32_t* exclude_surface, int64_t n, int32_t method, int32_t* hit, float* t,
+                          int64_t* stats, void* stream);
+
 /* Tree statistics: nodes, leaves, depth, triangles, surfaces. */
 rt_status rt_tree_info(const rt_tree* tree, int64_t* n_nodes, int64_t* n_tris, int32_t* depth,
                        int32_t* n_surfaces);
@@ -347,7 +371,8 @@ rt_status rt_tail_prior(const float* rates, const float* air, const float* level
  * Surrogate-tail mode (no counterpart in the paper: the learned late
  * reverberation of a room, with the method as fallback and judge).  A room is
  * traced twice with few rays -- 0-50 ms in 1 ms bins ("early") and a 2 s tail
- * probe in 10 ms bins -- and an ensemble of rt_mlp networks predicts its
+ * probe in 10 ms bins, each a batched trace in one tail-mode launch of
+ * 128-thread blocks -- and an ensemble of rt_mlp networks predicts its
  * 8-band tail (50 ms - 2 s in 10 ms bins) from those traces, the room's
  * descriptors and the specular tail prior (rt_tail_prior).  A gate sends the
  * room to full tracing when its descriptors leave the training range or the

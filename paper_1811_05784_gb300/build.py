@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libroomrays.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["rt_common.cu", "rt_build.cu", "rt_trace.cu", "rt_rir.cu", "rt_noalloc.cu", "rt_mlp.cu", "rt_prior.cu", "rt_post.cu",
-           "rt_surrogate.cu"]
+           "rt_surrogate.cu", "rt_levels.cu"]
 
 
 def nvcc() -> str:

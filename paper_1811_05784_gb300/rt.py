@@ -37,7 +37,7 @@ EXPORTED = ["rt_build_tree", "rt_build_tree_median", "rt_tree_free", "rt_tree_in
             "rt_room_parameters", "rt_pressure_rir",
             "rt_surrogate_inputs", "rt_surrogate_reference", "rt_surrogate_train", "rt_surrogate_free",
             "rt_surrogate_info", "rt_surrogate_save", "rt_surrogate_load", "rt_surrogate_predict",
-            "rt_surrogate_gate", "rt_surrogate_envelope", "rt_rir_surrogate"]
+            "rt_surrogate_gate", "rt_surrogate_envelope", "rt_rir_surrogate", "rt_nearest_hits"]
 
 
 class RtError(RuntimeError):
@@ -226,6 +226,8 @@ def lib():
                 getattr(L, name).restype = st
                 getattr(L, name).argtypes = args
             L.rt_surrogate_free.argtypes = [P]
+            L.rt_nearest_hits.restype = st
+            L.rt_nearest_hits.argtypes = [P, P, P, P, C.c_int64, C.c_int32, P, P, P, P]
             L.rt_set_allocator.restype = st
             L.rt_set_allocator.argtypes = [ALLOC_FN, FREE_FN, P]
             _lib = L
@@ -390,6 +392,33 @@ def rt_build_tree(vertices, tris, material_id, surface_id=None, stream=None, med
     fn = lib().rt_build_tree_median if median else lib().rt_build_tree
     _check(fn(C.byref(mesh), _stream_ptr(stream), C.byref(out)))
     return Tree(out)
+
+
+RT_NEAREST_STACK, RT_NEAREST_LEVELS = 0, 1
+
+
+def rt_nearest_hits(tree: Tree, origins, directions, exclude_surface=None, method=RT_NEAREST_STACK, stream=None):
+    """Nearest triangles of n rays (CUDA float32 [n][3] origins and
+    directions, optional CUDA int32 [n] surface to skip): (hit int32 [n],
+    t float32 [n], (node visits, triangle tests)); method RT_NEAREST_STACK
+    (per-ray stack traversal) or RT_NEAREST_LEVELS (the paper's level-by-level
+    distribution of rays through the tree)."""
+    import torch
+    n = int(origins.shape[0])
+    for x, name in ((origins, "origins"), (directions, "directions")):
+        if not (_is_cuda_tensor(x) and x.dtype == torch.float32 and x.is_contiguous() and tuple(x.shape) == (n, 3)):
+            raise ValueError(f"rt_nearest_hits: {name} must be a contiguous CUDA float32 tensor [n][3]")
+    if exclude_surface is not None and not (_is_cuda_tensor(exclude_surface) and exclude_surface.dtype == torch.int32
+                                            and exclude_surface.is_contiguous() and exclude_surface.numel() == n):
+        raise ValueError("rt_nearest_hits: exclude_surface must be a contiguous CUDA int32 tensor [n]")
+    hit = torch.empty(n, dtype=torch.int32, device=origins.device)
+    t = torch.empty(n, dtype=torch.float32, device=origins.device)
+    stats = np.zeros(2, np.int64)
+    _check(lib().rt_nearest_hits(tree._h, P(origins.data_ptr()), P(directions.data_ptr()),
+                                 P(exclude_surface.data_ptr()) if exclude_surface is not None else None, n,
+                                 int(method), P(hit.data_ptr()), P(t.data_ptr()), P(stats.ctypes.data),
+                                 _stream_ptr(stream)))
+    return hit, t, (int(stats[0]), int(stats[1]))
 
 
 class ImageSources:
