@@ -79,8 +79,9 @@ def parse():
     ap.add_argument("--no-config2", action="store_true", help="skip the closed L-room object of the default line")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-tail object of the default line")
     ap.add_argument("--clock-log", default=None, help="keep the nvidia-smi samples of the timed region here")
-    ap.add_argument("--workload", choices=["theatre", "batched", "tetra", "trees"], default="theatre",
-                    help="theatre: the headline line; batched: 64 rooms x 16 pairs x 262,144 rays x 30 bounces "
+    ap.add_argument("--workload", choices=["theatre", "lroom", "batched", "tetra", "trees"], default="theatre",
+                    help="theatre: the headline line; lroom: the closed L-room alone (102,400 tris, 1M rays x 50 "
+                         "bounces); batched: 64 rooms x 16 pairs x 262,144 rays x 30 bounces "
                          "in batched launches; tetra: the N = M scaling sweep of one iteration on the refined "
                          "tetrahedron; trees: the LBVH against the paper's median-split tree "
                          "(each its own line, one GPU)")
@@ -394,6 +395,44 @@ def timed_trace_steps(rt, torch, sc, kw, stream, tail, warmup, steps, flush, dev
                 graph=ws_trace.graph_launches > 0, ws=ws_trace, mesh=(V, T, Mt, St))
 
 
+def lroom_object(rt, torch, stream, tail, args, flush, dev, l2_peak, hbm, rng_kw):
+    """The closed L-room (102,400 triangles, 1M rays x 50 bounces, every ray
+    alive to its last bounce): queries/s per step of tree build + trace + RIR,
+    and the bounce kernel's roofline."""
+    sc2 = scenes.lroom(n_rays=N_RAYS, n_bounces=50)
+    kw2 = rt.scene_args(sc2)
+    kw2.update(rng_kw)
+    run2 = timed_trace_steps(rt, torch, sc2, kw2, stream, tail, args.warmup, args.steps, flush, dev, 1.0)
+    with torch.cuda.stream(stream):
+        roof2 = l2_roofline(rt, torch, run2["tree"], sc2, kw2, run2["chosen"],
+                            statistics.median(run2["phases"]["bounces"]), stream, dev, l2_peak, hbm,
+                            profiled_traffic("k_bounce_lroom.md", run2["chosen"]["tail_rays"]))
+    t2 = sum(run2["ms"]) / 1e3
+    return {"workload": f"closed L-room 102,400 tris / 8 surfaces, {N_RAYS:,} rays x 50 bounces, 4 receivers "
+                        f"r=0.5 m, RIR 8 bands x 1 s at 48 kHz",
+            "value": sum(run2["queries"]) / t2, "unit": UNIT, "ms_per_step": 1e3 * t2 / args.steps,
+            "queries_per_step": int(statistics.median(run2["queries"])), "bounce_kernel": run2["chosen"],
+            "phases_ms": {k: statistics.median(v) for k, v in run2["phases"].items()},
+            "roofline": roof2, "gpu_launches": int(run2["launches"])}
+
+
+def run_lroom(args):
+    import torch
+    from paper_1811_05784_gb300 import rt
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    tail = rt.RT_TAIL_AUTOTUNE if args.tail_rays is None else args.tail_rays
+    l2_peak = rt.rt_measure_l2_bandwidth(stream=stream)
+    with ClockSampler(0, args.clock_log) as clk:
+        o = lroom_object(rt, torch, stream, tail, args, flush, dev, l2_peak, measured_peaks(), {})
+    o.update({"metric": "ray-bounce hits/s, closed L-room", "n_gpus": 1, "steps": args.steps,
+              "warmup": args.warmup, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+              "clocks": clk.summary()})
+    print(json.dumps(o))
+
+
 SUR_TRAIN_ROOMS, SUR_TEST_ROOMS, SUR_TEST_SEED0 = 2048, 64, 1_000_000
 
 
@@ -512,24 +551,7 @@ def run_native(args):
                            stream, dev, l2_peak, hbm, profiled_traffic("k_bounce_theatre.md", chosen["tail_rays"]))
 
     # -- the closed L-room (config 2): full-length traversal -------------------
-    cfg2 = None
-    if not args.no_config2:
-        sc2 = scenes.lroom(n_rays=N_RAYS, n_bounces=50)
-        kw2 = rt.scene_args(sc2)
-        kw2.update(rng_kw)
-        run2 = timed_trace_steps(rt, torch, sc2, kw2, stream, tail, args.warmup, args.steps, flush, dev, 1.0)
-        with torch.cuda.stream(stream):
-            roof2 = l2_roofline(rt, torch, run2["tree"], sc2, kw2, run2["chosen"],
-                                statistics.median(run2["phases"]["bounces"]), stream, dev, l2_peak, hbm,
-                                profiled_traffic("k_bounce_lroom.md", run2["chosen"]["tail_rays"]))
-        t2 = sum(run2["ms"]) / 1e3
-        cfg2 = {"workload": f"closed L-room 102,400 tris / 8 surfaces, {N_RAYS:,} rays x 50 bounces, 4 receivers "
-                            f"r=0.5 m, RIR 8 bands x 1 s at 48 kHz",
-                "value": sum(run2["queries"]) / t2, "unit": UNIT, "ms_per_step": 1e3 * t2 / args.steps,
-                "queries_per_step": int(statistics.median(run2["queries"])), "bounce_kernel": run2["chosen"],
-                "phases_ms": {k: statistics.median(v) for k, v in run2["phases"].items()},
-                "roofline": roof2, "gpu_launches": int(run2["launches"])}
-        del run2
+    cfg2 = None if args.no_config2 else lroom_object(rt, torch, stream, tail, args, flush, dev, l2_peak, hbm, rng_kw)
 
     # max over ranks
     t_max = t_total
@@ -805,6 +827,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "lroom":
+        run_lroom(args)
     elif args.workload == "tetra":
         run_tetra(args)
     elif args.workload == "trees":

@@ -450,7 +450,7 @@ typedef struct {
  * 300 ms 4 in the squared error).  The training range is the descriptors'
  * span over the training rooms; the gate's tolerances are the 99th
  * percentiles (at least 3 dB) of the join and probe gaps (rt_surrogate_gate)
- * on up to 4096 training rooms.  Synchronises; n >= 64. */
+ * on up to 4096 of the validation rooms.  Synchronises; n >= 64. */
 rt_status rt_surrogate_train(const float* X, const float* tail_db, const float* desc, const float* base_db,
                              const float* prior_db, int32_t n, const rt_surrogate_train_params* p,
                              rt_surrogate** out);

@@ -832,10 +832,11 @@ static rt_status train_impl(const float* X, const float* tail_db, const float* d
         }
         if (have_best) RR_TRY(rt_mlp_copy(net, 0, best_w.data(), 1, s));
     }
-    // gate tolerances: 99th percentiles of the gaps on up to 4096 training rooms
+    // gate tolerances: 99th percentiles of the gaps on up to 4096 validation
+    // rooms (never trained on, so their gaps are those of new rooms)
     m->join_db = m->probe_db = INFINITY;
-    const int n_g = std::min(n_tr, 4096);
-    std::vector<int32_t> pick(tr);
+    const int n_g = std::min(n_val, 4096);
+    std::vector<int32_t> pick(val);
     std::shuffle(pick.begin(), pick.end(), rng);
     pick.resize((size_t)n_g);
     int32_t* d_pick;
