@@ -79,7 +79,7 @@ def parse():
     ap.add_argument("--no-config2", action="store_true", help="skip the closed L-room object of the default line")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-tail object of the default line")
     ap.add_argument("--clock-log", default=None, help="keep the nvidia-smi samples of the timed region here")
-    ap.add_argument("--workload", choices=["theatre", "lroom", "batched", "tetra", "trees"], default="theatre",
+    ap.add_argument("--workload", choices=["theatre", "lroom", "batched", "tetra", "trees", "gemm"], default="theatre",
                     help="theatre: the headline line; lroom: the closed L-room alone (102,400 tris, 1M rays x 50 "
                          "bounces); batched: 64 rooms x 16 pairs x 262,144 rays x 30 bounces "
                          "in batched launches; tetra: the N = M scaling sweep of one iteration on the refined "
@@ -821,6 +821,49 @@ def run_trees(args):
                       "warmup": args.warmup, "data": "synthetic", "rows": rows}))
 
 
+def run_gemm(args):
+    """The surrogate network's BF16 GEMMs (rt_gemm_bf16) at batch 65,536: the
+    forward products 960 -> 512, 512 -> 512, 512 -> 1568 and a weight
+    gradient (K = batch), with the TMA kernel and the register-staged one;
+    TFLOP/s from CUDA events (median of the timed launches), against the
+    measured cuBLAS BF16 peak."""
+    import torch
+    from paper_1811_05784_gb300 import rt
+    torch.cuda.set_device(0)
+    peak = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        peak = float(json.load(open(p))["bf16_tflops"])
+    g = torch.Generator(device="cuda").manual_seed(0)
+    rows = []
+    for M, N, K in ((65536, 512, 960), (65536, 512, 512), (65536, 1568, 512), (512, 960, 65536)):
+        A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+        B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+        C = torch.empty((M, N), dtype=torch.float32, device="cuda")
+        row = {"M": M, "N": N, "K": K}
+        for kernel, name in ((rt.RT_GEMM_TMA, "tma"), (rt.RT_GEMM_STAGED, "staged")):
+            for _ in range(max(args.warmup, 1)):
+                rt.rt_gemm_bf16(A, B, kernel=kernel, out=C)
+            ms = []
+            for _ in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                rt.rt_gemm_bf16(A, B, kernel=kernel, out=C)
+                e1.record()
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            t = statistics.median(ms)
+            tf = 2.0 * M * N * K / (t * 1e-3) / 1e12
+            row[name] = {"ms": t, "tflops": tf, "frac_of_bf16_peak": tf / peak if peak else None}
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    print(json.dumps({"metric": "BF16 GEMM TFLOP/s of the surrogate network", "unit": "TFLOP/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "dtype": "bf16 x bf16 -> f32",
+                      "peak": {"bf16_tflops": peak, "source": "MEASURED_PEAKS.json (cuBLAS, burst)"},
+                      "note": "each time includes the call's tensor-map set-up, status read and synchronisation",
+                      "rows": rows}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -829,6 +872,8 @@ def main():
         run_batched(args)
     elif args.workload == "lroom":
         run_lroom(args)
+    elif args.workload == "gemm":
+        run_gemm(args)
     elif args.workload == "tetra":
         run_tetra(args)
     elif args.workload == "trees":

@@ -348,6 +348,19 @@ rt_status rt_mlp_set_weight_decay(rt_mlp* net, float weight_decay);
 rt_status rt_mlp_get_step(const rt_mlp* net, int64_t* step);
 rt_status rt_mlp_set_step(rt_mlp* net, int64_t step);
 
+/* The BF16 GEMM of the network (measurement and test entry point, no
+ * counterpart in the paper): C[M][N] = A[M][K] . B[N][K]^T with FP32
+ * accumulation; A, B device BF16 row-major (K innermost, K % 8 == 0, rows
+ * 16-byte aligned), C device float.  kernel RT_GEMM_TMA: tile loads by TMA
+ * into a 4-stage ring, one producer warp, one MMA-issuing thread, four
+ * epilogue warps, 128 x 128 tiles (the network's kernel); RT_GEMM_STAGED:
+ * tiles copied through registers by all warps, 128 x 64 tiles (the earlier
+ * kernel).  Synchronises; RT_ERR_CUDA if a tile timed out. */
+#define RT_GEMM_TMA 0
+#define RT_GEMM_STAGED 1
+rt_status rt_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K, float* C, int32_t kernel,
+                       void* stream);
+
 /* Specular tail prior of the learned tail (no counterpart in the paper).  In a
  * room whose walls are grouped by the axis their normal is closest to, a ray
  * of direction d loses energy at R(d) = sum_k |d_k| rate[k][f] + air[f] (1/s);

@@ -18,7 +18,9 @@
 // surrogate mode (room descriptors and short traces in, late decay out).
 #include "rt_internal.cuh"
 #include "rt_tc_gemm.cuh"
+#include "rt_tc_tma.cuh"
 
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -167,14 +169,67 @@ static rt_status mlp_reserve(rt_mlp* net, int B, cudaStream_t s) {
     return RT_OK;
 }
 
-// K % 32 == 0 for every product here (layer sizes and the padded batch), so
-// rows are 16-byte aligned as the tile copies need
+// TMA descriptor of a row-major BF16 matrix [rows][K] read in 128-row x
+// 64-column boxes with the 128-byte swizzle (the layout the MMA descriptors
+// expect); rows and columns past the matrix read as zero.  cuTensorMapEncodeTiled
+// is taken from the driver through the runtime's entry-point query.
+static rt_status tensor_map(CUtensorMap* map, const bf16* base, int rows, int K) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            set_error("rt_mlp: cuTensorMapEncodeTiled is not available from the driver");
+            return RT_ERR_CUDA;
+        }
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    if (((uintptr_t)base & 15u) || K % 8 || rows < 1 || K < 1) {
+        set_error("rt_mlp: a GEMM operand needs 16-byte aligned rows (K %% 8 == 0)");
+        return RT_ERR_INVALID_ARG;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)K * sizeof(bf16)};
+    const cuuint32_t box[2] = {(cuuint32_t)tma::BK, (cuuint32_t)tma::BM};
+    const cuuint32_t elem[2] = {1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, elem,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("rt_mlp: cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return RT_ERR_CUDA;
+    }
+    return RT_OK;
+}
+
+// C = A B^T through the TMA-fed, warp-specialised tensor-core kernel
+// (rt_tc_tma.cuh).  K % 32 == 0 for every product here (layer sizes and the
+// padded batch), so rows are 16-byte aligned as the TMA needs.
 template <int EPI>
-static void gemm(const bf16* A, const bf16* B, int M, int N, int K, const float* bias, float* Cf, float* Cpre, bf16* Cb,
-                 unsigned int* status, cudaStream_t s) {
+static rt_status gemm(const bf16* A, const bf16* B, int M, int N, int K, const float* bias, float* Cf, float* Cpre,
+                      bf16* Cb, unsigned int* status, cudaStream_t s) {
+    CUtensorMap ma, mb;
+    RR_TRY(tensor_map(&ma, A, M, K));
+    RR_TRY(tensor_map(&mb, B, N, K));
+    dim3 grid(gridn(N, tma::BN), gridn(M, tma::BM));
+    RR_CUDA(cudaFuncSetAttribute(tma::k_gemm_tma<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, tma::SMEM_BYTES));
+    RR_LAUNCH(tma::k_gemm_tma<EPI>, grid, tma::THREADS, tma::SMEM_BYTES, s, ma, mb, M, N, K, bias, Cf, Cpre, Cb,
+              status);
+    return RT_OK;
+}
+
+// the register-staged kernel (rt_tc_gemm.cuh), kept as the measured baseline
+// of rt_gemm_bf16
+template <int EPI>
+static rt_status gemm_staged(const bf16* A, const bf16* B, int M, int N, int K, const float* bias, float* Cf,
+                             float* Cpre, bf16* Cb, unsigned int* status, cudaStream_t s) {
     dim3 grid(gridn(N, tc::BN), gridn(M, tc::BM));
-    cudaFuncSetAttribute(tc::k_gemm_tc<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    RR_CUDA(cudaFuncSetAttribute(tc::k_gemm_tc<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES));
     RR_LAUNCH(tc::k_gemm_tc<EPI>, grid, 128, tc::SMEM_BYTES, s, A, B, M, N, K, bias, Cf, Cpre, Cb, status);
+    return RT_OK;
 }
 
 static void transpose(const bf16* in, int R, int C, int R_pad, bf16* out, cudaStream_t s) {
@@ -195,12 +250,12 @@ static void refresh_bf16(rt_mlp* net, cudaStream_t s) {
 static rt_status mlp_forward_impl(rt_mlp* net, const float* x, int B, float* y_out, cudaStream_t s) {
     RR_TRY(mlp_reserve(net, B, s));
     RR_LAUNCH(k_f32_to_bf16, gridn((int64_t)B * net->n_in, 256), 256, 0, s, x, (int64_t)B * net->n_in, net->xb);
-    gemm<EPI_BIAS_GELU>(net->xb, net->wb + net->off[0], B, net->n_h, net->n_in, net->w + net->off[1], nullptr, net->z1,
-                        net->h1, net->tc_status, s);
-    gemm<EPI_BIAS_GELU>(net->h1, net->wb + net->off[2], B, net->n_h, net->n_h, net->w + net->off[3], nullptr, net->z2,
-                        net->h2, net->tc_status, s);
-    gemm<EPI_BIAS_F32>(net->h2, net->wb + net->off[4], B, net->n_out, net->n_h, net->w + net->off[5],
-                       y_out ? y_out : net->y, nullptr, nullptr, net->tc_status, s);
+    RR_TRY(gemm<EPI_BIAS_GELU>(net->xb, net->wb + net->off[0], B, net->n_h, net->n_in, net->w + net->off[1], nullptr, net->z1,
+                        net->h1, net->tc_status, s));
+    RR_TRY(gemm<EPI_BIAS_GELU>(net->h1, net->wb + net->off[2], B, net->n_h, net->n_h, net->w + net->off[3], nullptr, net->z2,
+                        net->h2, net->tc_status, s));
+    RR_TRY(gemm<EPI_BIAS_F32>(net->h2, net->wb + net->off[4], B, net->n_out, net->n_h, net->w + net->off[5],
+                       y_out ? y_out : net->y, nullptr, nullptr, net->tc_status, s));
     RR_CUDA(cudaGetLastError());
     return RT_OK;
 }
@@ -215,21 +270,21 @@ static rt_status mlp_backward_impl(rt_mlp* net, const float* x, const float* tar
     // layer 3: dW3 = dY^T H2, db3 = colsum dY, dH2 = dY W3
     transpose(net->dz, B, NO, Bp, net->dzt, s);
     transpose(net->h2, B, H, Bp, net->at, s);
-    gemm<EPI_F32>(net->dzt, net->at, NO, H, Bp, nullptr, net->g + net->off[4], nullptr, nullptr, net->tc_status, s);
+    RR_TRY(gemm<EPI_F32>(net->dzt, net->at, NO, H, Bp, nullptr, net->g + net->off[4], nullptr, nullptr, net->tc_status, s));
     RR_LAUNCH(k_colsum, gridn(NO, 128), 128, 0, s, net->dz, B, NO, net->g + net->off[5]);
-    gemm<EPI_F32>(net->dz, net->wt[2], B, H, NO, nullptr, net->dh, nullptr, nullptr, net->tc_status, s);
+    RR_TRY(gemm<EPI_F32>(net->dz, net->wt[2], B, H, NO, nullptr, net->dh, nullptr, nullptr, net->tc_status, s));
     RR_LAUNCH(k_gelu_back, gridn((int64_t)B * H, 256), 256, 0, s, net->dh, net->z2, (int64_t)B * H, net->dz);
     // layer 2
     transpose(net->dz, B, H, Bp, net->dzt, s);
     transpose(net->h1, B, H, Bp, net->at, s);
-    gemm<EPI_F32>(net->dzt, net->at, H, H, Bp, nullptr, net->g + net->off[2], nullptr, nullptr, net->tc_status, s);
+    RR_TRY(gemm<EPI_F32>(net->dzt, net->at, H, H, Bp, nullptr, net->g + net->off[2], nullptr, nullptr, net->tc_status, s));
     RR_LAUNCH(k_colsum, gridn(H, 128), 128, 0, s, net->dz, B, H, net->g + net->off[3]);
-    gemm<EPI_F32>(net->dz, net->wt[1], B, H, H, nullptr, net->dh, nullptr, nullptr, net->tc_status, s);
+    RR_TRY(gemm<EPI_F32>(net->dz, net->wt[1], B, H, H, nullptr, net->dh, nullptr, nullptr, net->tc_status, s));
     RR_LAUNCH(k_gelu_back, gridn((int64_t)B * H, 256), 256, 0, s, net->dh, net->z1, (int64_t)B * H, net->dz);
     // layer 1 (no input gradient needed)
     transpose(net->dz, B, H, Bp, net->dzt, s);
     transpose(net->xb, B, NI, Bp, net->at, s);
-    gemm<EPI_F32>(net->dzt, net->at, H, NI, Bp, nullptr, net->g + net->off[0], nullptr, nullptr, net->tc_status, s);
+    RR_TRY(gemm<EPI_F32>(net->dzt, net->at, H, NI, Bp, nullptr, net->g + net->off[0], nullptr, nullptr, net->tc_status, s));
     RR_LAUNCH(k_colsum, gridn(H, 128), 128, 0, s, net->dz, B, H, net->g + net->off[1]);
     RR_CUDA(cudaGetLastError());
     return RT_OK;
@@ -439,5 +494,35 @@ extern "C" rt_status rt_mlp_set_step(rt_mlp* net, int64_t step) {
         return RT_ERR_INVALID_ARG;
     }
     net->step = step;
+    return RT_OK;
+}
+
+// Measurement and test entry point of the two GEMM kernels behind the network.
+extern "C" rt_status rt_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K, float* C,
+                                  int32_t kernel, void* stream) {
+    rr::clear_error();
+    if (!A || !B || !C || M < 1 || N < 1 || K < 1 || K % 8 || (kernel != RT_GEMM_TMA && kernel != RT_GEMM_STAGED)) {
+        rr::set_error("rt_gemm_bf16: need device A [M][K], B [N][K], C [M][N], sizes >= 1, K %% 8 == 0 and a kernel");
+        return RT_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    rr::Arena tmp(s);
+    unsigned int* status;
+    RR_TRY(tmp.alloc(&status, 1));
+    RR_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned int), s));
+    const rr::bf16* a = (const rr::bf16*)A;
+    const rr::bf16* b = (const rr::bf16*)B;
+    if (kernel == RT_GEMM_TMA)
+        RR_TRY(rr::gemm<rr::EPI_F32>(a, b, M, N, K, nullptr, C, nullptr, nullptr, status, s));
+    else
+        RR_TRY(rr::gemm_staged<rr::EPI_F32>(a, b, M, N, K, nullptr, C, nullptr, nullptr, status, s));
+    RR_CUDA(cudaGetLastError());
+    unsigned int st = 0;
+    RR_CUDA(cudaMemcpyAsync(&st, status, sizeof st, cudaMemcpyDeviceToHost, s));
+    RR_CUDA(cudaStreamSynchronize(s));
+    if (st) {
+        rr::set_error("rt_gemm_bf16: a tensor-core tile timed out waiting for its copies or MMAs");
+        return RT_ERR_CUDA;
+    }
     return RT_OK;
 }

@@ -37,7 +37,7 @@ EXPORTED = ["rt_build_tree", "rt_build_tree_median", "rt_tree_free", "rt_tree_in
             "rt_room_parameters", "rt_pressure_rir",
             "rt_surrogate_inputs", "rt_surrogate_reference", "rt_surrogate_train", "rt_surrogate_free",
             "rt_surrogate_info", "rt_surrogate_save", "rt_surrogate_load", "rt_surrogate_predict",
-            "rt_surrogate_gate", "rt_surrogate_envelope", "rt_rir_surrogate", "rt_nearest_hits"]
+            "rt_surrogate_gate", "rt_surrogate_envelope", "rt_rir_surrogate", "rt_nearest_hits", "rt_gemm_bf16"]
 
 
 class RtError(RuntimeError):
@@ -226,6 +226,8 @@ def lib():
                 getattr(L, name).restype = st
                 getattr(L, name).argtypes = args
             L.rt_surrogate_free.argtypes = [P]
+            L.rt_gemm_bf16.restype = st
+            L.rt_gemm_bf16.argtypes = [P, P, C.c_int32, C.c_int32, C.c_int32, P, C.c_int32, P]
             L.rt_nearest_hits.restype = st
             L.rt_nearest_hits.argtypes = [P, P, P, P, C.c_int64, C.c_int32, P, P, P, P]
             L.rt_set_allocator.restype = st
@@ -392,6 +394,24 @@ def rt_build_tree(vertices, tris, material_id, surface_id=None, stream=None, med
     fn = lib().rt_build_tree_median if median else lib().rt_build_tree
     _check(fn(C.byref(mesh), _stream_ptr(stream), C.byref(out)))
     return Tree(out)
+
+
+RT_GEMM_TMA, RT_GEMM_STAGED = 0, 1
+
+
+def rt_gemm_bf16(A, B, kernel=RT_GEMM_TMA, out=None, stream=None):
+    """C = A B^T (CUDA bfloat16 A [M][K], B [N][K]) -> CUDA float32 [M][N]."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16 or B.shape[1] != K:
+        raise ValueError("rt_gemm_bf16: bfloat16 A [M][K] and B [N][K]")
+    A, B = A.contiguous(), B.contiguous()
+    if out is None:
+        out = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    _check(lib().rt_gemm_bf16(P(A.data_ptr()), P(B.data_ptr()), int(M), int(N), int(K), P(out.data_ptr()),
+                              int(kernel), _stream_ptr(stream)))
+    return out
 
 
 RT_NEAREST_STACK, RT_NEAREST_LEVELS = 0, 1
