@@ -306,7 +306,7 @@ def l2_roofline(rt, torch, tree, sc, kw, chosen, bounce_ms, stream, dev, l2_peak
     fixed_tail = chosen["tail_rays"] if chosen["tail_rays"] > 0 else -1
     isrc = rt.rt_trace(tree, tail_rays=fixed_tail, block_size=chosen["block_size"], stream=stream,
                        compaction_period=chosen["compaction_period"], stack_entries=chosen["stack_entries"],
-                       sort_queue=chosen["sort_queue"], debug_cost=cost, **kw)
+                       debug_cost=cost, **kw)
     torch.cuda.synchronize()
     c = cost.double().sum((0, 1)).cpu().numpy()
     del cost
@@ -354,8 +354,7 @@ def timed_trace_steps(rt, torch, sc, kw, stream, tail, warmup, steps, flush, dev
             prev = None
             for _ in range(40):
                 _, isrc_t, _ = step()
-                cur = (isrc_t.block_size, int(isrc_t.tail_rays), isrc_t.compaction_period, isrc_t.stack_entries,
-                       isrc_t.sort_queue)
+                cur = (isrc_t.block_size, int(isrc_t.tail_rays), isrc_t.compaction_period, isrc_t.stack_entries)
                 if cur == prev:
                     break
                 prev = cur
@@ -363,8 +362,7 @@ def timed_trace_steps(rt, torch, sc, kw, stream, tail, warmup, steps, flush, dev
             _, isrc_w, _ = step()
         torch.cuda.synchronize()
         chosen = {"block_size": isrc_w.block_size, "tail_rays": int(isrc_w.tail_rays),
-                  "compaction_period": isrc_w.compaction_period, "stack_entries": isrc_w.stack_entries,
-                  "sort_queue": isrc_w.sort_queue}
+                  "compaction_period": isrc_w.compaction_period, "stack_entries": isrc_w.stack_entries}
         torch.cuda.synchronize()
         launches0 = rt.rt_launch_count()
         ms, queries = [], []
@@ -635,7 +633,7 @@ def run_batched(args):
             q += isrc.queries
             cfg = {"block_size": isrc.block_size, "tail_rays": int(isrc.tail_rays),
                    "compaction_period": isrc.compaction_period, "stack_entries": isrc.stack_entries,
-                   "sort_queue": isrc.sort_queue, "ms_bounces": isrc.ms_bounces}
+                   "ms_bounces": isrc.ms_bounces}
             del isrc
         return q, cfg
 
@@ -649,7 +647,7 @@ def run_batched(args):
         for _ in range(40):
             isrc = rt.rt_trace_batch(rooms, n_rays, B, ray_begin=0, ray_count=chunk, tail_rays=rt.RT_TAIL_AUTOTUNE,
                                      stream=stream, workspace=ws_trace)
-            cur = (isrc.block_size, int(isrc.tail_rays), isrc.compaction_period, isrc.stack_entries, isrc.sort_queue)
+            cur = (isrc.block_size, int(isrc.tail_rays), isrc.compaction_period, isrc.stack_entries)
             del isrc
             if cur == prev:
                 break

@@ -118,7 +118,7 @@ typedef struct {
                               of resident threads, -1 = never: one launch per bounce,
                               RT_TAIL_AUTOTUNE = the library times each of its candidate
                               configurations (block size, threshold, compaction period,
-                              stack depth, queue sort) twice on the first calls of each workload class
+                              stack depth) twice on the first calls of each workload class
                               and keeps the fastest; results do not depend on it) */
     void* stream;          /* cudaStream_t */
     /* optional device outputs for parity checks (NULL = off) */
@@ -145,10 +145,6 @@ typedef struct {
                                 the next queue (0 = 1: one bounce per launch) */
     int32_t stack_entries;   /* traversal stack per thread: 0 or 64, or 48 (used only when
                                 every tree has binary depth <= 32, else 64) */
-    int32_t sort_queue;      /* 1: before every bounce launch but the first, the live rays are
-                                sorted by the octant of their direction, then the Morton cell
-                                of their origin in their room's box (neighbouring, alike rays
-                                share a warp); such traces launch without a CUDA graph */
 } rt_trace_params;
 
 #define RT_TAIL_AUTOTUNE (-2)
@@ -196,7 +192,6 @@ typedef struct {
     int32_t n_rcv;             /* receivers of the trace (all rooms of a batch) */
     int32_t compaction_period; /* bounce-kernel configuration used (with block_size, tail_rays) */
     int32_t stack_entries;
-    int32_t sort_queue;
 } rt_is_view;
 
 typedef struct {
@@ -488,9 +483,8 @@ rt_status rt_surrogate_predict(const rt_surrogate* model, const float* X, const 
 /* Gate of n rooms: pass (host [n]) = descriptors within the training range
  * widened by 2 % of its span, join gap <= join_db and probe gap <= probe_db.
  * Join gap: the largest over the bands with traced energy in 40-50 ms of
- * |predicted 50-60 ms energy - traced 40-50 ms energy| in dB (0 when no band
- * has any: sparse early traces of large rooms say nothing about the join, and
- * the probe gap checks the level); probe gap: the largest over bands of the RMS difference (dB)
+ * |predicted 50-60 ms energy - traced 40-50 ms energy| in dB (+inf when no
+ * band has any); probe gap: the largest over bands of the RMS difference (dB)
  * between the predicted and the probe's decay, both relative to the prior, at
  * the features' probe bins.  gaps (host [n][2], nullable) receives both.
  * Synchronises. */

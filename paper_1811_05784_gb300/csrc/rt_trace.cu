@@ -39,7 +39,6 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
-#include <memory>
 #include <mutex>
 #include <string>
 
@@ -662,76 +661,6 @@ __global__ void k_reconstruct(ReconArgs a) {
 static unsigned grid_of(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 // ---------------------------------------------------------------------------
-// queue order between bounce launches: live rays sorted by the octant of
-// their direction, then the 27-bit Morton cell of their origin within their
-// room's root box, so that the lanes of a warp start neighbouring, similarly
-// directed rays (their traversals visit the same nodes).  Slots past the
-// live count sort last; results per ray do not depend on the order.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t spread3(uint32_t x) {  // 9 bits -> every third bit
-    x &= 0x1FFu;
-    x = (x | (x << 16)) & 0x030000FFu;
-    x = (x | (x << 8)) & 0x0300F00Fu;
-    x = (x | (x << 4)) & 0x030C30C3u;
-    x = (x | (x << 2)) & 0x09249249u;
-    return x;
-}
-
-__global__ void k_queue_keys(Queue q, const unsigned int* __restrict__ live, int k, int64_t n_cap,
-                             const RoomDev* __restrict__ rooms, const int32_t* __restrict__ room_of_src,
-                             int64_t per_src, uint64_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_cap) return;
-    uint32_t key = 0xFFFFFFFFu;
-    if ((uint64_t)i < (uint64_t)live[k]) {
-        const float4 o = q.o[i], d = q.d[i];
-        const RoomDev& rm = rooms[room_of_src[(int64_t)q.m[i].x / per_src]];
-        // the root box: the union of the root node's non-empty child boxes
-        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (int a = 0; a < 3; a++) {
-            const float4 l = __ldg(rm.nodes + a), h = __ldg(rm.nodes + 3 + a);
-            const float lv[4] = {l.x, l.y, l.z, l.w}, hv[4] = {h.x, h.y, h.z, h.w};
-            for (int c = 0; c < 4; c++)
-                if (lv[c] < INFINITY) lo[a] = fminf(lo[a], lv[c]), hi[a] = fmaxf(hi[a], hv[c]);
-        }
-        const float p[3] = {o.x, o.y, o.z};
-        uint32_t cell[3];
-        for (int a = 0; a < 3; a++) {
-            const float e = hi[a] - lo[a];
-            const float x = e > 0.f ? (p[a] - lo[a]) / e * 512.0f : 0.f;
-            cell[a] = x <= 0.f ? 0u : (x >= 511.0f ? 511u : (uint32_t)x);
-        }
-        const uint32_t oct = (d.x > 0.f ? 4u : 0u) | (d.y > 0.f ? 2u : 0u) | (d.z > 0.f ? 1u : 0u);
-        key = (oct << 27) | (spread3(cell[0]) << 2) | (spread3(cell[1]) << 1) | spread3(cell[2]);
-    }
-    keys[i] = key;
-    vals[i] = (uint32_t)i;
-}
-
-__global__ void k_queue_gather(Queue in, const uint32_t* __restrict__ order, const unsigned int* __restrict__ live,
-                               int k, int64_t n_cap, Queue out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_cap || (uint64_t)i >= (uint64_t)live[k]) return;
-    const uint32_t j = order[i];
-    out.o[i] = in.o[j];
-    out.d[i] = in.d[j];
-    out.e0[i] = in.e0[j];
-    out.e1[i] = in.e1[j];
-    out.m[i] = in.m[j];
-}
-
-// buffers of the queue sort: a third queue and the sort's keys and scratch
-struct QueueSort {
-    Queue q;
-    uint64_t *keys, *keys_alt;
-    uint32_t *vals, *vals_alt;
-    void* tmp;
-    const RoomDev* rooms;
-    const int32_t* room_of_src;
-    int64_t per_src, n_cap;
-};
-
-// ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
 static rt_status alloc_queue(Arena& ar, Queue& q, int64_t n) {
@@ -755,16 +684,13 @@ static rt_status alloc_queue(Arena& ar, Queue& q, int64_t n) {
 // (optionally persisted in the file named by RT_AUTOTUNE_CACHE).
 struct Config {
     int block;
-    int tail_mode;  // 0 never, 1 resident threads, 2 every ray, 3 after the first bounce
+    int tail_mode;  // 0 never, 1 resident threads, 2 every ray
     int period;     // compaction period: bounces per launch above the tail threshold
     int stack;      // traversal stack entries (STACK_SHORT only for trees it provably fits)
-    int sort;       // sort the live rays (direction octant, origin cell) before every launch but the first
 };
-static const Config CANDIDATES[] = {
-    {128, 2, 1, STACK_SMEM, 0},  {256, 2, 1, STACK_SMEM, 0},  {128, 2, 1, STACK_SHORT, 0}, {256, 2, 1, STACK_SHORT, 0},
-    {128, 1, 1, STACK_SMEM, 0},  {128, 1, 4, STACK_SMEM, 0},  {128, 0, 1, STACK_SMEM, 0},  {128, 0, 4, STACK_SMEM, 0},
-    {256, 0, 8, STACK_SHORT, 0}, {128, 3, 1, STACK_SHORT, 1}, {256, 3, 1, STACK_SHORT, 1}, {128, 0, 4, STACK_SHORT, 1},
-    {256, 0, 2, STACK_SHORT, 1}};
+static const Config CANDIDATES[] = {{128, 2, 1, STACK_SMEM},  {256, 2, 1, STACK_SMEM}, {128, 2, 1, STACK_SHORT},
+                                    {256, 2, 1, STACK_SHORT}, {128, 1, 1, STACK_SMEM}, {128, 1, 4, STACK_SMEM},
+                                    {128, 0, 1, STACK_SMEM},  {128, 0, 4, STACK_SMEM}, {256, 0, 8, STACK_SHORT}};
 static constexpr int N_CANDIDATES = sizeof(CANDIDATES) / sizeof(CANDIDATES[0]);
 static constexpr int TUNE_ROUNDS = 2;
 
@@ -924,7 +850,7 @@ namespace rr {
 // graph and later replayed with updated kernel parameters (one graph launch
 // per trace).
 static rt_status run_bounces(BounceArgs a, const Queue q[2], int n_launch, int period, int stack, int block,
-                             int grid, cudaStream_t s, rt_workspace* ws, const QueueSort* qs = nullptr) {
+                             int grid, cudaStream_t s, rt_workspace* ws) {
     const bool replay = a.replay != nullptr;
     void* kern = kernel_of(block, replay, stack);
     const size_t smem = stack_bytes(block, stack);
@@ -940,20 +866,10 @@ static rt_status run_bounces(BounceArgs a, const Queue q[2], int n_launch, int p
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     const bool can_graph = ws && s != nullptr && cudaStreamIsCapturing(s, &cs) == cudaSuccess &&
-                           cs == cudaStreamCaptureStatusNone && !qs;
+                           cs == cudaStreamCaptureStatusNone;
     cudaGetLastError();
     if (!can_graph) {
         for (int b = 0; b < B; b++) {
-            if (qs && b > 0) {
-                // sort the live rays of this launch's input queue into the third queue
-                const unsigned g = grid_of(qs->n_cap, 256);
-                RR_LAUNCH(k_queue_keys, g, 256, 0, s, args[b].in, args[b].live, b, qs->n_cap, qs->rooms,
-                          qs->room_of_src, qs->per_src, qs->keys, qs->vals);
-                RR_TRY(radix_sort_pairs(qs->keys, qs->vals, qs->keys_alt, qs->vals_alt, qs->n_cap, 0, 32, qs->tmp,
-                                        s));
-                RR_LAUNCH(k_queue_gather, g, 256, 0, s, args[b].in, qs->vals, args[b].live, b, qs->n_cap, qs->q);
-                args[b].in = qs->q;
-            }
             void* params[] = {&args[b]};
             RR_CUDA(cudaLaunchKernel(kern, dim3(grid), dim3(block), params, smem, s));
             note_launch();
@@ -1312,7 +1228,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     int cand = -1;
     int block = p->block_size > 0 ? p->block_size : 128;
     int tail_mode = p->tail_rays < 0 ? 0 : 1;
-    int period = 1, stack = STACK_SMEM, sort = p->sort_queue > 0 ? 1 : 0;
+    int period = 1, stack = STACK_SMEM;
     if (autotune) {
         key = tune_key(h.total_tris, n_traced, B, n_rooms) + (p->replay_hist ? "_replay" : "");
         cand = tune_pick(key);
@@ -1320,7 +1236,6 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
         tail_mode = CANDIDATES[cand].tail_mode;
         period = CANDIDATES[cand].period;
         stack = CANDIDATES[cand].stack;
-        sort = CANDIDATES[cand].sort;
     }
     if (p->compaction_period > 0) period = p->compaction_period;
     if (p->stack_entries > 0) stack = p->stack_entries <= STACK_SHORT ? STACK_SHORT : STACK_SMEM;
@@ -1331,10 +1246,8 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     const int grid = grid_of_block(block, stack);
     unsigned int tail = 0;
     if (autotune) {
-        tail = tail_mode == 0   ? 0u
-               : tail_mode == 1 ? (unsigned int)grid * (unsigned int)block
-               : tail_mode == 3 ? (unsigned int)std::max<int64_t>(n_traced - 1, 0)
-                                : (unsigned int)std::min<int64_t>(n_traced, UINT32_MAX);
+        tail = tail_mode == 0 ? 0u : (tail_mode == 1 ? (unsigned int)grid * (unsigned int)block
+                                                    : (unsigned int)std::min<int64_t>(n_traced, UINT32_MAX));
     } else if (p->tail_rays > 0) {
         tail = (unsigned int)p->tail_rays;
     } else if (p->tail_rays == 0) {
@@ -1350,8 +1263,6 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     int32_t *rec_rcv = nullptr, *rec_ray = nullptr, *rec_m = nullptr;
     float* rec_len = nullptr;
     uint64_t* rec_key = nullptr;
-    std::unique_ptr<Arena> sort_arena;  // queue-sort buffers, made on first use
-    QueueSort sort_bufs{};
     for (int attempt = 0; attempt < 2; attempt++) {
         {
             Carve cv;
@@ -1401,31 +1312,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
         a.debug_cost = p->debug_cost;
         a.replay = p->replay_hist;
         const int n_launch = (uint64_t)tail >= (uint64_t)n_traced ? 1 : (B + period - 1) / period;
-        QueueSort qsort{};
-        if (sort && n_launch > 1) {
-            if (!sort_arena) {
-                sort_arena.reset(new Arena(s));
-                Carve cv;
-                cv.add(&qsort.q.o, (size_t)n_traced);
-                cv.add(&qsort.q.d, (size_t)n_traced);
-                cv.add(&qsort.q.e0, (size_t)n_traced);
-                cv.add(&qsort.q.e1, (size_t)n_traced);
-                cv.add(&qsort.q.m, (size_t)n_traced);
-                cv.add(&qsort.keys, (size_t)n_traced);
-                cv.add(&qsort.keys_alt, (size_t)n_traced);
-                cv.add(&qsort.vals, (size_t)n_traced);
-                cv.add(&qsort.vals_alt, (size_t)n_traced);
-                cv.add((unsigned char**)&qsort.tmp, sort_temp_bytes(n_traced));
-                RR_TRY(cv.alloc(*sort_arena));
-                sort_bufs = qsort;
-            }
-            qsort = sort_bufs;
-            qsort.rooms = d_rooms;
-            qsort.room_of_src = d_room_of_src;
-            qsort.per_src = per_src;
-            qsort.n_cap = n_traced;
-        }
-        RR_TRY(run_bounces(a, q, n_launch, period, stack, block, grid, s, ws, (sort && n_launch > 1) ? &qsort : nullptr));
+        RR_TRY(run_bounces(a, q, n_launch, period, stack, block, grid, s, ws));
         RR_CUDA(cudaGetLastError());
         RR_CUDA(cudaEventRecord(ev.e[2], s));
         RR_CUDA(cudaMemcpyAsync(h_cnt.data(), counters, sizeof(unsigned int) * n_counters, cudaMemcpyDeviceToHost, s));
@@ -1582,7 +1469,6 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
     v.tail_rays = (int64_t)tail;
     v.compaction_period = period;
     v.stack_entries = stack;
-    v.sort_queue = sort;
     cudaEventElapsedTime(&v.ms_rays, ev.e[0], ev.e[1]);
     v.ms_bounces = ms_bounce;
     if (nr > 0) cudaEventElapsedTime(&v.ms_image_sources, ev.e[2], ev.e[3]);

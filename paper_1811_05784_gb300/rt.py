@@ -85,7 +85,7 @@ class rt_trace_params(C.Structure):
                 ("block_size", C.c_int32), ("max_node_visits", C.c_int32), ("tail_rays", C.c_int32),
                 ("stream", P), ("debug_t", P),
                 ("debug_state", P), ("debug_cost", P), ("workspace", P), ("replay_hist", P),
-                ("compaction_period", C.c_int32), ("stack_entries", C.c_int32), ("sort_queue", C.c_int32)]
+                ("compaction_period", C.c_int32), ("stack_entries", C.c_int32)]
 
 
 def _replay_ptr(replay):
@@ -112,8 +112,7 @@ class rt_is_view(C.Structure):
                 ("rec_rcv", P), ("rec_ray", P), ("rec_order", P), ("rec_length", P), ("queries", C.c_int64),
                 ("hash_collisions", C.c_int64), ("block_size", C.c_int32), ("tail_rays", C.c_int64),
                 ("ms_rays", C.c_float), ("ms_bounces", C.c_float), ("ms_image_sources", C.c_float),
-                ("n_rcv", C.c_int32), ("compaction_period", C.c_int32), ("stack_entries", C.c_int32),
-                ("sort_queue", C.c_int32)]
+                ("n_rcv", C.c_int32), ("compaction_period", C.c_int32), ("stack_entries", C.c_int32)]
 
 
 class rt_response_view(C.Structure):
@@ -470,7 +469,6 @@ class ImageSources:
         self.ms_rays, self.ms_bounces, self.ms_image_sources = v.ms_rays, v.ms_bounces, v.ms_image_sources
         self.block_size, self.tail_rays = v.block_size, v.tail_rays
         self.compaction_period, self.stack_entries = v.compaction_period, v.stack_entries
-        self.sort_queue = v.sort_queue
         self.n_rcv = v.n_rcv
 
     def __getattr__(self, name):
@@ -498,7 +496,7 @@ def rt_trace(tree: Tree, sources, rcv_center, rcv_radius, rcv_source, band_absor
              ray_begin=0, ray_count=0, max_distance=0.0, air_beta=None, c=343.2, block_size=0,
              max_node_visits=0, tail_rays=0, stream=None, debug_t=None, debug_state=None,
              debug_cost=None, workspace=None, replay=None, src_axis=None, src_pattern=None, compaction_period=0,
-             stack_entries=0, sort_queue=0) -> ImageSources:
+             stack_entries=0) -> ImageSources:
     """Propagate rays and build image sources (host inputs; see roomrays.h).
     replay: the result (or its hist) of an earlier trace of the same rays --
     the queries then re-test the recorded triangles, for new receivers.
@@ -519,7 +517,7 @@ def rt_trace(tree: Tree, sources, rcv_center, rcv_radius, rcv_source, band_absor
                           P(debug_state.data_ptr()) if debug_state is not None else None,
                           P(debug_cost.data_ptr()) if debug_cost is not None else None,
                           workspace._h if workspace is not None else None, _replay_ptr(replay),
-                          int(compaction_period), int(stack_entries), int(sort_queue))
+                          int(compaction_period), int(stack_entries))
     out = P()
     _check(lib().rt_trace(tree._h, C.byref(S), C.byref(R), pal, len(al), C.byref(prm), C.byref(out)))
     res = ImageSources(out)
@@ -609,7 +607,7 @@ def _rooms(rooms):
 def rt_trace_batch(rooms, n_rays, n_bounces, ray_begin=0, ray_count=0, max_distance=0.0, air_beta=None, c=343.2,
                    block_size=0, max_node_visits=0, tail_rays=0, stream=None, workspace=None,
                    replay=None, debug_t=None, debug_state=None, debug_cost=None, compaction_period=0,
-                   stack_entries=0, sort_queue=0) -> ImageSources:
+                   stack_entries=0) -> ImageSources:
     """Trace many rooms in one persistent launch.  `rooms` is a list of dicts
     with keys tree, sources, rcv_center, rcv_radius, rcv_source,
     band_absorption (and optionally src_axis, src_pattern).  Receivers are
@@ -625,7 +623,7 @@ def rt_trace_batch(rooms, n_rays, n_bounces, ray_begin=0, ray_count=0, max_dista
                           P(debug_state.data_ptr()) if debug_state is not None else None,
                           P(debug_cost.data_ptr()) if debug_cost is not None else None,
                           workspace._h if workspace is not None else None, _replay_ptr(replay),
-                          int(compaction_period), int(stack_entries), int(sort_queue))
+                          int(compaction_period), int(stack_entries))
     out = P()
     _check(lib().rt_trace_batch(arr, len(rooms), C.byref(prm), C.byref(out)))
     res = ImageSources(out)

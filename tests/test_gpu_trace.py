@@ -445,39 +445,33 @@ def test_deterministic():
     assert np.array_equal(ha, hb)
 
 
-@pytest.mark.parametrize("tail,period,stack,sort", [(-1, 1, 0, 0), (1, 1, 0, 0), (5000, 1, 0, 0), (-1, 4, 0, 0),
-                                                    (5000, 3, 48, 0), (-1, 7, 48, 0), (200_000, 1, 48, 0),
-                                                    (199_999, 1, 48, 1), (-1, 4, 48, 1), (-1, 1, 0, 1)])
-def test_tail_mode_matches_per_bounce_launches(tail, period, stack, sort):
+@pytest.mark.parametrize("tail,period,stack", [(-1, 1, 0), (1, 1, 0), (5000, 1, 0), (-1, 4, 0), (5000, 3, 48),
+                                               (-1, 7, 48), (200_000, 1, 48)])
+def test_tail_mode_matches_per_bounce_launches(tail, period, stack):
     """Finishing the last bounces in one launch, compacting every few
-    bounces instead of every bounce, a shorter traversal stack, or sorting
-    the live rays between launches changes nothing per ray."""
+    bounces instead of every bounce, or a shorter traversal stack changes
+    nothing per ray."""
     sc = scenes.theatre(n_rays=200_000, n_bounces=30)
     tree = _tree(sc)
     assert tree.info()["depth"] <= 32          # the 48-entry stack serves this tree
     a = rt.rt_trace(tree, tail_rays=-1, **rt.scene_args(sc))
-    b = rt.rt_trace(tree, tail_rays=tail, compaction_period=period, stack_entries=stack, sort_queue=sort,
-                    **rt.scene_args(sc))
+    b = rt.rt_trace(tree, tail_rays=tail, compaction_period=period, stack_entries=stack, **rt.scene_args(sc))
     assert b.compaction_period == period and b.stack_entries == (48 if stack == 48 else 64)
-    assert b.sort_queue == sort
     assert torch.equal(a.hist, b.hist)
     assert torch.equal(a.ray_energy, b.ray_energy) and torch.equal(a.ray_length, b.ray_length)
     assert a.queries == b.queries and a.n == b.n and a.n_records == b.n_records
     assert torch.equal(a.energy, b.energy) and torch.equal(a.count, b.count)
 
 
-@pytest.mark.parametrize("sort", [0, 1])
-def test_compaction_period_lockstep_against_the_oracle(sort):
+def test_compaction_period_lockstep_against_the_oracle():
     """Every query of an L-room trace run with a compaction period of 3 and
-    the 48-entry stack (and the live rays sorted between launches), in
-    lockstep with the FP64 oracle."""
+    the 48-entry stack, in lockstep with the FP64 oracle."""
     sc = scenes.lroom(h=0.5, n_rays=30_000, n_bounces=20)
     B, N = sc.n_bounces, sc.n_rays
     ds_t = torch.empty((B, N, 6), dtype=torch.float32, device="cuda")
     dt_t = torch.empty((B, N), dtype=torch.float32, device="cuda")
-    tree, isrc = _trace(sc, debug_t=dt_t, debug_state=ds_t, tail_rays=-1, compaction_period=3, stack_entries=48,
-                        sort_queue=sort)
-    assert isrc.compaction_period == 3 and isrc.stack_entries == 48 and isrc.sort_queue == sort
+    tree, isrc = _trace(sc, debug_t=dt_t, debug_state=ds_t, tail_rays=-1, compaction_period=3, stack_entries=48)
+    assert isrc.compaction_period == 3 and isrc.stack_entries == 48
     hist = isrc.hist.cpu().numpy()
     _check_lockstep(sc, oracle.OracleScene(sc, tree=True), ds_t.cpu().numpy(), dt_t.cpu().numpy(), hist)
     _check_compensated_lengths(isrc, dt_t.cpu().numpy(), hist)
