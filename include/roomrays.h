@@ -483,8 +483,9 @@ rt_status rt_surrogate_predict(const rt_surrogate* model, const float* X, const 
 /* Gate of n rooms: pass (host [n]) = descriptors within the training range
  * widened by 2 % of its span, join gap <= join_db and probe gap <= probe_db.
  * Join gap: the largest over the bands with traced energy in 40-50 ms of
- * |predicted 50-60 ms energy - traced 40-50 ms energy| in dB (+inf when no
- * band has any); probe gap: the largest over bands of the RMS difference (dB)
+ * |predicted 50-60 ms energy - traced 40-50 ms energy| in dB (0 when no band
+ * has any: sparse early traces of large rooms say nothing about the join, and
+ * the probe gap checks the level); probe gap: the largest over bands of the RMS difference (dB)
  * between the predicted and the probe's decay, both relative to the prior, at
  * the features' probe bins.  gaps (host [n][2], nullable) receives both.
  * Synchronises. */

@@ -137,15 +137,15 @@ def gate_gaps(desc, X, pred_db, prior_db, lo, hi):
     """(inside the training range with a 2 % margin, join gap dB, probe gap dB) per room.
 
     Join gap: the largest over the bands with traced energy in 40-50 ms of
-    |predicted 50-60 ms energy - traced 40-50 ms energy| in dB (+inf when no
-    band has traced energy there).  Probe gap: the largest over bands of the
+    |predicted 50-60 ms energy - traced 40-50 ms energy| in dB (0 when no band
+    has traced energy there: nothing to join against).  Probe gap: the largest over bands of the
     RMS of (predicted - prior) - (probe - prior) in target form at PROBE_BINS."""
     desc, X = np.asarray(desc, np.float64), np.asarray(X, np.float64)
     lo, hi = np.asarray(lo, np.float64), np.asarray(hi, np.float64)
     span = hi - lo
     inside = np.all((desc >= lo - 0.02 * span) & (desc <= hi + 0.02 * span), axis=1)
     n = len(X)
-    join = np.full(n, np.inf)
+    join = np.zeros(n)
     probe = np.zeros(n)
     tp = to_targets(np.asarray(pred_db, np.float64))
     tq = to_targets(np.asarray(prior_db, np.float64))

@@ -272,7 +272,9 @@ __global__ void k_predict_db(const float* __restrict__ Y, int n_nets, int64_t n,
 // -- gate ----------------------------------------------------------------------
 // per room: inside the training range (2 % margin), the join gap (largest over
 // bands with traced energy in 40-50 ms of |predicted 50-60 ms - traced
-// 40-50 ms| in dB; +inf when no band has traced energy there) and the probe
+// 40-50 ms| in dB; 0 when no band has traced energy there: the early trace
+// then says nothing about the join, and the probe gap still checks the
+// level) and the probe
 // gap (largest over bands of the RMS between the predicted and the probe's
 // decay in target form at the probe bins)
 __global__ void k_gate(const float* __restrict__ desc, const float* __restrict__ X, const float* __restrict__ pred_db,
@@ -307,7 +309,7 @@ __global__ void k_gate(const float* __restrict__ desc, const float* __restrict__
         }
         probe = fmax(probe, sqrt(ss / N_PROBE));
     }
-    gaps[2 * room] = join < 0.0 ? INFINITY : (float)join;
+    gaps[2 * room] = join < 0.0 ? 0.0f : (float)join;  // no traced 40-50 ms energy: nothing to join against
     gaps[2 * room + 1] = (float)probe;
 }
 
