@@ -351,15 +351,26 @@ rt_status rt_mlp_set_step(rt_mlp* net, int64_t step);
 /* The BF16 GEMM of the network (measurement and test entry point, no
  * counterpart in the paper): C[M][N] = A[M][K] . B[N][K]^T with FP32
  * accumulation; A, B device BF16 row-major (K innermost, K % 8 == 0, rows
- * 16-byte aligned), C device float.  kernel RT_GEMM_TMA: tile loads by TMA
- * into a 4-stage ring, one producer warp, one MMA-issuing thread, four
- * epilogue warps, 128 x 128 tiles (the network's kernel); RT_GEMM_STAGED:
- * tiles copied through registers by all warps, 128 x 64 tiles (the earlier
- * kernel).  Synchronises; RT_ERR_CUDA if a tile timed out. */
+ * 16-byte aligned), C device float [M][N].
+ * kernel RT_GEMM_TMA (the network's kernel): one persistent CTA per SM walks
+ * 128 x bn output tiles (bn <= 256, a multiple of 16 chosen to cover N with
+ * the fewest columns); tile loads by TMA into a 4-stage ring, one producer
+ * warp, one MMA-issuing thread, two tensor-memory accumulators so that four
+ * epilogue warps store one tile while the next is computed.  With a device
+ * workspace (workspace_floats > 0) a product whose tiles fill less than half
+ * of the SMs is also cut along K (at most 16 ranges, at least 4 K steps of 64
+ * each, splits x M x N <= workspace_floats); the partial sums are added in
+ * range order, so results do not depend on timing.  workspace may be NULL
+ * with workspace_floats 0 (no cutting); the caller owns it.
+ * kernel RT_GEMM_STAGED: tiles copied through registers by all warps,
+ * 128 x 64 tiles (the earlier kernel; workspace unused).
+ * ms (host, nullable): device time of the product's kernels, from CUDA events
+ * recorded on the stream around them.
+ * Synchronises; RT_ERR_CUDA if a tile timed out. */
 #define RT_GEMM_TMA 0
 #define RT_GEMM_STAGED 1
 rt_status rt_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K, float* C, int32_t kernel,
-                       void* stream);
+                       float* workspace, int64_t workspace_floats, float* ms, void* stream);
 
 /* Specular tail prior of the learned tail (no counterpart in the paper).  In a
  * room whose walls are grouped by the axis their normal is closest to, a ray

@@ -138,6 +138,8 @@ struct rt_mlp {
     rr::bf16 *dz = nullptr, *dzt = nullptr, *at = nullptr;   // backward BF16 scratch
     float* loss_part = nullptr;
     unsigned int* tc_status = nullptr;   // bit 0: a tensor-core GEMM gave up waiting for its MMAs
+    float* splitk = nullptr;             // partial sums of the weight-gradient products cut along the batch
+    size_t splitk_floats = 0;
     std::vector<void*> owned;
     cudaStream_t stream = nullptr;
 };
@@ -164,16 +166,21 @@ static rt_status mlp_reserve(rt_mlp* net, int B, cudaStream_t s) {
     RR_TRY(ar.alloc(&net->dzt, (int64_t)Bp * W));
     RR_TRY(ar.alloc(&net->at, (int64_t)Bp * W));
     RR_TRY(ar.alloc(&net->loss_part, (int64_t)gridn((int64_t)Bp * net->n_out, 256)));
+    // up to 8 partial sums of the largest weight gradient
+    const int64_t wmax = std::max(std::max((int64_t)net->n_out * net->n_h, (int64_t)net->n_h * net->n_h),
+                                  (int64_t)net->n_h * net->n_in);
+    net->splitk_floats = (size_t)(8 * wmax);
+    RR_TRY(ar.alloc(&net->splitk, net->splitk_floats));
     net->act = ar.release();
     net->cap_b = B;
     return RT_OK;
 }
 
-// TMA descriptor of a row-major BF16 matrix [rows][K] read in 128-row x
+// TMA descriptor of a row-major BF16 matrix [rows][K] read in box_rows x
 // 64-column boxes with the 128-byte swizzle (the layout the MMA descriptors
 // expect); rows and columns past the matrix read as zero.  cuTensorMapEncodeTiled
 // is taken from the driver through the runtime's entry-point query.
-static rt_status tensor_map(CUtensorMap* map, const bf16* base, int rows, int K) {
+static rt_status tensor_map(CUtensorMap* map, const bf16* base, int rows, int K, int box_rows) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void* fn = nullptr;
@@ -193,7 +200,7 @@ static rt_status tensor_map(CUtensorMap* map, const bf16* base, int rows, int K)
     }
     const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)K * sizeof(bf16)};
-    const cuuint32_t box[2] = {(cuuint32_t)tma::BK, (cuuint32_t)tma::BM};
+    const cuuint32_t box[2] = {(cuuint32_t)tma::BK, (cuuint32_t)box_rows};
     const cuuint32_t elem[2] = {1, 1};
     const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, elem,
                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -205,19 +212,52 @@ static rt_status tensor_map(CUtensorMap* map, const bf16* base, int rows, int K)
     return RT_OK;
 }
 
-// C = A B^T through the TMA-fed, warp-specialised tensor-core kernel
-// (rt_tc_tma.cuh).  K % 32 == 0 for every product here (layer sizes and the
-// padded batch), so rows are 16-byte aligned as the TMA needs.
+static int sm_count() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (!cached[dev] && cudaDeviceGetAttribute(&cached[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 148;
+    }
+    return cached[dev];
+}
+
+template <auto kernel>
+static rt_status allow_smem(int bytes) {
+    static bool done = false;  // one per kernel
+    if (!done) {
+        RR_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        done = true;
+    }
+    return RT_OK;
+}
+
+// C = A B^T through the persistent TMA-fed, warp-specialised tensor-core
+// kernel (rt_tc_tma.cuh), one CTA per SM.  With a workspace (ws, ws_floats)
+// a product with few output tiles is also cut along K and its partial sums
+// added by k_splitk_reduce.  K % 8 == 0 for the TMA (16-byte rows).
 template <int EPI>
 static rt_status gemm(const bf16* A, const bf16* B, int M, int N, int K, const float* bias, float* Cf, float* Cpre,
-                      bf16* Cb, unsigned int* status, cudaStream_t s) {
+                      bf16* Cb, unsigned int* status, cudaStream_t s, float* ws = nullptr, size_t ws_floats = 0) {
+    const int sms = sm_count();
+    const tma::Shape sh = tma::plan(M, N, K, sms, ws ? ws_floats : 0);
     CUtensorMap ma, mb;
-    RR_TRY(tensor_map(&ma, A, M, K));
-    RR_TRY(tensor_map(&mb, B, N, K));
-    dim3 grid(gridn(N, tma::BN), gridn(M, tma::BM));
-    RR_CUDA(cudaFuncSetAttribute(tma::k_gemm_tma<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, tma::SMEM_BYTES));
-    RR_LAUNCH(tma::k_gemm_tma<EPI>, grid, tma::THREADS, tma::SMEM_BYTES, s, ma, mb, M, N, K, bias, Cf, Cpre, Cb,
-              status);
+    RR_TRY(tensor_map(&ma, A, M, K, tma::BM));
+    RR_TRY(tensor_map(&mb, B, N, K, sh.bn));
+    const int grid = std::min(sh.tiles * sh.splits, sms);
+    if (sh.splits == 1) {
+        RR_TRY(allow_smem<tma::k_gemm_tma<EPI>>(tma::SMEM_BYTES));
+        RR_LAUNCH(tma::k_gemm_tma<EPI>, grid, tma::THREADS, tma::SMEM_BYTES, s, ma, mb, sh, bias, Cf, Cpre, Cb,
+                  (int64_t)0, status);
+    } else {
+        const int64_t MN = (int64_t)M * N;
+        RR_TRY(allow_smem<tma::k_gemm_tma<EPI_F32>>(tma::SMEM_BYTES));
+        RR_LAUNCH(tma::k_gemm_tma<EPI_F32>, grid, tma::THREADS, tma::SMEM_BYTES, s, ma, mb, sh, nullptr, ws, nullptr,
+                  nullptr, MN, status);
+        RR_LAUNCH(tma::k_splitk_reduce<EPI>, (unsigned)std::min<int64_t>((MN / 4 + 255) / 256 + 1, 4 * sms), 256, 0,
+                  s, ws, sh.splits, MN, N, bias, Cf, Cpre, Cb);
+    }
     return RT_OK;
 }
 
@@ -270,21 +310,24 @@ static rt_status mlp_backward_impl(rt_mlp* net, const float* x, const float* tar
     // layer 3: dW3 = dY^T H2, db3 = colsum dY, dH2 = dY W3
     transpose(net->dz, B, NO, Bp, net->dzt, s);
     transpose(net->h2, B, H, Bp, net->at, s);
-    RR_TRY(gemm<EPI_F32>(net->dzt, net->at, NO, H, Bp, nullptr, net->g + net->off[4], nullptr, nullptr, net->tc_status, s));
+    RR_TRY(gemm<EPI_F32>(net->dzt, net->at, NO, H, Bp, nullptr, net->g + net->off[4], nullptr, nullptr, net->tc_status, s,
+                         net->splitk, net->splitk_floats));
     RR_LAUNCH(k_colsum, gridn(NO, 128), 128, 0, s, net->dz, B, NO, net->g + net->off[5]);
     RR_TRY(gemm<EPI_F32>(net->dz, net->wt[2], B, H, NO, nullptr, net->dh, nullptr, nullptr, net->tc_status, s));
     RR_LAUNCH(k_gelu_back, gridn((int64_t)B * H, 256), 256, 0, s, net->dh, net->z2, (int64_t)B * H, net->dz);
     // layer 2
     transpose(net->dz, B, H, Bp, net->dzt, s);
     transpose(net->h1, B, H, Bp, net->at, s);
-    RR_TRY(gemm<EPI_F32>(net->dzt, net->at, H, H, Bp, nullptr, net->g + net->off[2], nullptr, nullptr, net->tc_status, s));
+    RR_TRY(gemm<EPI_F32>(net->dzt, net->at, H, H, Bp, nullptr, net->g + net->off[2], nullptr, nullptr, net->tc_status, s,
+                         net->splitk, net->splitk_floats));
     RR_LAUNCH(k_colsum, gridn(H, 128), 128, 0, s, net->dz, B, H, net->g + net->off[3]);
     RR_TRY(gemm<EPI_F32>(net->dz, net->wt[1], B, H, H, nullptr, net->dh, nullptr, nullptr, net->tc_status, s));
     RR_LAUNCH(k_gelu_back, gridn((int64_t)B * H, 256), 256, 0, s, net->dh, net->z1, (int64_t)B * H, net->dz);
     // layer 1 (no input gradient needed)
     transpose(net->dz, B, H, Bp, net->dzt, s);
     transpose(net->xb, B, NI, Bp, net->at, s);
-    RR_TRY(gemm<EPI_F32>(net->dzt, net->at, H, NI, Bp, nullptr, net->g + net->off[0], nullptr, nullptr, net->tc_status, s));
+    RR_TRY(gemm<EPI_F32>(net->dzt, net->at, H, NI, Bp, nullptr, net->g + net->off[0], nullptr, nullptr, net->tc_status, s,
+                         net->splitk, net->splitk_floats));
     RR_LAUNCH(k_colsum, gridn(H, 128), 128, 0, s, net->dz, B, H, net->g + net->off[1]);
     RR_CUDA(cudaGetLastError());
     return RT_OK;
@@ -499,10 +542,13 @@ extern "C" rt_status rt_mlp_set_step(rt_mlp* net, int64_t step) {
 
 // Measurement and test entry point of the two GEMM kernels behind the network.
 extern "C" rt_status rt_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K, float* C,
-                                  int32_t kernel, void* stream) {
+                                  int32_t kernel, float* workspace, int64_t workspace_floats, float* ms,
+                                  void* stream) {
     rr::clear_error();
-    if (!A || !B || !C || M < 1 || N < 1 || K < 1 || K % 8 || (kernel != RT_GEMM_TMA && kernel != RT_GEMM_STAGED)) {
-        rr::set_error("rt_gemm_bf16: need device A [M][K], B [N][K], C [M][N], sizes >= 1, K %% 8 == 0 and a kernel");
+    if (!A || !B || !C || M < 1 || N < 1 || K < 1 || K % 8 || (kernel != RT_GEMM_TMA && kernel != RT_GEMM_STAGED) ||
+        workspace_floats < 0 || (workspace_floats > 0 && !workspace)) {
+        rr::set_error("rt_gemm_bf16: need device A [M][K], B [N][K], C [M][N], sizes >= 1, K %% 8 == 0, a kernel "
+                      "and a workspace pointer with a positive size");
         return RT_ERR_INVALID_ARG;
     }
     cudaStream_t s = (cudaStream_t)stream;
@@ -510,16 +556,36 @@ extern "C" rt_status rt_gemm_bf16(const void* A, const void* B, int32_t M, int32
     unsigned int* status;
     RR_TRY(tmp.alloc(&status, 1));
     RR_CUDA(cudaMemsetAsync(status, 0, sizeof(unsigned int), s));
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (ms) {
+        RR_CUDA(cudaEventCreate(&ev[0]));
+        if (cudaEventCreate(&ev[1]) != cudaSuccess) {
+            cudaEventDestroy(ev[0]);
+            RR_CUDA(cudaGetLastError());
+        }
+        cudaEventRecord(ev[0], s);
+    }
     const rr::bf16* a = (const rr::bf16*)A;
     const rr::bf16* b = (const rr::bf16*)B;
-    if (kernel == RT_GEMM_TMA)
-        RR_TRY(rr::gemm<rr::EPI_F32>(a, b, M, N, K, nullptr, C, nullptr, nullptr, status, s));
-    else
-        RR_TRY(rr::gemm_staged<rr::EPI_F32>(a, b, M, N, K, nullptr, C, nullptr, nullptr, status, s));
-    RR_CUDA(cudaGetLastError());
+    rt_status st_launch = kernel == RT_GEMM_TMA
+                              ? rr::gemm<rr::EPI_F32>(a, b, M, N, K, nullptr, C, nullptr, nullptr, status, s, workspace,
+                                                      (size_t)workspace_floats)
+                              : rr::gemm_staged<rr::EPI_F32>(a, b, M, N, K, nullptr, C, nullptr, nullptr, status, s);
+    if (ms) cudaEventRecord(ev[1], s);
     unsigned int st = 0;
-    RR_CUDA(cudaMemcpyAsync(&st, status, sizeof st, cudaMemcpyDeviceToHost, s));
-    RR_CUDA(cudaStreamSynchronize(s));
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, status, sizeof st, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (ms) {
+        if (e == cudaSuccess && st_launch == RT_OK) e = cudaEventElapsedTime(ms, ev[0], ev[1]);
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+    }
+    if (st_launch != RT_OK) return st_launch;
+    if (e != cudaSuccess) {
+        rr::set_error("rt_gemm_bf16: %s", cudaGetErrorString(e));
+        return RT_ERR_CUDA;
+    }
     if (st) {
         rr::set_error("rt_gemm_bf16: a tensor-core tile timed out waiting for its copies or MMAs");
         return RT_ERR_CUDA;

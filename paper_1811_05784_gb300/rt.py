@@ -227,7 +227,8 @@ def lib():
                 getattr(L, name).argtypes = args
             L.rt_surrogate_free.argtypes = [P]
             L.rt_gemm_bf16.restype = st
-            L.rt_gemm_bf16.argtypes = [P, P, C.c_int32, C.c_int32, C.c_int32, P, C.c_int32, P]
+            L.rt_gemm_bf16.argtypes = [P, P, C.c_int32, C.c_int32, C.c_int32, P, C.c_int32, P, C.c_int64,
+                                       C.POINTER(C.c_float), P]
             L.rt_nearest_hits.restype = st
             L.rt_nearest_hits.argtypes = [P, P, P, P, C.c_int64, C.c_int32, P, P, P, P]
             L.rt_set_allocator.restype = st
@@ -399,19 +400,27 @@ def rt_build_tree(vertices, tris, material_id, surface_id=None, stream=None, med
 RT_GEMM_TMA, RT_GEMM_STAGED = 0, 1
 
 
-def rt_gemm_bf16(A, B, kernel=RT_GEMM_TMA, out=None, stream=None):
-    """C = A B^T (CUDA bfloat16 A [M][K], B [N][K]) -> CUDA float32 [M][N]."""
+def rt_gemm_bf16(A, B, kernel=RT_GEMM_TMA, out=None, stream=None, workspace=None, timed=False):
+    """C = A B^T (CUDA bfloat16 A [M][K], B [N][K]) -> CUDA float32 [M][N].
+    workspace: CUDA float32 tensor for the partial sums of a product cut
+    along K (None: not cut).  timed=True returns (C, device ms of the
+    product's kernels)."""
     import torch
     M, K = A.shape
     N = B.shape[0]
     if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16 or B.shape[1] != K:
         raise ValueError("rt_gemm_bf16: bfloat16 A [M][K] and B [N][K]")
+    if workspace is not None and (workspace.dtype != torch.float32 or not workspace.is_contiguous()):
+        raise ValueError("rt_gemm_bf16: the workspace is a contiguous float32 tensor")
     A, B = A.contiguous(), B.contiguous()
     if out is None:
         out = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    ms = C.c_float(0.0)
     _check(lib().rt_gemm_bf16(P(A.data_ptr()), P(B.data_ptr()), int(M), int(N), int(K), P(out.data_ptr()),
-                              int(kernel), _stream_ptr(stream)))
-    return out
+                              int(kernel), P(workspace.data_ptr()) if workspace is not None else None,
+                              int(workspace.numel()) if workspace is not None else 0,
+                              C.byref(ms) if timed else None, _stream_ptr(stream)))
+    return (out, ms.value) if timed else out
 
 
 RT_NEAREST_STACK, RT_NEAREST_LEVELS = 0, 1
