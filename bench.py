@@ -262,13 +262,21 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_source_sha():
+    """First 16 hex digits of the SHA-256 of the bounce kernel's sources
+    (rt_trace.cu followed by rt_traverse.cuh)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("rt_trace.cu", "rt_traverse.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1811_05784_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(name, tail):
     """DRAM bytes per trace of the bounce kernel from a committed ncu
     summary under profiles/, if that capture matches the current kernel
     source and configuration (else None)."""
-    import hashlib
     path = os.path.join(ROOT, "profiles", name)
-    src = os.path.join(ROOT, "paper_1811_05784_gb300", "csrc", "rt_trace.cu")
     if not os.path.exists(path):
         return None
     kv = {}
@@ -276,8 +284,7 @@ def profiled_traffic(name, tail):
         if ":" in line and line.split(":")[0].startswith("traffic_"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if kv.get("traffic_source_sha256_16") != sha or kv.get("traffic_config") != f"tail_rays={tail}":
+    if kv.get("traffic_source_sha256_16") != kernel_source_sha() or kv.get("traffic_config") != f"tail_rays={tail}":
         return None
     return float(kv["traffic_bytes_per_trace"])
 

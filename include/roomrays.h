@@ -310,9 +310,10 @@ int32_t rt_api_version(void);
 int64_t rt_launch_count(void);
 
 /* Measurement utility (no counterpart in the paper): L2 read bandwidth of
- * the current device in GB/s, from streaming a 32 MiB L2-resident buffer 16
- * times with L1-bypassing 128-bit loads (best of 5 timed launches after one
- * warm-up).  Used as the roofline denominator of the traversal kernel. */
+ * the current device in GB/s, from streaming a 32 MiB L2-resident buffer 64
+ * times per launch with L1-bypassing 128-bit loads: launches for at least
+ * 200 ms first (a cold GPU raises its clocks), then the best of 10.  Used as
+ * the roofline denominator of the traversal kernel.  Synchronises. */
 rt_status rt_measure_l2_bandwidth(double* read_gbs, void* stream);
 
 /* ---------------------------------------------------------------------------
@@ -564,7 +565,10 @@ int64_t rt_workspace_graph_launches(const rt_workspace* ws);
 
 /* Optional device allocator (e.g. a framework's caching allocator).  Both
  * NULL restores cudaMallocAsync / cudaFreeAsync on the call's stream.  An
- * allocator that returns NULL makes the call fail with RT_ERR_OOM. */
+ * allocator that returns NULL makes the call fail with RT_ERR_OOM.  Blocks
+ * must be 256-byte aligned, as cudaMalloc's are: the traversal reads the
+ * tree in 32-byte sectors, and rt_build_tree fails with RT_ERR_INVALID_ARG
+ * on a node or triangle array that is not 32-byte aligned. */
 typedef void* (*rt_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*rt_free_fn)(void* ptr, void* stream, void* ctx);
 rt_status rt_set_allocator(rt_alloc_fn alloc, rt_free_fn free_fn, void* ctx);

@@ -843,6 +843,10 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out, 
         set_error("rt_build_tree: %u triangles differ in material from their surface", mixed);
         return RT_ERR_INVALID_ARG;
     }
+    if (((uintptr_t)nodes | (uintptr_t)tris) & 31u) {  // the traversal reads them in 32-byte sectors
+        set_error("rt_build_tree: the device allocator returned memory that is not 32-byte aligned");
+        return RT_ERR_INVALID_ARG;
+    }
     tree->depth = hm.depth;
     tree->n_nodes = n_nodes;
     tree->nodes = nodes;

@@ -529,7 +529,7 @@ static rt_status measure_l2_impl(double* gbs, cudaStream_t s) {
     }
     const int64_t bytes = 32ll << 20;  // 32 MiB: well inside the L2
     const int64_t n4 = bytes / 16;
-    const int reps = 16;
+    const int reps = 64;  // 2 GiB of L2 reads per launch, about 0.15 ms
     Arena ar(s);
     float4* buf;
     float* sink;
@@ -539,16 +539,30 @@ static rt_status measure_l2_impl(double* gbs, cudaStream_t s) {
     const int grid = device_sm_count() * 4;
     cudaEvent_t e0, e1;
     RR_CUDA(cudaEventCreate(&e0));
-    RR_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    for (int k = 0; k < 6; k++) {
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        RR_CUDA(cudaGetLastError());
+    }
+    // keep the L2 busy for at least 200 ms first, so that a cold GPU has
+    // raised its clocks, then keep the best of 10 launches
+    float warm = 0.f, best = 1e30f;
+    for (int k = 0; k < 4000 && warm < 200.f; k++) {
         cudaEventRecord(e0, s);
         RR_LAUNCH(k_l2_read, grid, 512, 0, s, buf, n4, reps, sink);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (k > 0 && ms < best) best = ms;  // first launch warms the L2
+        warm += ms;
+    }
+    for (int k = 0; k < 10; k++) {
+        cudaEventRecord(e0, s);
+        RR_LAUNCH(k_l2_read, grid, 512, 0, s, buf, n4, reps, sink);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms > 0.f && ms < best) best = ms;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
