@@ -352,7 +352,8 @@ rt_status rt_mlp_set_step(rt_mlp* net, int64_t step);
 /* The BF16 GEMM of the network (measurement and test entry point, no
  * counterpart in the paper): C[M][N] = A[M][K] . B[N][K]^T with FP32
  * accumulation; A, B device BF16 row-major (K innermost, K % 8 == 0, rows
- * 16-byte aligned), C device float [M][N].
+ * 16-byte aligned), C device float [M][N]; A, B, C and the workspace start on
+ * 16-byte boundaries (RT_ERR_INVALID_ARG otherwise).
  * kernel RT_GEMM_TMA (the network's kernel): one persistent CTA per SM walks
  * 128 x bn output tiles (bn <= 256, a multiple of 16 chosen to cover N with
  * the fewest columns); tile loads by TMA into a 4-stage ring, one producer
@@ -566,9 +567,9 @@ int64_t rt_workspace_graph_launches(const rt_workspace* ws);
 /* Optional device allocator (e.g. a framework's caching allocator).  Both
  * NULL restores cudaMallocAsync / cudaFreeAsync on the call's stream.  An
  * allocator that returns NULL makes the call fail with RT_ERR_OOM.  Blocks
- * must be 256-byte aligned, as cudaMalloc's are: the traversal reads the
- * tree in 32-byte sectors, and rt_build_tree fails with RT_ERR_INVALID_ARG
- * on a node or triangle array that is not 32-byte aligned. */
+ * must be 256-byte aligned, as cudaMalloc's are (the kernels use 16- and
+ * 32-byte vector accesses): a block that is not goes straight back to
+ * free_fn and the call fails with RT_ERR_OOM, before any kernel uses it. */
 typedef void* (*rt_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*rt_free_fn)(void* ptr, void* stream, void* ctx);
 rt_status rt_set_allocator(rt_alloc_fn alloc, rt_free_fn free_fn, void* ctx);

@@ -55,15 +55,32 @@ static void keep_pool_memory() {
     done[dev] = true;
 }
 
+thread_local bool g_alloc_misaligned = false;
+
+bool last_alloc_misaligned() { return g_alloc_misaligned; }
+
 void* dev_alloc(size_t bytes, cudaStream_t s) {
     rt_alloc_fn a;
+    rt_free_fn f;
     void* ctx;
     {
         std::lock_guard<std::mutex> lk(g_alloc_mu);
         a = g_alloc;
+        f = g_free;
         ctx = g_ctx;
     }
-    if (a) return a(bytes, (void*)s, ctx);
+    g_alloc_misaligned = false;
+    if (a) {
+        void* p = a(bytes, (void*)s, ctx);
+        // the kernels use 16- and 32-byte vector accesses: a block that is not
+        // 256-byte aligned goes back to its owner before any kernel sees it
+        if (p && ((uintptr_t)p & 255u)) {
+            if (f) f(p, (void*)s, ctx);
+            g_alloc_misaligned = true;
+            return nullptr;
+        }
+        return p;
+    }
     keep_pool_memory();
     void* p = nullptr;
     if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {

@@ -44,6 +44,9 @@ rt_status cuda_status(cudaError_t e, const char* what);
 // device memory
 // ---------------------------------------------------------------------------
 void* dev_alloc(size_t bytes, cudaStream_t s);
+// true if the last dev_alloc on this thread failed because the caller's
+// allocator returned a block that is not 256-byte aligned
+bool last_alloc_misaligned();
 void dev_free(void* p, cudaStream_t s);
 
 // Owns device allocations made during one call; frees them on scope exit
@@ -61,7 +64,11 @@ struct Arena {
         if (bytes == 0) bytes = 16;
         void* p = dev_alloc(bytes, stream);
         if (!p) {
-            set_error("device allocation of %zu bytes failed", bytes);
+            if (last_alloc_misaligned())
+                set_error("device allocation of %zu bytes failed: the allocator's block is not 256-byte aligned",
+                          bytes);
+            else
+                set_error("device allocation of %zu bytes failed", bytes);
             return RT_ERR_OOM;
         }
         ptrs.push_back(p);

@@ -551,6 +551,10 @@ extern "C" rt_status rt_gemm_bf16(const void* A, const void* B, int32_t M, int32
                       "and a workspace pointer with a positive size");
         return RT_ERR_INVALID_ARG;
     }
+    if (((uintptr_t)A | (uintptr_t)B | (uintptr_t)C | (uintptr_t)workspace) & 15u) {
+        rr::set_error("rt_gemm_bf16: A, B, C and the workspace must be 16-byte aligned");
+        return RT_ERR_INVALID_ARG;
+    }
     cudaStream_t s = (cudaStream_t)stream;
     rr::Arena tmp(s);
     unsigned int* status;

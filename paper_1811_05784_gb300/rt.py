@@ -88,6 +88,17 @@ class rt_trace_params(C.Structure):
                 ("compaction_period", C.c_int32), ("stack_entries", C.c_int32)]
 
 
+def _check_debug(debug_t, debug_state, debug_cost, n_bounces, n_traced):
+    """The optional per-query outputs cover n_bounces x n_traced queries."""
+    q = int(n_bounces) * int(n_traced)
+    if debug_t is not None:
+        _cuda(debug_t, "debug_t", "float32", min_numel=q)
+    if debug_state is not None:
+        _cuda(debug_state, "debug_state", "float32", min_numel=6 * q)
+    if debug_cost is not None:
+        _cuda(debug_cost, "debug_cost", "int32", min_numel=2 * q)
+
+
 def _replay_ptr(replay):
     """Hit history of an earlier trace: an ImageSources or a CUDA int32 tensor
     [n_bounces][n_traced]."""
@@ -263,6 +274,8 @@ ROOM_PARAMS = ("EDT", "T20", "T30", "C80", "D50", "Ts", "SPL")
 def rt_room_parameters(H, fs, stream=None):
     """Room-acoustic parameters [n_rcv][8][7] (numpy, ROOM_PARAMS order) of
     CUDA histograms H [n_rcv][8][n_bins] (e.g. Response.data)."""
+    if not _is_cuda_tensor(H):
+        raise ValueError("rt_room_parameters: H must be a CUDA tensor")
     H = H.contiguous().float()
     R, nb = int(H.shape[0]), int(H.shape[-1])
     if H.dim() != 3 or H.shape[1] != N_BANDS:
@@ -279,6 +292,7 @@ def rt_pressure_rir(image_sources, fs, n_out, n_taps=4095, out=None, stream=None
     R = image_sources.n_rcv
     if out is None:
         out = torch.empty((R, int(n_out)), dtype=torch.float32, device="cuda")
+    _cuda(out, "rt_pressure_rir: out", "float32", (R, int(n_out)))
     _check(lib().rt_pressure_rir(image_sources._h, float(fs), int(n_out), int(n_taps), P(out.data_ptr()),
                                  _stream_ptr(stream)))
     return out
@@ -289,12 +303,15 @@ def rt_tail_prior(rates, air, level, n_nodes, t0, dt, n_bins, out=None, stream=N
     from per-axis decay rates [n][3][8], air rates [n][8] and levels [n]
     (CUDA tensors), with an n_nodes x n_nodes Gauss-Legendre direction rule."""
     import torch
+    if not all(_is_cuda_tensor(x) for x in (rates, air, level)):
+        raise ValueError("rt_tail_prior: rates, air and level must be CUDA tensors")
     rates, air, level = (x.contiguous().float() for x in (rates, air, level))
     n = rates.shape[0]
     if rates.shape != (n, 3, N_BANDS) or air.shape != (n, N_BANDS) or level.shape != (n,):
         raise ValueError("rt_tail_prior: rates [n][3][8], air [n][8], level [n]")
     if out is None:
         out = torch.empty((n, N_BANDS, int(n_bins)), dtype=torch.float32, device=rates.device)
+    _cuda(out, "rt_tail_prior: out", "float32", (n, N_BANDS, int(n_bins)))
     _check(lib().rt_tail_prior(P(rates.data_ptr()), P(air.data_ptr()), P(level.data_ptr()), int(n), int(n_nodes),
                                float(t0), float(dt), int(n_bins), P(out.data_ptr()), _stream_ptr(stream)))
     return out
@@ -316,6 +333,28 @@ def _stream_ptr(stream):
 
 def _is_cuda_tensor(x):
     return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _cuda(t, name, dtype=None, shape=None, min_numel=None):
+    """t itself if it is a contiguous CUDA tensor of the given dtype (a torch
+    dtype name such as "float32"), shape and at least min_numel elements;
+    ValueError otherwise, before anything is launched: a device pointer the
+    library reads or writes must cover what it touches."""
+    ok = _is_cuda_tensor(t) and t.is_contiguous()
+    if ok and dtype is not None:
+        ok = str(t.dtype) == "torch." + dtype
+    if ok and shape is not None:
+        ok = tuple(t.shape) == tuple(int(x) for x in shape)
+    if ok and min_numel is not None:
+        ok = t.numel() >= int(min_numel)
+    if not ok:
+        want = "a contiguous CUDA " + (dtype or "") + " tensor"
+        if shape is not None:
+            want += f" of shape {tuple(int(x) for x in shape)}"
+        if min_numel is not None:
+            want += f" of at least {int(min_numel)} elements"
+        raise ValueError(f"{name}: {want}")
+    return t
 
 
 def _host(x, dtype):
@@ -410,11 +449,16 @@ def rt_gemm_bf16(A, B, kernel=RT_GEMM_TMA, out=None, stream=None, workspace=None
     N = B.shape[0]
     if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16 or B.shape[1] != K:
         raise ValueError("rt_gemm_bf16: bfloat16 A [M][K] and B [N][K]")
+    if not (_is_cuda_tensor(A) and _is_cuda_tensor(B)):
+        raise ValueError("rt_gemm_bf16: A and B must be CUDA tensors")
     if workspace is not None and (workspace.dtype != torch.float32 or not workspace.is_contiguous()):
         raise ValueError("rt_gemm_bf16: the workspace is a contiguous float32 tensor")
     A, B = A.contiguous(), B.contiguous()
     if out is None:
         out = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    _cuda(out, "rt_gemm_bf16: out", "float32", (M, N))
+    if workspace is not None:
+        _cuda(workspace, "rt_gemm_bf16: workspace", "float32")
     ms = C.c_float(0.0)
     _check(lib().rt_gemm_bf16(P(A.data_ptr()), P(B.data_ptr()), int(M), int(N), int(K), P(out.data_ptr()),
                               int(kernel), P(workspace.data_ptr()) if workspace is not None else None,
@@ -511,6 +555,9 @@ def rt_trace(tree: Tree, sources, rcv_center, rcv_radius, rcv_source, band_absor
     the queries then re-test the recorded triangles, for new receivers.
     src_axis / src_pattern: directional sources (see _sources)."""
     S, keep_src = _sources(sources, src_axis, src_pattern)
+    per_src = int(ray_count) if int(ray_count) > 0 else int(n_rays) - int(ray_begin)
+    _check_debug(debug_t, debug_state, debug_cost, n_bounces,
+                 max(per_src, 0) * np.asarray(sources, np.float64).reshape(-1, 3).shape[0])
     rc, prc = _host(np.asarray(rcv_center, np.float64).reshape(-1, 3), np.float64)
     rr, prr = _host(np.asarray(rcv_radius, np.float64).reshape(-1), np.float64)
     rs, prs = _host(np.asarray(rcv_source, np.int32).reshape(-1), np.int32)
@@ -553,9 +600,17 @@ class Response:
 
     def download(self, out=None, stream=None):
         """Copy to host through rt_response_download (out: numpy or CPU tensor)."""
+        need = max(self.n_rcv, 1) * N_BANDS * self.n_bins
         if out is None:
             out = np.empty((max(self.n_rcv, 1), N_BANDS, self.n_bins), np.float32)
-        ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        if hasattr(out, "data_ptr"):
+            if out.is_cuda or str(out.dtype) != "torch.float32" or not out.is_contiguous() or out.numel() < need:
+                raise ValueError(f"download: out must be a contiguous host float32 buffer of {need} elements")
+            ptr = out.data_ptr()
+        else:
+            if out.dtype != np.float32 or not out.flags.c_contiguous or out.size < need:
+                raise ValueError(f"download: out must be a contiguous host float32 buffer of {need} elements")
+            ptr = out.ctypes.data
         _check(lib().rt_response_download(self._h, P(ptr), _stream_ptr(stream)))
         return out
 
@@ -621,6 +676,9 @@ def rt_trace_batch(rooms, n_rays, n_bounces, ray_begin=0, ray_count=0, max_dista
     with keys tree, sources, rcv_center, rcv_radius, rcv_source,
     band_absorption (and optionally src_axis, src_pattern).  Receivers are
     numbered room after room.  replay and the debug outputs: see rt_trace."""
+    per_src = int(ray_count) if int(ray_count) > 0 else int(n_rays) - int(ray_begin)
+    n_src = sum(np.asarray(r["sources"], np.float64).reshape(-1, 3).shape[0] for r in rooms)
+    _check_debug(debug_t, debug_state, debug_cost, n_bounces, max(per_src, 0) * n_src)
     arr, keep, n_rcv = _rooms(rooms)
     if air_beta is not None:
         be, pbe = _host(np.asarray(air_beta, np.float32).reshape(N_BANDS), np.float32)
@@ -708,24 +766,35 @@ class MLP:
         self.n_in, self.n_hidden, self.n_out, self.n_params = a.value, b.value, c.value, n.value
         self.offsets = [int(x) for x in off]
 
+    def _inputs(self, x, target=None):
+        if not _is_cuda_tensor(x) or x.dim() != 2 or x.shape[1] != self.n_in:
+            raise ValueError(f"rt_mlp: x must be a CUDA tensor [batch][{self.n_in}]")
+        x = x.contiguous().float()
+        if target is not None:
+            if not _is_cuda_tensor(target) or tuple(target.shape) != (x.shape[0], self.n_out):
+                raise ValueError(f"rt_mlp: target must be a CUDA tensor [batch][{self.n_out}]")
+            target = target.contiguous().float()
+        return x, target
+
     def forward(self, x, y=None, stream=None):
         import torch
-        x = x.contiguous().float()
+        x, _ = self._inputs(x)
         if y is None:
             y = torch.empty((x.shape[0], self.n_out), dtype=torch.float32, device=x.device)
+        _cuda(y, "rt_mlp: y", "float32", (x.shape[0], self.n_out))
         _check(lib().rt_mlp_forward(self._h, P(x.data_ptr()), int(x.shape[0]), P(y.data_ptr()), _stream_ptr(stream)))
         return y
 
     def gradients(self, x, target, stream=None):
         loss = C.c_float()
-        x, target = x.contiguous().float(), target.contiguous().float()
+        x, target = self._inputs(x, target)
         _check(lib().rt_mlp_gradients(self._h, P(x.data_ptr()), P(target.data_ptr()), int(x.shape[0]),
                                       C.byref(loss), _stream_ptr(stream)))
         return loss.value
 
     def train_step(self, x, target, lr, stream=None, want_loss=True):
         loss = C.c_float()
-        x, target = x.contiguous().float(), target.contiguous().float()
+        x, target = self._inputs(x, target)
         _check(lib().rt_mlp_train_step(self._h, P(x.data_ptr()), P(target.data_ptr()), int(x.shape[0]), float(lr),
                                        C.byref(loss) if want_loss else None, _stream_ptr(stream)))
         return loss.value if want_loss else None

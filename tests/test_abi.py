@@ -111,3 +111,38 @@ def test_static_histogram_binding_rejects_a_wrong_output_before_any_call():
     for bad in (torch.zeros((2, 8, 100)), torch.zeros((2, 8, 99)), torch.zeros((2, 8, 100), dtype=torch.float64)):
         with pytest.raises(ValueError):
             rt.rt_rir_static(_Fake(), 100.0, 1.0, out=bad)
+
+
+def test_binding_rejects_host_tensors_and_short_buffers_before_any_call():
+    """Every binding call that hands a caller's tensor to the library checks
+    it first: host tensors (their pointers would reach kernels), wrong
+    dtypes, and output or per-query buffers too small for what the library
+    writes, all raise ValueError without the library being reached."""
+    import numpy as np
+    from paper_1811_05784_gb300 import rt
+    torch = pytest.importorskip("torch")
+    a = torch.zeros((16, 8), dtype=torch.bfloat16)  # host tensors
+    with pytest.raises(ValueError):
+        rt.rt_gemm_bf16(a, a)
+    with pytest.raises(ValueError):
+        rt.rt_room_parameters(torch.zeros((1, 8, 10)), 48000.0)
+    with pytest.raises(ValueError):
+        rt.rt_tail_prior(torch.zeros((1, 3, 8)), torch.zeros((1, 8)), torch.zeros(1), 8, 0.05, 0.01, 10)
+    # per-query debug outputs sized for 2 bounces x 10 rays of one source
+    kw = dict(sources=[[0.0, 0.0, 1.0]], rcv_center=[[1.0, 0.0, 1.0]], rcv_radius=[0.5], rcv_source=[0],
+              band_absorption=np.zeros((1, 8)), n_rays=10, n_bounces=2)
+    for bad in (dict(debug_t=torch.zeros(20)), dict(debug_state=torch.zeros(120)),
+                dict(debug_cost=torch.zeros(40, dtype=torch.int32))):
+        with pytest.raises(ValueError):
+            rt.rt_trace(None, **kw, **bad)
+    with pytest.raises(ValueError):
+        rt.rt_trace_batch([dict(tree=None, **{k: v for k, v in kw.items() if k not in ("n_rays", "n_bounces")})],
+                          10, 2, debug_t=torch.zeros(20))
+
+    class _Response:
+        n_rcv, n_bins = 1, 10
+        download = rt.Response.download
+
+    for bad in (np.zeros(79, np.float32), np.zeros(80, np.float64), torch.zeros(79)):
+        with pytest.raises(ValueError):
+            _Response().download(out=bad)
