@@ -225,10 +225,12 @@ static int sm_count() {
 
 template <auto kernel>
 static rt_status allow_smem(int bytes) {
-    static bool done = false;  // one per kernel
-    if (!done) {
+    static bool done[64] = {};  // one per kernel and device
+    int dev = 0;
+    RR_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64 || !done[dev]) {
         RR_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-        done = true;
+        if (dev >= 0 && dev < 64) done[dev] = true;
     }
     return RT_OK;
 }

@@ -292,7 +292,8 @@ def rt_pressure_rir(image_sources, fs, n_out, n_taps=4095, out=None, stream=None
     R = image_sources.n_rcv
     if out is None:
         out = torch.empty((R, int(n_out)), dtype=torch.float32, device="cuda")
-    _cuda(out, "rt_pressure_rir: out", "float32", (R, int(n_out)))
+    if int(n_out) >= 1:  # the library reports invalid sizes itself
+        _cuda(out, "rt_pressure_rir: out", "float32", (R, int(n_out)))
     _check(lib().rt_pressure_rir(image_sources._h, float(fs), int(n_out), int(n_taps), P(out.data_ptr()),
                                  _stream_ptr(stream)))
     return out
@@ -311,7 +312,8 @@ def rt_tail_prior(rates, air, level, n_nodes, t0, dt, n_bins, out=None, stream=N
         raise ValueError("rt_tail_prior: rates [n][3][8], air [n][8], level [n]")
     if out is None:
         out = torch.empty((n, N_BANDS, int(n_bins)), dtype=torch.float32, device=rates.device)
-    _cuda(out, "rt_tail_prior: out", "float32", (n, N_BANDS, int(n_bins)))
+    if int(n_bins) >= 1 and n >= 1:  # the library reports invalid sizes itself
+        _cuda(out, "rt_tail_prior: out", "float32", (n, N_BANDS, int(n_bins)))
     _check(lib().rt_tail_prior(P(rates.data_ptr()), P(air.data_ptr()), P(level.data_ptr()), int(n), int(n_nodes),
                                float(t0), float(dt), int(n_bins), P(out.data_ptr()), _stream_ptr(stream)))
     return out
