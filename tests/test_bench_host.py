@@ -60,3 +60,34 @@ def test_directional_source_arguments_are_checked_before_any_call():
     assert np.asarray(keep[2]).tolist() == [0.0]
     with pytest.raises(ValueError):
         rt._sources(np.zeros((2, 3)), [[0, 0, 1]], [0.1])
+
+
+def _bench_lines(args, env=None):
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                       timeout=600, env=env, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference times the oracle on the host on a bounded
+    sample and prints one JSON line with the contract's keys."""
+    lines = _bench_lines(["--impl", "reference", "--steps", "1", "--warmup", "0", "--cpu-sample-rays", "2000"])
+    assert len(lines) == 1
+    d = lines[0]
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    for key in ("metric", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "scaling", "dtype", "data", "config"):
+        assert key in d, key
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert "workload" in d["config"]
+
+
+def test_reference_arm_prints_nothing_on_other_ranks():
+    env = dict(os.environ, RANK="1", LOCAL_RANK="1", WORLD_SIZE="2")
+    assert _bench_lines(["--impl", "reference", "--steps", "1", "--warmup", "0", "--cpu-sample-rays", "2000"],
+                        env=env) == []
