@@ -1,0 +1,71 @@
+"""Degenerate but valid inputs through the C ABI, against the FP64 oracle:
+a mesh of one triangle (the tree build's one-element path), a scene where
+every ray escapes at its first query (no image source at all, an all-zero
+RIR), and a single ray (fewer rays than a warp)."""
+import numpy as np
+import pytest
+
+import oracle
+import scenes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1811_05784_gb300 import rt  # noqa: E402
+
+
+def _scene(name, vertices, source, receiver, radius, n_rays, n_bounces, alpha=0.1):
+    f = scenes.f32
+    return scenes.Scene(name, f(np.asarray(vertices, np.float64)), np.array([[0, 1, 2]], np.int32),
+                        np.zeros(1, np.int32), np.zeros(1, np.int32), np.full((1, 8), alpha, np.float32),
+                        np.zeros(8, np.float32), f(np.asarray([source], np.float64)),
+                        f(np.asarray([receiver], np.float64)), f(np.asarray([radius], np.float64)),
+                        np.zeros(1, np.int32), n_rays, n_bounces)
+
+
+def _against_oracle(sc, duration=0.1):
+    tree = rt.rt_build_tree(sc.vertices, sc.tris, sc.material_id, sc.surface_id)
+    isrc = rt.rt_trace(tree, **rt.scene_args(sc))
+    H = rt.rt_rir(isrc, sc.fs, duration=duration).download()
+    tr = oracle.trace(oracle.OracleScene(sc, tree=False))
+    hist = isrc.hist.cpu().numpy().T
+    ok = tr.first_amb == tr.B
+    assert ok.all()
+    assert np.array_equal(hist, tr.hist)
+    ois = oracle.image_sources(sc, tr)
+    Ho = oracle.rir(ois, 1, sc.fs, duration=duration)
+    assert isrc.n == len(ois.order)
+    if len(ois.order):  # the same arrival times, in FP64
+        got = np.sort(isrc.time.cpu().numpy())
+        assert np.allclose(got, np.sort(ois.t), rtol=1e-9, atol=0)
+    return isrc, H, Ho, tr
+
+
+def test_one_triangle_mesh():
+    """A floor triangle under the source: the rays going down hit it once and
+    leave upwards, the others escape at once; hits, image sources (the direct
+    sound and the floor's mirror image) and the RIR agree with the oracle."""
+    sc = _scene("one-triangle", [(-10, -10, 0), (10, -10, 0), (0, 10, 0)], (0.0, 0.0, 1.0), (1.0, 1.0, 0.5),
+                0.3, 2000, 4)
+    isrc, H, Ho, tr = _against_oracle(sc)
+    assert (tr.hist[:, 0] >= 0).any() and (tr.hist[:, 0] < 0).any() and (tr.hist[:, 1] < 0).all()
+    assert np.abs(Ho).sum() > 0
+    assert np.linalg.norm(H - Ho) <= 1e-6 * np.linalg.norm(Ho)
+
+
+def test_every_ray_escapes_at_once():
+    """A tiny triangle far away and a small receiver far away: no ray hits
+    or crosses anything, so each ray makes one query, there is no record and
+    no image source, and the RIR is all zero."""
+    sc = _scene("nothing", [(100, 100, 100), (100.001, 100, 100), (100, 100.001, 100)], (0.0, 0.0, 0.0),
+                (-50.0, 0.0, 0.0), 0.01, 1000, 5)
+    isrc, H, Ho, tr = _against_oracle(sc)
+    assert isrc.queries == sc.n_rays and isrc.n == 0 and isrc.n_records == 0
+    assert (tr.hist[:, 0] == -1).all()
+    assert not H.any() and not np.asarray(Ho).any()
+
+
+def test_a_single_ray():
+    sc = scenes.shoebox(n_rays=1, n_bounces=10)
+    isrc, H, Ho, tr = _against_oracle(sc, duration=0.25)
+    assert isrc.queries == 10
