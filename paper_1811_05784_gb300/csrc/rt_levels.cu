@@ -68,84 +68,94 @@ __global__ void k_ray_rows(const float* __restrict__ org, const float* __restric
     best[i] = ~0ull;
 }
 
-// one level: pairs (ray, node) -> child pairs and leaf tests
-__global__ void k_level(QueryTree tr, const RayRow* __restrict__ rows, const int2* __restrict__ in, uint32_t n_in,
-                        int2* __restrict__ out, uint32_t* __restrict__ n_out, uint32_t cap,
-                        unsigned long long* __restrict__ best, unsigned long long* __restrict__ counts,
+// one level: pairs (ray, node) -> child pairs and leaf tests.  The level's
+// pair count is read from the device (n_in_p, written by the level before),
+// so the host queues every level without reading it back; a count above the
+// pair buffers' capacity means pairs were dropped, which the host finds in the
+// counters afterwards and answers by running the chunk again in halves.
+__global__ void k_level(QueryTree tr, const RayRow* __restrict__ rows, const int2* __restrict__ in,
+                        const uint32_t* __restrict__ n_in_p, int2* __restrict__ out, uint32_t* __restrict__ n_out,
+                        uint32_t cap, unsigned long long* __restrict__ best, unsigned long long* __restrict__ counts,
                         unsigned int* __restrict__ status) {
-    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t n_in = min(*n_in_p, cap);
     const int lane = threadIdx.x & 31;
-    bool act = j < n_in;
-    int ray = 0, node = 0;
-    if (act) {
-        const int2 p = in[j];
-        ray = p.x, node = p.y;
-        if ((int64_t)node >= tr.n_nodes || node < 0) {
-            atomicOr(status, ST_BOUNDS);
-            act = false;
-        }
-    }
-    float t[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
-    int ref[4] = {0, 0, 0, 0};
-    int tests = 0;
-    if (act) {
-        const RayRow w = rows[ray];
-        const RayPre r = row_pre(w);
-        const int exclude = __float_as_int(w.c.z);
-        const unsigned long long b0 = best[ray];
-        float tfar = b0 == ~0ull ? INFINITY : __uint_as_float((unsigned int)(b0 >> 32));
-        const float4* np = tr.nodes + 8 * (int64_t)node;
-        const float4 lx = __ldg(np), ly = __ldg(np + 1), lz = __ldg(np + 2);
-        const float4 hx = __ldg(np + 3), hy = __ldg(np + 4), hz = __ldg(np + 5);
-        const int4 rf = __ldg(reinterpret_cast<const int4*>(np + 6));
-        t[0] = slab(r, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x, tfar);
-        t[1] = slab(r, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, tfar);
-        t[2] = slab(r, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z, tfar);
-        t[3] = slab(r, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w, tfar);
-        ref[0] = rf.x, ref[1] = rf.y, ref[2] = rf.z, ref[3] = rf.w;
-        // leaf children: their triangles now
-        float bt = tfar;
-        int bid = b0 == ~0ull ? 0x7FFFFFFF : (int)(unsigned int)(b0 & 0xFFFFFFFFu);
-        for (int c = 0; c < 4; c++) {
-            if (!(t[c] < INFINITY) || ref[c] >= 0) continue;
-            const int code = ~ref[c];
-            const int first = code >> 3, cnt = code & 7;
-            if ((int64_t)first + cnt > tr.n_tris) {
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n_in; base += gridDim.x * blockDim.x) {
+        const uint32_t j = base + threadIdx.x;
+        bool act = j < n_in;
+        int ray = 0, node = 0;
+        if (act) {
+            const int2 p = in[j];
+            ray = p.x, node = p.y;
+            if ((int64_t)node >= tr.n_nodes || node < 0) {
                 atomicOr(status, ST_BOUNDS);
-                continue;
+                act = false;
             }
-            for (int k = 0; k < cnt; k++) tri_test(r, tr.tris + 3 * (int64_t)(first + k), exclude, bt, bid);
-            tests += cnt;
         }
-        if (bid != 0x7FFFFFFF && pack_hit(bt, bid) < b0) atomicMin(best + ray, pack_hit(bt, bid));
-    }
-    // internal children met: one pair each, one atomic per warp and child slot
-    for (int c = 0; c < 4; c++) {
-        const bool emit = act && t[c] < INFINITY && ref[c] >= 0;
-        const unsigned int m = __ballot_sync(0xffffffffu, emit);
-        if (!m) continue;
-        const int leader = __ffs(m) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(n_out, (uint32_t)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (emit) {
-            const uint32_t p = base + __popc(m & ((1u << lane) - 1u));
-            if (p < cap) out[p] = make_int2(ray, ref[c]);
+        float t[4] = {INFINITY, INFINITY, INFINITY, INFINITY};
+        int ref[4] = {0, 0, 0, 0};
+        int tests = 0;
+        if (act) {
+            const RayRow w = rows[ray];
+            const RayPre r = row_pre(w);
+            const int exclude = __float_as_int(w.c.z);
+            const unsigned long long b0 = best[ray];
+            float tfar = b0 == ~0ull ? INFINITY : __uint_as_float((unsigned int)(b0 >> 32));
+            const float4* np = tr.nodes + 8 * (int64_t)node;
+            float4 lx, ly, lz, hx, hy, hz;
+            ld_v8(np, lx, ly);
+            ld_v8(np + 2, lz, hx);
+            ld_v8(np + 4, hy, hz);
+            const int4 rf = __ldg(reinterpret_cast<const int4*>(np + 6));
+            t[0] = slab(r, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x, tfar);
+            t[1] = slab(r, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y, tfar);
+            t[2] = slab(r, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z, tfar);
+            t[3] = slab(r, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w, tfar);
+            ref[0] = rf.x, ref[1] = rf.y, ref[2] = rf.z, ref[3] = rf.w;
+            // leaf children: their triangles now
+            float bt = tfar;
+            int bid = b0 == ~0ull ? 0x7FFFFFFF : (int)(unsigned int)(b0 & 0xFFFFFFFFu);
+            for (int c = 0; c < 4; c++) {
+                if (!(t[c] < INFINITY) || ref[c] >= 0) continue;
+                const int code = ~ref[c];
+                const int first = code >> 3, cnt = code & 7;
+                if ((int64_t)first + cnt > tr.n_tris) {
+                    atomicOr(status, ST_BOUNDS);
+                    continue;
+                }
+                for (int k = 0; k < cnt; k++) tri_test(r, tr.tris + 3 * (int64_t)(first + k), exclude, bt, bid);
+                tests += cnt;
+            }
+            if (bid != 0x7FFFFFFF && pack_hit(bt, bid) < b0) atomicMin(best + ray, pack_hit(bt, bid));
         }
-    }
-    // node visits and triangle tests of this level
-    const unsigned int nv = __popc(__ballot_sync(0xffffffffu, act));
-    int tt = tests;
-    for (int o = 16; o > 0; o >>= 1) tt += __shfl_down_sync(0xffffffffu, tt, o);
-    if (lane == 0 && nv) {
-        atomicAdd(counts, (unsigned long long)nv);
-        atomicAdd(counts + 1, (unsigned long long)tt);
+        // internal children met: one pair each, one atomic per warp and child slot
+        for (int c = 0; c < 4; c++) {
+            const bool emit = act && t[c] < INFINITY && ref[c] >= 0;
+            const unsigned int m = __ballot_sync(0xffffffffu, emit);
+            if (!m) continue;
+            const int leader = __ffs(m) - 1;
+            uint32_t obase = 0;
+            if (lane == leader) obase = atomicAdd(n_out, (uint32_t)__popc(m));
+            obase = __shfl_sync(0xffffffffu, obase, leader);
+            if (emit) {
+                const uint32_t p = obase + __popc(m & ((1u << lane) - 1u));
+                if (p < cap) out[p] = make_int2(ray, ref[c]);
+            }
+        }
+        // node visits and triangle tests of this level
+        const unsigned int nv = __popc(__ballot_sync(0xffffffffu, act));
+        int tt = tests;
+        for (int o = 16; o > 0; o >>= 1) tt += __shfl_down_sync(0xffffffffu, tt, o);
+        if (lane == 0 && nv) {
+            atomicAdd(counts, (unsigned long long)nv);
+            atomicAdd(counts + 1, (unsigned long long)tt);
+        }
     }
 }
 
-__global__ void k_level_seed(int64_t r0, uint32_t n, int2* __restrict__ out) {
+__global__ void k_level_seed(int64_t r0, uint32_t n, int2* __restrict__ out, uint32_t* __restrict__ n_level0) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < n) out[j] = make_int2((int)(r0 + j), 0);
+    if (j == 0) *n_level0 = n;
 }
 
 __global__ void k_level_finish(const unsigned long long* __restrict__ best, int64_t n, int32_t* __restrict__ hit,
@@ -225,31 +235,46 @@ static rt_status nearest_impl(const rt_tree* tree, const float* org, const float
         // pair buffers: 2^26 pairs (512 MiB) each, or fewer for small queries
         const uint32_t cap = (uint32_t)std::min<int64_t>((int64_t)1 << 26, std::max<int64_t>(1 << 20, 64 * n));
         int2 *pa, *pb;
-        uint32_t* n_out;
         RR_TRY(tmp.alloc(&pa, cap));
         RR_TRY(tmp.alloc(&pb, cap));
-        RR_TRY(tmp.alloc(&n_out, 1));
+        // the levels' pair counts stay on the device: a batch of L levels is
+        // queued at once (a 4-wide tree of binary depth D has about D / 2 + 1
+        // levels) and the counts are read once per batch
+        const int L = (std::max(4, tree->depth / 2 + 3) + 1) & ~1;  // even: level L's pairs land in pa
+        uint32_t* lvl;
+        RR_TRY(tmp.alloc(&lvl, (size_t)L + 1));
+        std::vector<uint32_t> hl((size_t)L + 1);
+        const unsigned lgrid = (unsigned)(8 * device_sm_count());
         int64_t chunk = std::min<int64_t>(n, cap / 4);
         for (int64_t r0 = 0; r0 < n;) {
             const int64_t m = std::min(chunk, n - r0);
-            bool overflow = false;
-            uint32_t n_in = (uint32_t)m;
-            RR_LAUNCH(k_level_seed, (unsigned)((m + 255) / 256), 256, 0, s, r0, n_in, pa);
-            int2 *in = pa, *out = pb;
-            for (int level = 0; n_in > 0 && level < 256; level++) {
-                RR_CUDA(cudaMemsetAsync(n_out, 0, sizeof(uint32_t), s));
-                RR_LAUNCH(k_level, (unsigned)((n_in + 255) / 256), 256, 0, s, tr, rows, in, n_in, out, n_out, cap,
-                          best, counts, status);
+            bool overflow = false, done = false;
+            RR_CUDA(cudaMemsetAsync(lvl, 0, sizeof(uint32_t) * ((size_t)L + 1), s));
+            RR_LAUNCH(k_level_seed, (unsigned)((m + 255) / 256), 256, 0, s, r0, (uint32_t)m, pa, lvl);
+            int2* buf[2] = {pa, pb};
+            for (int batch = 0; batch < 64 && !done; batch++) {
+                for (int l = 0; l < L; l++)
+                    RR_LAUNCH(k_level, lgrid, 256, 0, s, tr, rows, buf[l & 1], lvl + l, buf[(l + 1) & 1], lvl + l + 1,
+                              cap, best, counts, status);
                 RR_CUDA(cudaGetLastError());
-                uint32_t nn = 0;
-                RR_CUDA(cudaMemcpyAsync(&nn, n_out, sizeof nn, cudaMemcpyDeviceToHost, s));
+                RR_CUDA(cudaMemcpyAsync(hl.data(), lvl, sizeof(uint32_t) * ((size_t)L + 1), cudaMemcpyDeviceToHost, s));
                 RR_CUDA(cudaStreamSynchronize(s));
-                if (nn > cap) {
-                    overflow = true;
+                for (int l = 1; l <= L; l++)
+                    if (hl[(size_t)l] > cap) overflow = true;
+                if (overflow) break;
+                if (hl[(size_t)L] == 0) {
+                    done = true;
                     break;
                 }
-                n_in = nn;
-                std::swap(in, out);
+                // pairs left after L levels: they are in pa, go on from there
+                hl[0] = hl[(size_t)L];
+                RR_CUDA(cudaMemsetAsync(lvl, 0, sizeof(uint32_t) * ((size_t)L + 1), s));
+                RR_CUDA(cudaMemcpyAsync(lvl, hl.data(), sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+                RR_CUDA(cudaStreamSynchronize(s));
+            }
+            if (!overflow && !done) {
+                set_error("rt_nearest_hits: the level-by-level distribution did not finish in %d levels", 64 * L);
+                return RT_ERR_INTERNAL;
             }
             if (overflow) {
                 // the chunk's pairs did not fit: split it and start it again;
