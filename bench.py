@@ -26,6 +26,11 @@ surrogate  the metric's second half: RIRs/s of the surrogate-tail pipeline
 config2    the same measurement on the closed L-room (102,400 triangles,
            1M rays x 50 bounces, 4 receivers): every ray lives to its last
            bounce, so it measures full-length traversal.
+extras     three short measurements: one iteration of the paper's scaling
+           workload at N = M = 2^20 (tree build apart), a moved listener on the
+           theatre (recorded paths replayed for 17 new receivers, against a
+           full trace; the two must agree), and the surrogate network's
+           first-layer GEMM at batch 65,536 against the BF16 peak.
 ms_step_spread  median, min and max of the timed steps (Python's garbage
            collector is off during them).
 phases_ms  medians over the timed steps (CUDA events): tree build, ray
@@ -78,6 +83,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-config2", action="store_true", help="skip the closed L-room object of the default line")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate-tail object of the default line")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the tetra 2^20, moved-listener and GEMM objects of the default line")
     ap.add_argument("--clock-log", default=None, help="keep the nvidia-smi samples of the timed region here")
     ap.add_argument("--workload", choices=["theatre", "lroom", "batched", "tetra", "trees", "gemm"], default="theatre",
                     help="theatre: the headline line; lroom: the closed L-room alone (102,400 tris, 1M rays x 50 "
@@ -593,6 +600,11 @@ def run_native(args):
             result["surrogate"] = surrogate_object(rt, torch, stream, args)
         except Exception as e:  # reported, never costs the benchmark line
             result["surrogate"] = {"error": f"{type(e).__name__}: {e}"}
+    if ws == 1 and not args.no_extras:
+        try:
+            result["extras"] = extras_object(rt, torch, stream, sc, kw, run["tree"], chosen, args.steps, dev)
+        except Exception as e:  # reported, never costs the benchmark line
+            result["extras"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         q, dt, threads = oracle_sample(sc, args.cpu_sample_rays)
         result["cpu_baseline"] = {"value": q / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -607,6 +619,92 @@ def run_native(args):
         print(json.dumps(result))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def extras_object(rt, torch, stream, sc, kw, tree, chosen, steps, dev):
+    """Three short measurements beside the headline, so that the line itself
+    carries them: the paper's scaling workload at N = M = 2^20 (one
+    iteration, tree build apart), a moved listener on the theatre (the
+    recorded paths replayed for new receivers, against a full trace with
+    them) and the surrogate network's first-layer GEMM at batch 65,536.
+    Device times from CUDA events on the launching stream, medians of
+    `steps` after two untimed calls; the traces run in the bounce-kernel
+    configuration the headline chose."""
+    import copy
+    out = {}
+    n_meas = max(steps, 3)
+    with torch.cuda.stream(stream):
+        # -- tetrahedron N = M = 2^20, one bounce -----------------------------
+        tsc = scenes.tetra(9)
+        tkw = rt.scene_args(tsc)
+        mesh = tuple(torch.as_tensor(x, device=dev) for x in (tsc.vertices, tsc.tris, tsc.material_id,
+                                                              tsc.surface_id))
+        b_ms, t_ms = [], []
+        for k in range(n_meas + 2):
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+            ttree = rt.rt_build_tree(*mesh, stream=stream)
+            e[1].record(stream)
+            isrc = rt.rt_trace(ttree, stream=stream, **tkw)
+            e[2].record(stream)
+            e[2].synchronize()
+            if k >= 2:
+                b_ms.append(e[0].elapsed_time(e[1]))
+                t_ms.append(e[1].elapsed_time(e[2]))
+        out["tetra_2p20"] = {"faces": len(tsc.tris), "rays": tsc.n_rays, "queries": int(isrc.queries),
+                             "tree_ms": statistics.median(b_ms), "iteration_ms": statistics.median(t_ms),
+                             "paper_single_core_s": 13.78}
+        del isrc, ttree
+        # -- moved listener: replay against a full trace ----------------------
+        cfg = dict(tail_rays=chosen["tail_rays"] if chosen["tail_rays"] > 0 else -1, block_size=chosen["block_size"],
+                   compaction_period=chosen["compaction_period"], stack_entries=chosen["stack_entries"])
+        first = rt.rt_trace(tree, stream=stream, **cfg, **kw)
+        moved = copy.copy(sc)
+        lo, hi = sc.vertices.min(0), sc.vertices.max(0)
+        g = np.random.default_rng(3)
+        n = len(sc.rcv_center) + 1
+        moved.rcv_center = scenes.f32(g.uniform(lo + 0.25 * (hi - lo), hi - 0.25 * (hi - lo), (n, 3)))
+        moved.rcv_radius = scenes.f32(g.uniform(0.3, 1.5, n))
+        moved.rcv_source = np.zeros(n, np.int32)
+        mkw = rt.scene_args(moved)
+        times = {"full": [], "replay": []}
+        for k in range(n_meas + 2):
+            for name, extra in (("full", {}), ("replay", {"replay": first})):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = rt.rt_trace(tree, stream=stream, **cfg, **mkw, **extra)
+                e1.record(stream)
+                e1.synchronize()
+                if k >= 2:
+                    times[name].append(e0.elapsed_time(e1))
+                if name == "replay":
+                    same = bool(torch.equal(r.hist, full_hist)) and r.n == full_n
+                else:
+                    full_hist, full_n = r.hist.clone(), r.n
+                del r
+        out["moved_listener"] = {"receivers": n, "full_trace_ms": statistics.median(times["full"]),
+                                 "replay_ms": statistics.median(times["replay"]), "identical_to_full": same}
+        del first
+        # -- the surrogate network's GEMM -------------------------------------
+        gen = torch.Generator(device="cuda").manual_seed(0)
+        A = torch.randn(65536, 960, device=dev, generator=gen).to(torch.bfloat16)
+        B = torch.randn(512, 960, device=dev, generator=gen).to(torch.bfloat16)
+        C = torch.empty((65536, 512), dtype=torch.float32, device=dev)
+        g_ms = []
+        for k in range(n_meas + 2):
+            _, ms = rt.rt_gemm_bf16(A, B, out=C, stream=stream, timed=True)
+            if k >= 2:
+                g_ms.append(ms)
+        tf = 2.0 * 65536 * 512 * 960 / (statistics.median(g_ms) * 1e-3) / 1e12
+        bf16 = None
+        p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(p):
+            bf16 = float(json.load(open(p))["bf16_tflops"])
+        out["gemm_65536x512x960"] = {"tflops": tf, "ms": statistics.median(g_ms),
+                                     "frac_of_bf16_peak": tf / bf16 if bf16 else None,
+                                     "kernel": "k_gemm_tma (TMA, tcgen05, TMEM)"}
+        del A, B, C
+    return out
 
 
 def run_batched(args):
