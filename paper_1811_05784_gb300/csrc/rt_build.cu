@@ -876,11 +876,13 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out, 
 }  // namespace rr
 
 extern "C" rt_status rt_build_tree(const rt_mesh* mesh, void* stream, rt_tree** out) {
+    rr::NvtxRange nvtx_range("rt_build_tree");
     rr::clear_error();
     return rr::build_impl(mesh, (cudaStream_t)stream, out);
 }
 
 extern "C" rt_status rt_build_tree_median(const rt_mesh* mesh, void* stream, rt_tree** out) {
+    rr::NvtxRange nvtx_range("rt_build_tree_median");
     rr::clear_error();
     return rr::build_impl(mesh, (cudaStream_t)stream, out, true);
 }

@@ -5,6 +5,7 @@
 // build, trace and histogram stages.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -18,6 +19,16 @@
 #include "../../include/roomrays.h"
 
 namespace rr {
+
+// NVTX range over one call of the C ABI, for timeline tools (nsys, ncu's
+// range filters); without a tool attached the push and pop do nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 // ---------------------------------------------------------------------------
 // errors

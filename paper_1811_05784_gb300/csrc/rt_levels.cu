@@ -313,6 +313,7 @@ static rt_status nearest_impl(const rt_tree* tree, const float* org, const float
 extern "C" rt_status rt_nearest_hits(const rt_tree* tree, const float* origins, const float* directions,
                                      const int32_t* exclude_surface, int64_t n, int32_t method, int32_t* hit,
                                      float* t, int64_t* stats, void* stream) {
+    rr::NvtxRange nvtx_range("rt_nearest_hits");
     rr::clear_error();
     return rr::nearest_impl(tree, origins, directions, exclude_surface, n, method, hit, t, stats,
                             (cudaStream_t)stream);

@@ -451,6 +451,7 @@ extern "C" rt_status rt_mlp_info(const rt_mlp* net, int32_t* n_in, int32_t* n_hi
 }
 
 extern "C" rt_status rt_mlp_forward(rt_mlp* net, const float* x, int32_t batch, float* y, void* stream) {
+    rr::NvtxRange nvtx_range("rt_mlp_forward");
     rr::clear_error();
     if (!net || !x || !y || batch < 1) {
         rr::set_error("rt_mlp_forward: need a network, device x [batch][n_in], y [batch][n_out], batch >= 1");
@@ -461,6 +462,7 @@ extern "C" rt_status rt_mlp_forward(rt_mlp* net, const float* x, int32_t batch, 
 
 extern "C" rt_status rt_mlp_gradients(rt_mlp* net, const float* x, const float* target, int32_t batch,
                                       float* loss, void* stream) {
+    rr::NvtxRange nvtx_range("rt_mlp_gradients");
     rr::clear_error();
     if (!net || !x || !target || batch < 1) {
         rr::set_error("rt_mlp_gradients: need a network, device x, target and batch >= 1");
@@ -474,6 +476,7 @@ extern "C" rt_status rt_mlp_gradients(rt_mlp* net, const float* x, const float* 
 
 extern "C" rt_status rt_mlp_train_step(rt_mlp* net, const float* x, const float* target, int32_t batch, float lr,
                                        float* loss, void* stream) {
+    rr::NvtxRange nvtx_range("rt_mlp_train_step");
     rr::clear_error();
     if (!net || !x || !target || batch < 1 || !(lr > 0)) {
         rr::set_error("rt_mlp_train_step: need a network, device x, target, batch >= 1 and lr > 0");
@@ -546,6 +549,7 @@ extern "C" rt_status rt_mlp_set_step(rt_mlp* net, int64_t step) {
 extern "C" rt_status rt_gemm_bf16(const void* A, const void* B, int32_t M, int32_t N, int32_t K, float* C,
                                   int32_t kernel, float* workspace, int64_t workspace_floats, float* ms,
                                   void* stream) {
+    rr::NvtxRange nvtx_range("rt_gemm_bf16");
     rr::clear_error();
     if (!A || !B || !C || M < 1 || N < 1 || K < 1 || K % 8 || (kernel != RT_GEMM_TMA && kernel != RT_GEMM_STAGED) ||
         workspace_floats < 0 || (workspace_floats > 0 && !workspace)) {

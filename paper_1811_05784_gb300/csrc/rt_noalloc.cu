@@ -137,6 +137,7 @@ static rt_status rir_static_impl(const double* time, const int32_t* rcv, const d
 
 extern "C" rt_status rt_rir_static(const double* time, const int32_t* rcv, const double* energy, int64_t n,
                                    int32_t n_rcv, double fs, int64_t n_bins, float* hist, void* stream) {
+    rr::NvtxRange nvtx_range("rt_rir_static");
     rr::clear_error();
     return rr::rir_static_impl(time, rcv, energy, n, n_rcv, fs, n_bins, hist, (cudaStream_t)stream);
 }

@@ -242,6 +242,7 @@ __global__ void k_pressure(const uint64_t* __restrict__ keys, int64_t n, const d
 
 extern "C" rt_status rt_room_parameters(const float* H, int32_t n_rcv, int64_t n_bins, double fs, double* out,
                                         void* stream) {
+    rr::NvtxRange nvtx_range("rt_room_parameters");
     rr::clear_error();
     if (!H || !out || n_rcv <= 0 || n_rcv > 65535 || n_bins <= 0 || !(fs > 0.0)) {
         rr::set_error("rt_room_parameters: need histograms, 0 < n_rcv <= 65535, n_bins > 0, fs > 0");
@@ -261,6 +262,7 @@ extern "C" rt_status rt_room_parameters(const float* H, int32_t n_rcv, int64_t n
 
 extern "C" rt_status rt_pressure_rir(const rt_image_sources* is, double fs, int64_t n_out, int32_t n_taps,
                                      float* out, void* stream) {
+    rr::NvtxRange nvtx_range("rt_pressure_rir");
     rr::clear_error();
     if (!is || !out || !(fs > 0.0) || n_out <= 0 || n_out > 0x7FFFFFFFll || n_taps < 3 || n_taps % 2 == 0 ||
         n_taps > (1 << 20)) {

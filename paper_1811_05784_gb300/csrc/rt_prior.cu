@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(PRIOR_THREADS) k_tail_prior(const float* __res
 
 extern "C" rt_status rt_tail_prior(const float* rates, const float* air, const float* level, int32_t n,
                                    int32_t n_nodes, float t0, float dt, int32_t n_bins, float* out, void* stream) {
+    rr::NvtxRange nvtx_range("rt_tail_prior");
     rr::clear_error();
     if (!rates || !air || !level || !out || n <= 0 || n_nodes <= 0 || n_nodes > rr::PRIOR_MAX_NODES ||
         n_bins <= 0 || !(dt > 0.0f) || !(t0 >= 0.0f) || n > 65535) {

@@ -133,6 +133,7 @@ static rt_status rir_impl(const rt_image_sources* is, double fs, double duration
 
 extern "C" rt_status rt_rir(const rt_image_sources* is, double fs, double duration, void* stream,
                             rt_response** out) {
+    rr::NvtxRange nvtx_range("rt_rir");
     rr::clear_error();
     return rr::rir_impl(is, fs, duration, (cudaStream_t)stream, out);
 }

@@ -1085,6 +1085,7 @@ using namespace rr::sur;
 extern "C" rt_status rt_surrogate_inputs(const rt_room* rooms, const double* volume, int32_t n,
                                          const rt_surrogate_trace_params* p, float* desc, float* early, float* probe,
                                          float* prior_db, float* base_db, float* X) {
+    rr::NvtxRange nvtx_range("rt_surrogate_inputs");
     rr::clear_error();
     TraceCfg t;
     RR_TRY(trace_cfg(p, t));
@@ -1098,6 +1099,7 @@ extern "C" rt_status rt_surrogate_inputs(const rt_room* rooms, const double* vol
 
 extern "C" rt_status rt_surrogate_reference(const rt_room* rooms, int32_t n, const rt_surrogate_trace_params* p,
                                             float* env, float* tail_db) {
+    rr::NvtxRange nvtx_range("rt_surrogate_reference");
     rr::clear_error();
     TraceCfg t;
     RR_TRY(trace_cfg(p, t));
@@ -1108,6 +1110,7 @@ extern "C" rt_status rt_surrogate_reference(const rt_room* rooms, int32_t n, con
 extern "C" rt_status rt_surrogate_train(const float* X, const float* tail_db, const float* desc, const float* base_db,
                                         const float* prior_db, int32_t n, const rt_surrogate_train_params* p,
                                         rt_surrogate** out) {
+    rr::NvtxRange nvtx_range("rt_surrogate_train");
     rr::clear_error();
     if (!X || !tail_db || !desc || !base_db || !prior_db || !p || !out || n < 64) {
         rr::set_error("rt_surrogate_train: need device X, tail_db, desc, base_db, prior_db, parameters, n >= 64");
@@ -1154,6 +1157,7 @@ extern "C" rt_status rt_surrogate_load(const void* buf, size_t bytes, void* stre
 
 extern "C" rt_status rt_surrogate_predict(const rt_surrogate* m, const float* X, const float* base_db, int32_t n,
                                           float* pred_db, void* stream) {
+    rr::NvtxRange nvtx_range("rt_surrogate_predict");
     rr::clear_error();
     if (!m || !X || !base_db || !pred_db || n < 1) {
         rr::set_error("rt_surrogate_predict: need a model, device X, base_db, pred_db and n >= 1");
@@ -1164,6 +1168,7 @@ extern "C" rt_status rt_surrogate_predict(const rt_surrogate* m, const float* X,
 
 extern "C" rt_status rt_surrogate_gate(const rt_surrogate* m, const float* desc, const float* X, const float* pred_db,
                                        const float* prior_db, int32_t n, int32_t* pass, float* gaps, void* stream) {
+    rr::NvtxRange nvtx_range("rt_surrogate_gate");
     rr::clear_error();
     if (!m || !desc || !X || !pred_db || !prior_db || n < 1) {
         rr::set_error("rt_surrogate_gate: need a model, device desc, X, pred_db, prior_db and n >= 1");
@@ -1174,6 +1179,7 @@ extern "C" rt_status rt_surrogate_gate(const rt_surrogate* m, const float* desc,
 
 extern "C" rt_status rt_surrogate_envelope(const float* early, const float* tail, int32_t tail_is_db, int32_t n,
                                            float* env, void* stream) {
+    rr::NvtxRange nvtx_range("rt_surrogate_envelope");
     rr::clear_error();
     if (!early || !tail || !env || n < 1) {
         rr::set_error("rt_surrogate_envelope: need device early, tail, env and n >= 1");
@@ -1187,6 +1193,7 @@ extern "C" rt_status rt_surrogate_envelope(const float* early, const float* tail
 
 extern "C" rt_status rt_rir_surrogate(const rt_room* rooms, const double* volume, int32_t n, const rt_surrogate* m,
                                       const rt_surrogate_trace_params* p, rt_response** out, int32_t* used_fallback) {
+    rr::NvtxRange nvtx_range("rt_rir_surrogate");
     rr::clear_error();
     if (!m || !out || !volume) {
         rr::set_error("rt_rir_surrogate: need a model, the room volumes and an output");

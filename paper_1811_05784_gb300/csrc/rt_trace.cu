@@ -1486,6 +1486,7 @@ static rt_status trace_batch_impl(const rt_room* rooms, int n_rooms, const rt_tr
 extern "C" rt_status rt_trace(const rt_tree* tree, const rt_sources* src, const rt_receivers* rcv,
                               const float* band_absorption, int32_t n_materials, const rt_trace_params* params,
                               rt_image_sources** out) {
+    rr::NvtxRange nvtx_range("rt_trace");
     rr::clear_error();
     if (!tree || !src || !rcv || !band_absorption) {
         rr::set_error("rt_trace: null argument");
@@ -1502,6 +1503,7 @@ extern "C" rt_status rt_trace(const rt_tree* tree, const rt_sources* src, const 
 
 extern "C" rt_status rt_trace_batch(const rt_room* rooms, int32_t n_rooms, const rt_trace_params* params,
                                     rt_image_sources** out) {
+    rr::NvtxRange nvtx_range("rt_trace_batch");
     rr::clear_error();
     return rr::trace_batch_impl(rooms, n_rooms, params, out);
 }

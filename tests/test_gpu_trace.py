@@ -544,6 +544,10 @@ def test_errors_are_reported():
     with pytest.raises(rt.RtError) as e:
         rt.rt_build_tree(sc.vertices, sc.tris, sc.material_id, neg)
     assert e.value.status == rt.RT_ERR_INVALID_ARG
+    # an empty mesh is refused before anything is launched
+    with pytest.raises(rt.RtError) as e:
+        rt.rt_build_tree(sc.vertices, np.zeros((0, 3), np.int32), np.zeros(0, np.int32), np.zeros(0, np.int32))
+    assert e.value.status == rt.RT_ERR_INVALID_ARG
 
 
 def test_sparse_surface_ids():
