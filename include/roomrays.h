@@ -119,7 +119,12 @@ typedef struct {
                               RT_TAIL_AUTOTUNE = the library times each of its candidate
                               configurations (block size, threshold, compaction period,
                               stack depth) twice on the first calls of each workload class
-                              and keeps the fastest; results do not depend on it) */
+                              and keeps the fastest; results do not depend on it.  If the
+                              environment variable RT_AUTOTUNE_CACHE names a file, the
+                              choices are read from it once per process and the file is
+                              rewritten (atomically) whenever a class is tuned; a class is
+                              the device model, the candidate list, the rooms, the tree and
+                              ray counts (powers of two) and the bounces) */
     void* stream;          /* cudaStream_t */
     /* optional device outputs for parity checks (NULL = off) */
     float* debug_t;        /* [n_bounces][n_traced] hit distance, +inf on escape */

@@ -41,6 +41,9 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <cctype>
+#include <cstdio>
+#include <unistd.h>
 
 namespace rr {
 
@@ -724,26 +727,49 @@ static void tune_load_locked() {
     fclose(f);
 }
 
+// the whole table, written to a temporary file and renamed over the cache,
+// so that another process never reads a half-written file
 static void tune_save_locked() {
     const char* path = getenv("RT_AUTOTUNE_CACHE");
     if (!path) return;
-    FILE* f = fopen(path, "w");
+    const std::string tmp = std::string(path) + ".tmp" + std::to_string((long long)getpid());
+    FILE* f = fopen(tmp.c_str(), "w");
     if (!f) return;
     for (auto& kv : g_tune)
         if (kv.second.best >= 0) fprintf(f, "%s %d\n", kv.first.c_str(), kv.second.best);
-    fclose(f);
+    if (fclose(f) != 0 || rename(tmp.c_str(), path) != 0) remove(tmp.c_str());
 }
 
+// workload class: the device model (a cache written on another GPU does not
+// apply), the candidate list's size (a changed list invalidates the stored
+// indices), rooms, and the tree size, ray count and bounce count
 static std::string tune_key(int64_t n_tris, int64_t n_traced, int B, int n_rooms) {
     int dev = 0;
     cudaGetDevice(&dev);
+    static std::mutex name_mu;
+    static std::string names[64];
+    std::string name = "unknown";
+    if (dev >= 0 && dev < 64) {
+        std::lock_guard<std::mutex> lk(name_mu);
+        if (names[dev].empty()) {
+            cudaDeviceProp prop;
+            std::string n = "unknown";
+            if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) n = prop.name;
+            cudaGetLastError();
+            for (char& c : n)
+                if (!isalnum((unsigned char)c)) c = '-';
+            names[dev] = n;
+        }
+        name = names[dev];
+    }
     auto lg = [](int64_t x) {
         int k = 0;
         while ((1ll << k) < x) k++;
         return k;
     };
-    char buf[128];
-    snprintf(buf, sizeof buf, "dev%d_rooms%d_tris2^%d_rays2^%d_b%d", dev, n_rooms, lg(n_tris), lg(n_traced), B);
+    char buf[384];
+    snprintf(buf, sizeof buf, "%s_c%d_rooms%d_tris2^%d_rays2^%d_b%d", name.c_str(), N_CANDIDATES, n_rooms,
+             lg(n_tris), lg(n_traced), B);
     return buf;
 }
 
