@@ -40,6 +40,9 @@ phases_ms  medians over the timed steps (CUDA events): tree build, ray
 cpu_baseline  the FP64 oracle (oracle/, C + numpy) on a bounded sample of the
            same workload on this host's cores; beside it the oracle's trace
            on one thread and the paper's single-core rate (Table 2).
+parity     that sample's rays traced on the GPU (the headline's
+           configuration) against the oracle: shares of identical triangle and
+           surface sequences.
 
 --impl reference runs that oracle as the reference arm.
 Under torchrun each rank traces its own ray shard of a world_size x 1M-ray
@@ -202,10 +205,10 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 # oracle (CPU) runs
 # ----------------------------------------------------------------------------
-def oracle_sample(sc, n_rays, seed=0):
+def oracle_sample(sc, n_rays, seed=0, keep=False):
     """Trace a seeded subset of the workload's rays with the FP64 oracle
     (median-split tree), build image sources and histograms; returns
-    (queries, seconds, threads)."""
+    (queries, seconds, threads), and with keep the trace and the ray ids."""
     import oracle
     rng = np.random.default_rng(seed)
     t0 = time.perf_counter()
@@ -215,7 +218,34 @@ def oracle_sample(sc, n_rays, seed=0):
     isrc = oracle.image_sources(sc, tr)
     oracle.rir(isrc, len(sc.rcv_center), sc.fs, DURATION)
     dt = time.perf_counter() - t0
+    if keep:
+        return tr.queries, dt, oracle.default_threads(), tr, ids
     return tr.queries, dt, oracle.default_threads()
+
+
+def parity_object(rt, torch, stream, sc, kw, tree, chosen, tr, ids):
+    """The GPU trace of the workload (the headline's configuration) against
+    the oracle's free-running trace of the sampled rays: shares of rays with
+    the same triangle sequence and the same surface sequence, overall and
+    among the rays the oracle finds unambiguous (no path within its edge
+    band).  Float32 and FP64 trajectories drift apart by ulps per bounce, so
+    the triangle inside one surface may differ late in a long path; the
+    tests hold the tolerances, this line reports the figures."""
+    cfg = dict(tail_rays=chosen["tail_rays"] if chosen["tail_rays"] > 0 else -1, block_size=chosen["block_size"],
+               compaction_period=chosen["compaction_period"], stack_entries=chosen["stack_entries"])
+    with torch.cuda.stream(stream):
+        isrc = rt.rt_trace(tree, stream=stream, **cfg, **kw)
+        g = isrc.hist[:, torch.as_tensor(ids, device=isrc.hist.device)].cpu().numpy().T
+    stream.synchronize()
+    o = np.asarray(tr.hist)
+    surf = np.append(np.asarray(sc.surface_id), -1)
+    same_tri = np.all(g == o, axis=1)
+    same_surf = np.all(surf[g] == surf[o], axis=1)
+    unamb = np.asarray(tr.first_amb) == tr.B
+    return {"rays": int(len(ids)), "identical_triangle_sequences": float(same_tri.mean()),
+            "identical_surface_sequences": float(same_surf.mean()), "unambiguous_rays": float(unamb.mean()),
+            "identical_triangles_among_unambiguous": float(same_tri[unamb].mean()) if unamb.any() else None,
+            "oracle": "FP64, median-split tree, free-running (oracle/rt_oracle.c)"}
 
 
 def oracle_single_thread(sc, n_rays, seed=1):
@@ -606,7 +636,12 @@ def run_native(args):
         except Exception as e:  # reported, never costs the benchmark line
             result["extras"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        q, dt, threads = oracle_sample(sc, args.cpu_sample_rays)
+        q, dt, threads, tr_o, ids_o = oracle_sample(sc, args.cpu_sample_rays, keep=True)
+        try:
+            result["parity"] = parity_object(rt, torch, stream, sc, kw, run["tree"], chosen, tr_o, ids_o)
+        except Exception as e:  # reported, never costs the benchmark line
+            result["parity"] = {"error": f"{type(e).__name__}: {e}"}
+        del tr_o
         result["cpu_baseline"] = {"value": q / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
                                   "single_thread": oracle_single_thread(sc, 20_000),
                                   "paper_single_core": {"value": 2 ** 20 / 13.78, "unit": UNIT,
