@@ -330,13 +330,15 @@ def test_reflection_counts_and_eyring_rate():
 # Sec. 1.4: histogram and decay metrics
 # ---------------------------------------------------------------------------
 def test_rir_binning():
-    isrc = oracle.ImageSources(np.array([0, 0, 1], np.int32), np.zeros(3, np.int32), np.ones(3, np.int64),
-                               np.zeros(3, np.int64), [(), (), ()], np.zeros((3, 3)), np.zeros(3),
-                               np.array([0.0, 1.5e-4, 2.0e-4]), np.ones((3, 8)))
+    """Arrival t goes to bin floor(t fs) (Sec. 1.4): arrivals 0.6 and 1.7 bins
+    into the response land in bins 0 and 1, where rounding would move them."""
+    isrc = oracle.ImageSources(np.array([0, 0, 0, 1], np.int32), np.zeros(4, np.int32), np.ones(4, np.int64),
+                               np.zeros(4, np.int64), [(), (), (), ()], np.zeros((4, 3)), np.zeros(4),
+                               np.array([0.0, 0.6e-4, 1.7e-4, 2.0e-4]), np.ones((4, 8)))
     H = oracle.rir(isrc, 2, fs=10_000.0, duration=0.001)
     assert H.shape == (2, 8, 10)
-    assert H[0, :, 0].tolist() == [1.0] * 8 and H[0, :, 1].tolist() == [1.0] * 8
-    assert H[1, :, 2].tolist() == [1.0] * 8 and H.sum() == 24
+    assert H[0, :, 0].tolist() == [2.0] * 8 and H[0, :, 1].tolist() == [1.0] * 8
+    assert H[1, :, 2].tolist() == [1.0] * 8 and H.sum() == 32
 
 
 @pytest.mark.parametrize("T", [0.5, 1.326, 3.0])

@@ -33,6 +33,23 @@ def test_parameters_of_an_exponential_decay():
         assert abs(P[6] - 10 * math.log10(1 - tail)) < 1e-9
 
 
+def test_decay_times_of_a_double_slope_decay():
+    """A Schroeder curve that falls at 60 dB/s down to -30 dB and at 20 dB/s
+    after it (the bins' energies are the differences of that curve, so its
+    backward integral gives it back): EDT (0 to -10 dB) and T20 (-5 to -25 dB)
+    fit the first slope alone and are 1 s; T30 (-5 to -35 dB) takes in the
+    second slope, so it lies strictly between the single-slope times 1 s and
+    3 s, and apart from T20."""
+    fs = 1000.0
+    t = np.arange(int(6.0 * fs) + 1) / fs
+    L = np.where(t <= 0.5, -60.0 * t, -30.0 - 20.0 * (t - 0.5))
+    S = 10.0 ** (L / 10.0)
+    e = np.append(S[:-1] - S[1:], S[-1])
+    P = post.room_parameters(e[None, None, :].repeat(8, axis=1), fs)[0, 0]
+    assert abs(P[0] - 1.0) < 1e-6 and abs(P[1] - 1.0) < 1e-6
+    assert 1.1 < P[2] < 3.0
+
+
 def test_parameters_of_edge_cases():
     fs = 1000.0
     H = np.zeros((2, 8, 100))
