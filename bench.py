@@ -5,8 +5,12 @@ Workload: the procedural open-air theatre (436,796 triangles, 20,459
 surfaces, 6 materials, ISO 9613-1 air at 20 C / 50 % RH), one source 1.6 m
 above the stage, 16 receiver spheres of radius 2 m on the tiers, 1,000,000
 Fibonacci rays x up to 30 bounces.  One step is the whole path on one batch:
-rt_build_tree (LBVH from the resident mesh) + rt_trace (rays, bounces,
-records, image sources) + rt_rir (8-band histograms, 2 s at 48 kHz).
+the tree build from the resident mesh + rt_trace (rays, bounces, records,
+image sources) + rt_rir (8-band histograms, 2 s at 48 kHz).  The builder
+is chosen per workload before the warm-up: three steps each with the plain
+LBVH (rt_build_tree) and the LBVH with SAH top levels (rt_build_tree_sah),
+the faster median step kept ("tree" and "tree_selection_ms_per_step" in
+config).
 
 value      nearest-element queries resolved (hits + escapes) per second, over
            all ranks, inputs resident in HBM, timed with CUDA events on the
@@ -82,6 +86,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--tail-rays", type=int, default=None, help="override the autotuned tail threshold")
+    ap.add_argument("--tree", choices=["auto", "lbvh", "sah_top"], default="auto",
+                    help="tree builder of the theatre and L-room steps (auto: the faster over three steps each)")
     ap.add_argument("--cpu-sample-rays", type=int, default=200_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-config2", action="store_true", help="skip the closed L-room object of the default line")
@@ -309,21 +315,28 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(name, tail):
+def profiled_traffic(name, tail, tree="lbvh"):
     """DRAM bytes per trace of the bounce kernel from a committed ncu
-    summary under profiles/, if that capture matches the current kernel
-    source and configuration (else None)."""
+    summary under profiles/, if one of its captures matches the current
+    kernel source, the configuration and the tree (else None).  A capture is
+    a block of traffic_* lines starting with traffic_bytes_per_trace; one
+    without a traffic_tree line was taken on the plain LBVH."""
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
-    kv = {}
+    blocks = []
     for line in open(path):
         if ":" in line and line.split(":")[0].startswith("traffic_"):
-            k, v = line.split(":", 1)
-            kv[k.strip()] = v.strip()
-    if kv.get("traffic_source_sha256_16") != kernel_source_sha() or kv.get("traffic_config") != f"tail_rays={tail}":
-        return None
-    return float(kv["traffic_bytes_per_trace"])
+            k, v = (x.strip() for x in line.split(":", 1))
+            if k == "traffic_bytes_per_trace":
+                blocks.append({})
+            if blocks:
+                blocks[-1][k] = v
+    for kv in blocks:
+        if (kv.get("traffic_source_sha256_16") == kernel_source_sha() and kv.get("traffic_config") == f"tail_rays={tail}"
+                and kv.get("traffic_tree", "lbvh") == tree):
+            return float(kv["traffic_bytes_per_trace"])
+    return None
 
 
 def host_cpu():
@@ -373,15 +386,22 @@ def l2_roofline(rt, torch, tree, sc, kw, chosen, bounce_ms, stream, dev, l2_peak
             "ms_per_launch_set": bounce_ms, "nodes_per_query": c[0] / n_q, "tris_per_query": c[1] / n_q}
 
 
-def timed_trace_steps(rt, torch, sc, kw, stream, tail, warmup, steps, flush, dev, duration):
+TREES = ("lbvh", "sah_top")
+
+
+def timed_trace_steps(rt, torch, sc, kw, stream, tail, warmup, steps, flush, dev, duration, tree_kind="auto"):
     """Tree build + trace + RIR per step on device-resident inputs: the
-    autotuner's trials first, then `warmup` steps, then `steps` timed steps
-    (CUDA events on the launching stream, L2 flushed before each)."""
+    autotuner's trials first; then, with tree_kind "auto", three steps with
+    each builder (rt_build_tree, rt_build_tree_sah), the faster median kept;
+    then `warmup` steps, then `steps` timed steps (CUDA events on the
+    launching stream, L2 flushed before each)."""
     V, T, Mt, St = (torch.as_tensor(x, device=dev) for x in (sc.vertices, sc.tris, sc.material_id, sc.surface_id))
     ws_trace = rt.Workspace()
+    kind = ["lbvh" if tree_kind == "auto" else tree_kind]
+    selection = {}
 
     def step(ev=None):
-        tree = rt.rt_build_tree(V, T, Mt, St, stream=stream)
+        tree = rt.rt_build_tree(V, T, Mt, St, stream=stream, sah=kind[0] == "sah_top")
         if ev is not None:
             ev[0].record(stream)
         isrc = rt.rt_trace(tree, tail_rays=tail, stream=stream, workspace=ws_trace, **kw)
@@ -402,6 +422,20 @@ def timed_trace_steps(rt, torch, sc, kw, stream, tail, warmup, steps, flush, dev
                 if cur == prev:
                     break
                 prev = cur
+        if tree_kind == "auto":  # the builder whose whole step is faster
+            for k in TREES:
+                kind[0] = k
+                t = []
+                for _ in range(3):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    step()
+                    b.record(stream)
+                    b.synchronize()
+                    t.append(a.elapsed_time(b))
+                selection[k] = statistics.median(t)
+            kind[0] = min(TREES, key=lambda k: selection[k])
         for _ in range(max(warmup, 1)):
             _, isrc_w, _ = step()
         torch.cuda.synchronize()
@@ -436,7 +470,8 @@ def timed_trace_steps(rt, torch, sc, kw, stream, tail, warmup, steps, flush, dev
         gc.enable()
         launches = rt.rt_launch_count() - launches0
     return dict(ms=ms, queries=queries, phases=phases, chosen=chosen, launches=launches, tree=tree,
-                graph=ws_trace.graph_launches > 0, ws=ws_trace, mesh=(V, T, Mt, St))
+                graph=ws_trace.graph_launches > 0, ws=ws_trace, mesh=(V, T, Mt, St), tree_kind=kind[0],
+                tree_selection_ms_per_step=selection)
 
 
 def lroom_object(rt, torch, stream, tail, args, flush, dev, l2_peak, hbm, rng_kw):
@@ -446,16 +481,17 @@ def lroom_object(rt, torch, stream, tail, args, flush, dev, l2_peak, hbm, rng_kw
     sc2 = scenes.lroom(n_rays=N_RAYS, n_bounces=50)
     kw2 = rt.scene_args(sc2)
     kw2.update(rng_kw)
-    run2 = timed_trace_steps(rt, torch, sc2, kw2, stream, tail, args.warmup, args.steps, flush, dev, 1.0)
+    run2 = timed_trace_steps(rt, torch, sc2, kw2, stream, tail, args.warmup, args.steps, flush, dev, 1.0, args.tree)
     with torch.cuda.stream(stream):
         roof2 = l2_roofline(rt, torch, run2["tree"], sc2, kw2, run2["chosen"],
                             statistics.median(run2["phases"]["bounces"]), stream, dev, l2_peak, hbm,
-                            profiled_traffic("k_bounce_lroom.md", run2["chosen"]["tail_rays"]))
+                            profiled_traffic("k_bounce_lroom.md", run2["chosen"]["tail_rays"], run2["tree_kind"]))
     t2 = sum(run2["ms"]) / 1e3
     return {"workload": f"closed L-room 102,400 tris / 8 surfaces, {N_RAYS:,} rays x 50 bounces, 4 receivers "
                         f"r=0.5 m, RIR 8 bands x 1 s at 48 kHz",
             "value": sum(run2["queries"]) / t2, "unit": UNIT, "ms_per_step": 1e3 * t2 / args.steps,
             "queries_per_step": int(statistics.median(run2["queries"])), "bounce_kernel": run2["chosen"],
+            "tree": run2["tree_kind"], "tree_selection_ms_per_step": run2["tree_selection_ms_per_step"],
             "phases_ms": {k: statistics.median(v) for k, v in run2["phases"].items()},
             "roofline": roof2, "gpu_launches": int(run2["launches"])}
 
@@ -562,7 +598,8 @@ def run_native(args):
     clk.wait_first_sample()
     if ws > 1:
         dist.barrier()
-    run = timed_trace_steps(rt, torch, sc, kw, stream, tail, args.warmup, args.steps, flush, dev, DURATION)
+    run = timed_trace_steps(rt, torch, sc, kw, stream, tail, args.warmup, args.steps, flush, dev, DURATION,
+                            args.tree)
     clk.__exit__(None, None, None)
     if ws > 1:
         dist.barrier()
@@ -583,7 +620,7 @@ def run_native(args):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            tree = rt.rt_build_tree(*host, stream=stream)
+            tree = rt.rt_build_tree(*host, stream=stream, sah=run["tree_kind"] == "sah_top")
             isrc = rt.rt_trace(tree, tail_rays=tail, stream=stream, workspace=run["ws"], **kw)
             resp = rt.rt_rir(isrc, sc.fs, duration=DURATION, stream=stream)
             resp.download(out, stream=stream)
@@ -592,7 +629,8 @@ def run_native(args):
                 e2e_ms.append(dt * 1e3)
                 e2e_q += isrc.queries
         roof = l2_roofline(rt, torch, run["tree"], sc, kw, chosen, statistics.median(run["phases"]["bounces"]),
-                           stream, dev, l2_peak, hbm, profiled_traffic("k_bounce_theatre.md", chosen["tail_rays"]))
+                           stream, dev, l2_peak, hbm,
+                           profiled_traffic("k_bounce_theatre.md", chosen["tail_rays"], run["tree_kind"]))
 
     # -- the closed L-room (config 2): full-length traversal -------------------
     cfg2 = None if args.no_config2 else lroom_object(rt, torch, stream, tail, args, flush, dev, l2_peak, hbm, rng_kw)
@@ -613,7 +651,8 @@ def run_native(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(ws), "rays_per_gpu": N_RAYS, "n_bounces": N_BOUNCES,
                    "queries_per_step_per_gpu": int(statistics.median(queries)),
-                   "bounce_kernel": chosen, "cuda_graph": run["graph"],
+                   "bounce_kernel": chosen, "cuda_graph": run["graph"], "tree": run["tree_kind"],
+                   "tree_selection_ms_per_step": run["tree_selection_ms_per_step"],
                    "l2": "flushed (256 MB write) before every timed step", "parallelism": f"ray shards x{ws}"},
         "e2e": {"value": e2e_q_all / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},

@@ -33,6 +33,7 @@ struct BuildMeta {
     int max_surf, min_surf, max_mat, min_mat;
     unsigned int bad_index, non_finite, degenerate, mixed_material;
     int depth;
+    unsigned int sah_error;  // inconsistencies found by the SAH top levels (none expected)
 };
 
 __device__ __forceinline__ unsigned int f2ord(float f) {
@@ -593,6 +594,64 @@ __global__ void k_reorder(const float4* __restrict__ tv, const uint32_t* __restr
 
 static unsigned grid_of(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+}  // namespace rr
+
+#include "rt_sah_top.cuh"
+
+namespace rr {
+
+// SAH top levels over the Morton cells of an LBVH whose boxes are refitted
+// (rt_sah_top.cuh); rewrites the top nodes' entries of the binary arrays
+static rt_status sah_top(const uint64_t* keys, int64_t M, int32_t* left, int32_t* right, int32_t* first,
+                         int32_t* last, int32_t* pint, int32_t* pleaf, const float4* leaf_box, float4* node_box,
+                         BuildMeta* meta, Arena& tmp, cudaStream_t s) {
+    const int64_t NI = M - 1;
+    uint32_t *cflag, *cid, *cell_first, *n_cells, *is_top, *top_pos, *n_top, *top_idx, *counts;
+    CellRec *rec0, *rec1;
+    SahSeg *seg_a, *seg_b, *seg_small;
+    RR_TRY(tmp.alloc(&cflag, M));
+    RR_TRY(tmp.alloc(&cid, M));
+    RR_TRY(tmp.alloc(&cell_first, M + 1));
+    RR_TRY(tmp.alloc(&n_cells, 1));
+    RR_TRY(tmp.alloc(&is_top, NI));
+    RR_TRY(tmp.alloc(&top_pos, NI));
+    RR_TRY(tmp.alloc(&n_top, 1));
+    RR_TRY(tmp.alloc(&top_idx, NI));
+    RR_TRY(tmp.alloc(&counts, SAH_LEVELS + 1));
+    RR_TRY(tmp.alloc(&rec0, M));
+    RR_TRY(tmp.alloc(&rec1, M));
+    RR_TRY(tmp.alloc(&seg_a, M));
+    RR_TRY(tmp.alloc(&seg_b, M));
+    RR_TRY(tmp.alloc(&seg_small, M));
+    void* scan_tmp;
+    RR_TRY(tmp.alloc((char**)&scan_tmp, scan_temp_bytes(M)));
+    // cells and their records (boxes from the refit)
+    RR_LAUNCH(k_cell_flags, grid_of(M, 256), 256, 0, s, keys, M, cflag);
+    RR_TRY(exclusive_scan_u32(cflag, cid, M, n_cells, scan_tmp, s));
+    RR_LAUNCH(k_cell_first, grid_of(M, 256), 256, 0, s, cflag, cid, M, cell_first);
+    RR_LAUNCH(k_cell_records, grid_of(M, 256), 256, 0, s, cell_first, n_cells, M, first, last, leaf_box, node_box,
+              rec0, meta);
+    // the Karras nodes above the cells give the top nodes their indices
+    RR_LAUNCH(k_top_flags, grid_of(NI, 256), 256, 0, s, keys, NI, first, last, is_top);
+    RR_CUDA(cudaGetLastError());
+    RR_TRY(exclusive_scan_u32(is_top, top_pos, NI, n_top, scan_tmp, s));
+    RR_LAUNCH(k_top_compact, grid_of(NI, 256), 256, 0, s, is_top, top_pos, NI, top_idx);
+    RR_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (SAH_LEVELS + 1), s));
+    SahLists li{seg_a, seg_b, seg_small, counts, rec0, rec1};
+    RR_LAUNCH(k_sah_init, 1, 1, 0, s, n_cells, n_top, li, meta);
+    for (int L = 0; L < SAH_LEVELS; L++) {
+        SahLists ll = li;
+        ll.seg_in = (L & 1) ? seg_b : seg_a;
+        ll.seg_next = (L & 1) ? seg_a : seg_b;
+        RR_LAUNCH(k_sah_level, SAH_GRID, SAH_THREADS, 0, s, L, L == SAH_LEVELS - 1, ll, top_idx, n_top, M, left,
+                  right, first, last, pint, pleaf, node_box, meta);
+    }
+    RR_LAUNCH(k_sah_small, SAH_GRID, 256, 0, s, li, top_idx, n_top, M, left, right, first, last, pint, pleaf,
+              node_box, meta);
+    RR_CUDA(cudaGetLastError());
+    return RT_OK;
+}
+
 // host grouping of triangles into surfaces by (material, plane) when the
 // caller gives no surface ids
 static std::vector<int32_t> group_surfaces(const double* V, const int32_t* T, const int32_t* mat, int64_t M) {
@@ -620,7 +679,10 @@ static std::vector<int32_t> group_surfaces(const double* V, const int32_t* T, co
     return out;
 }
 
-static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out, bool median = false) {
+enum BuildKind { BUILD_LBVH = 0, BUILD_MEDIAN = 1, BUILD_SAH_TOP = 2 };
+
+static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out, BuildKind kind = BUILD_LBVH) {
+    const bool median = kind == BUILD_MEDIAN;
     if (!mesh || !out) {
         set_error("rt_build_tree: null argument");
         return RT_ERR_INVALID_ARG;
@@ -691,6 +753,7 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out, 
     hm.max_surf = INT_MIN, hm.min_surf = INT_MAX, hm.max_mat = INT_MIN, hm.min_mat = INT_MAX;
     hm.bad_index = hm.non_finite = hm.degenerate = hm.mixed_material = 0;
     hm.depth = 0;
+    hm.sah_error = 0;
     RR_CUDA(cudaMemcpyAsync(meta, &hm, sizeof hm, cudaMemcpyHostToDevice, s));
 
     float4 *tv, *tri_nrm;
@@ -773,6 +836,8 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out, 
             RR_LAUNCH(k_median_topology, grid_of(NI, 256), 256, 0, s, M, left, right, first, last, pint, pleaf);
         RR_LAUNCH(k_leaf_boxes, grid_of(M, 256), 256, 0, s, tv, vals, M, leaf_box);
         RR_LAUNCH(k_refit, grid_of(M, 256), 256, 0, s, M, left, right, pint, pleaf, leaf_box, node_box, flags);
+        if (kind == BUILD_SAH_TOP)
+            RR_TRY(sah_top(keys, M, left, right, first, last, pint, pleaf, leaf_box, node_box, meta, tmp, s));
         RR_LAUNCH(k_depth, grid_of(M, 256), 256, 0, s, M, pint, pleaf, meta);
         RR_LAUNCH(k_keep, grid_of(NI, 256), 256, 0, s, NI, first, last, keep);
         RR_LAUNCH(k_keep4, grid_of(NI, 256), 256, 0, s, NI, pint, keep, keep4);
@@ -816,6 +881,10 @@ static rt_status build_impl(const rt_mesh* mesh, cudaStream_t s, rt_tree** out, 
     if (hm.bad_index) {
         set_error("rt_build_tree: %u triangles index vertices out of range", hm.bad_index);
         return RT_ERR_INVALID_ARG;
+    }
+    if (hm.sah_error) {
+        set_error("rt_build_tree_sah: %u inconsistencies in the top levels", hm.sah_error);
+        return RT_ERR_INTERNAL;
     }
     if (hm.non_finite) {
         set_error("rt_build_tree: %u triangles have non-finite coordinates", hm.non_finite);
@@ -884,7 +953,13 @@ extern "C" rt_status rt_build_tree(const rt_mesh* mesh, void* stream, rt_tree** 
 extern "C" rt_status rt_build_tree_median(const rt_mesh* mesh, void* stream, rt_tree** out) {
     rr::NvtxRange nvtx_range("rt_build_tree_median");
     rr::clear_error();
-    return rr::build_impl(mesh, (cudaStream_t)stream, out, true);
+    return rr::build_impl(mesh, (cudaStream_t)stream, out, rr::BUILD_MEDIAN);
+}
+
+extern "C" rt_status rt_build_tree_sah(const rt_mesh* mesh, void* stream, rt_tree** out) {
+    rr::NvtxRange nvtx_range("rt_build_tree_sah");
+    rr::clear_error();
+    return rr::build_impl(mesh, (cudaStream_t)stream, out, rr::BUILD_SAH_TOP);
 }
 
 extern "C" void rt_tree_free(rt_tree* tree) {

@@ -27,7 +27,7 @@ RT_MEM_HOST, RT_MEM_DEVICE = 0, 1
 
 RT_TAIL_AUTOTUNE = -2
 
-EXPORTED = ["rt_build_tree", "rt_build_tree_median", "rt_tree_free", "rt_tree_info", "rt_trace", "rt_trace_batch", "rt_image_sources_view",
+EXPORTED = ["rt_build_tree", "rt_build_tree_median", "rt_build_tree_sah", "rt_tree_free", "rt_tree_info", "rt_trace", "rt_trace_batch", "rt_image_sources_view",
             "rt_workspace_create", "rt_workspace_free", "rt_workspace_graph_launches",
             "rt_image_sources_free", "rt_rir", "rt_rir_static", "rt_response_get", "rt_response_download",
             "rt_response_free",
@@ -163,6 +163,8 @@ def lib():
             L.rt_build_tree.argtypes = [C.POINTER(rt_mesh), P, C.POINTER(P)]
             L.rt_build_tree_median.restype = st
             L.rt_build_tree_median.argtypes = [C.POINTER(rt_mesh), P, C.POINTER(P)]
+            L.rt_build_tree_sah.restype = st
+            L.rt_build_tree_sah.argtypes = [C.POINTER(rt_mesh), P, C.POINTER(P)]
             L.rt_tree_free.argtypes = [P]
             L.rt_tree_info.restype = st
             L.rt_tree_info.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
@@ -407,10 +409,13 @@ class Tree:
     __del__ = free
 
 
-def rt_build_tree(vertices, tris, material_id, surface_id=None, stream=None, median=False) -> Tree:
+def rt_build_tree(vertices, tris, material_id, surface_id=None, stream=None, median=False, sah=False) -> Tree:
     """Build the LBVH of a triangle mesh (host numpy / CPU tensors or CUDA
     tensors); median=True builds the paper's median-split tree instead
-    (rt_build_tree_median)."""
+    (rt_build_tree_median), sah=True the LBVH with SAH top levels
+    (rt_build_tree_sah)."""
+    if median and sah:
+        raise ValueError("rt_build_tree: median and sah exclude each other")
     dev = _is_cuda_tensor(vertices)
     keep = []
     if dev:
@@ -433,7 +438,7 @@ def rt_build_tree(vertices, tris, material_id, surface_id=None, stream=None, med
         keep += [v, t, m, s]
         mesh = rt_mesh(pv, len(v), pt, len(t), pm, ps, RT_MEM_HOST)
     out = P()
-    fn = lib().rt_build_tree_median if median else lib().rt_build_tree
+    fn = lib().rt_build_tree_median if median else (lib().rt_build_tree_sah if sah else lib().rt_build_tree)
     _check(fn(C.byref(mesh), _stream_ptr(stream), C.byref(out)))
     return Tree(out)
 

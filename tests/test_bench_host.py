@@ -91,3 +91,23 @@ def test_reference_arm_prints_nothing_on_other_ranks():
     env = dict(os.environ, RANK="1", LOCAL_RANK="1", WORLD_SIZE="2")
     assert _bench_lines(["--impl", "reference", "--steps", "1", "--warmup", "0", "--cpu-sample-rays", "2000"],
                         env=env) == []
+
+
+def test_profiled_traffic_picks_the_capture_of_the_tree(tmp_path, monkeypatch):
+    """A profile may hold one capture per tree; a block without traffic_tree
+    was taken on the plain LBVH; a stale source or another configuration
+    gives None."""
+    bench = _bench()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "k.md").write_text(
+        "# summary\n\ntraffic_bytes_per_trace: 100\ntraffic_config: tail_rays=7\ntraffic_source_sha256_16: abc\n\n"
+        "traffic_bytes_per_trace: 80\ntraffic_config: tail_rays=7\ntraffic_source_sha256_16: abc\n"
+        "traffic_tree: sah_top\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "abc")
+    assert bench.profiled_traffic("k.md", 7) == 100.0
+    assert bench.profiled_traffic("k.md", 7, "sah_top") == 80.0
+    assert bench.profiled_traffic("k.md", 8, "sah_top") is None
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "def")
+    assert bench.profiled_traffic("k.md", 7) is None
