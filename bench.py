@@ -783,7 +783,8 @@ def extras_object(rt, torch, stream, sc, kw, tree, chosen, steps, dev):
 
 def run_batched(args):
     """64 seeded rooms of 12 to 182,400 triangles, 16 source / receiver pairs
-    each, 262,144 rays per pair, 30 bounces: every step builds the 64 trees and
+    each, 262,144 rays per pair, 30 bounces: every step builds the 64 trees
+    (the builder chosen by one step with each, as for the theatre) and
     traces all 268M rays of all rooms in one batched trace (its bounce loop one
     CUDA graph of persistent launches, configuration autotuned), followed by
     the 8-band RIRs of all 1,024 receivers.  --batch-chunk splits the rays of
@@ -799,9 +800,11 @@ def run_batched(args):
     mesh = [tuple(torch.as_tensor(x, device=dev) for x in (r.vertices, r.tris, r.material_id, r.surface_id))
             for r in rooms_sc]
     chunk = min(args.batch_chunk, n_rays)
+    kind = ["lbvh" if args.tree == "auto" else args.tree]
+    selection = {}
 
     def step():
-        trees = [rt.rt_build_tree(*m, stream=stream) for m in mesh]
+        trees = [rt.rt_build_tree(*m, stream=stream, sah=kind[0] == "sah_top") for m in mesh]
         rooms = [dict(tree=t, sources=r.sources, rcv_center=r.rcv_center, rcv_radius=r.rcv_radius,
                       rcv_source=r.rcv_source, band_absorption=r.alpha) for t, r in zip(trees, rooms_sc)]
         q, cfg = 0, None
@@ -832,6 +835,16 @@ def run_batched(args):
                 break
             prev = cur
         del trees, rooms
+        if args.tree == "auto":  # the builder whose whole step is faster (one step each)
+            for k in TREES:
+                kind[0] = k
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                step()
+                b.record(stream)
+                b.synchronize()
+                selection[k] = a.elapsed_time(b)
+            kind[0] = min(TREES, key=lambda k: selection[k])
         for _ in range(max(args.warmup, 1)):
             step()
         torch.cuda.synchronize()
@@ -857,6 +870,7 @@ def run_batched(args):
                                f"{len(rooms_sc[0].sources)} pairs x {n_rays} rays x {B} bounces, receivers r=0.5 m",
                    "rays_per_trace_per_pair": chunk, "traces_per_step": -(-n_rays // chunk),
                    "bounce_kernel": cfg, "queries_per_step": statistics.mean(queries),
+                   "tree": kind[0], "tree_selection_ms_per_step": selection,
                    "step": "64 tree builds + batched traces + RIRs", "l2": "inputs larger than L2"},
         "gpu_launches": launches, "clocks": clk.summary()}))
 
