@@ -315,12 +315,25 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
+def tree_source_sha():
+    """First 16 hex digits of the SHA-256 of the tree builder's sources
+    (rt_build.cu followed by rt_sah_top.cuh): a capture on the SAH-top tree
+    holds for this builder only."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("rt_build.cu", "rt_sah_top.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1811_05784_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profiled_traffic(name, tail, tree="lbvh"):
     """DRAM bytes per trace of the bounce kernel from a committed ncu
     summary under profiles/, if one of its captures matches the current
     kernel source, the configuration and the tree (else None).  A capture is
     a block of traffic_* lines starting with traffic_bytes_per_trace; one
-    without a traffic_tree line was taken on the plain LBVH."""
+    without a traffic_tree line was taken on the plain LBVH, and a capture on
+    the SAH-top tree holds only for the builder source it names
+    (traffic_tree_source_sha256_16)."""
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
@@ -333,8 +346,10 @@ def profiled_traffic(name, tail, tree="lbvh"):
             if blocks:
                 blocks[-1][k] = v
     for kv in blocks:
+        tree_sha = kv.get("traffic_tree_source_sha256_16")
         if (kv.get("traffic_source_sha256_16") == kernel_source_sha() and kv.get("traffic_config") == f"tail_rays={tail}"
-                and kv.get("traffic_tree", "lbvh") == tree):
+                and kv.get("traffic_tree", "lbvh") == tree
+                and (tree == "lbvh" or tree_sha == tree_source_sha())):
             return float(kv["traffic_bytes_per_trace"])
     return None
 

@@ -55,16 +55,18 @@
 // BuildMeta::sah_error and fail the build; every write checks its index.
 //
 // Measured on one GB300 against rt_build_tree: the theatre (436,796
-// triangles) visits 16.3 instead of 19.6 nodes per query and its bounce loop
-// takes 2.51 instead of 2.83 ms; the closed L-room 12.6 instead of 14.7 and
-// 11.2 instead of 15.2 ms.  The build takes 1.6-1.8 ms instead of 0.3-0.5:
+// triangles) visits 15.7 instead of 19.6 nodes per query and its bounce loop
+// takes 2.43 instead of 2.83 ms; the closed L-room 12.5 instead of 14.7 and
+// 10.3 instead of 15.2 ms.  The build takes 2.0-3.0 ms instead of 0.3-0.5:
 // the top levels run one block per segment, so the first ones use few SMs.
+// Cells of 21 bits build in 1.6-1.8 ms but leave 16.3 and 12.6 nodes per
+// query; of 27 bits, 4.8 ms for the theatre and no fewer nodes.
 
 #pragma once
 
 namespace rr {
 
-static constexpr int CELL_BITS = 21;      // 7 bits per axis: 128^3 cells
+static constexpr int CELL_BITS = 24;      // 8 bits per axis: 256^3 cells
 static constexpr int SAH_BINS = 16;       // per axis
 static constexpr int SAH_SMALL = 32;      // segments up to this size go to the warp kernel
 static constexpr int SAH_LEVELS = 14;     // block-per-segment levels

@@ -103,11 +103,16 @@ def test_profiled_traffic_picks_the_capture_of_the_tree(tmp_path, monkeypatch):
     (prof / "k.md").write_text(
         "# summary\n\ntraffic_bytes_per_trace: 100\ntraffic_config: tail_rays=7\ntraffic_source_sha256_16: abc\n\n"
         "traffic_bytes_per_trace: 80\ntraffic_config: tail_rays=7\ntraffic_source_sha256_16: abc\n"
-        "traffic_tree: sah_top\n")
+        "traffic_tree: sah_top\ntraffic_tree_source_sha256_16: 123\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "kernel_source_sha", lambda: "abc")
+    monkeypatch.setattr(bench, "tree_source_sha", lambda: "123")
     assert bench.profiled_traffic("k.md", 7) == 100.0
     assert bench.profiled_traffic("k.md", 7, "sah_top") == 80.0
     assert bench.profiled_traffic("k.md", 8, "sah_top") is None
+    # an SAH-top capture holds for the builder source it was taken with only
+    monkeypatch.setattr(bench, "tree_source_sha", lambda: "456")
+    assert bench.profiled_traffic("k.md", 7, "sah_top") is None
+    assert bench.profiled_traffic("k.md", 7) == 100.0
     monkeypatch.setattr(bench, "kernel_source_sha", lambda: "def")
     assert bench.profiled_traffic("k.md", 7) is None
