@@ -99,7 +99,7 @@ def parse():
                     help="theatre: the headline line; lroom: the closed L-room alone (102,400 tris, 1M rays x 50 "
                          "bounces); batched: 64 rooms x 16 pairs x 262,144 rays x 30 bounces "
                          "in batched launches; tetra: the N = M scaling sweep of one iteration on the refined "
-                         "tetrahedron; trees: the LBVH against the paper's median-split tree "
+                         "tetrahedron; trees: the LBVH against the paper's median-split tree and the SAH top "
                          "(each its own line, one GPU)")
     ap.add_argument("--batch-chunk", type=int, default=262_144,
                     help="rays per pair per batched trace (default: all of them, one trace per step)")
@@ -958,9 +958,10 @@ def run_tetra(args):
 
 
 def run_trees(args):
-    """The LBVH against the paper's median-split tree on the same meshes and
-    rays: build time, node visits and triangle tests per query, bounce-loop
-    time (the same 4-wide traversal kernel); and for the first bounce's
+    """The LBVH against the paper's median-split tree and the LBVH with SAH
+    top levels on the same meshes and rays: build time, node visits and
+    triangle tests per query, bounce-loop time (the same 4-wide traversal
+    kernel); and for the first bounce's
     queries the per-ray stack traversal against the paper's level-by-level
     distribution of rays through the tree (rt_nearest_hits): time, node
     visits, triangle tests and the bytes they read."""
@@ -976,17 +977,18 @@ def run_trees(args):
         sc = make()
         kw = rt.scene_args(sc)
         mesh = tuple(torch.as_tensor(x, device=dev) for x in (sc.vertices, sc.tris, sc.material_id, sc.surface_id))
-        for median in (False, True):
+        for kind in ("lbvh", "median", "sah_top"):
+            build = dict(median=kind == "median", sah=kind == "sah_top")
             with torch.cuda.stream(stream):
                 for _ in range(max(args.warmup, 1)):
-                    tree = rt.rt_build_tree(*mesh, stream=stream, median=median)
+                    tree = rt.rt_build_tree(*mesh, stream=stream, **build)
                     rt.rt_trace(tree, tail_rays=N_RAYS, block_size=256, stream=stream, **kw)
                 torch.cuda.synchronize()
                 b_ms, q_ms = [], []
                 for _ in range(args.steps):
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
-                    tree = rt.rt_build_tree(*mesh, stream=stream, median=median)
+                    tree = rt.rt_build_tree(*mesh, stream=stream, **build)
                     e1.record(stream)
                     isrc = rt.rt_trace(tree, tail_rays=N_RAYS, block_size=256, stream=stream, **kw)
                     torch.cuda.synchronize()
@@ -998,7 +1000,8 @@ def run_trees(args):
                 c = cost.double().sum((0, 1)).cpu().numpy()
                 del cost
             info = tree.info()
-            row = {"mesh": name, "tris": len(sc.tris), "tree": "median split" if median else "LBVH",
+            row = {"mesh": name, "tris": len(sc.tris),
+                   "tree": {"lbvh": "LBVH", "median": "median split", "sah_top": "LBVH + SAH top"}[kind],
                    "depth": info["depth"], "wide_nodes": info["n_nodes"], "build_ms": statistics.median(b_ms),
                    "bounce_ms": statistics.median(q_ms), "queries": isrc.queries,
                    "nodes_per_query": c[0] / isrc.queries, "tris_per_query": c[1] / isrc.queries}
