@@ -228,8 +228,8 @@ rt_status rt_build_tree_median(const rt_mesh* mesh, void* stream, rt_tree** out)
  * area(left box) x triangles(left) + area(right box) x triangles(right),
  * over 16 bins of the cell centres per axis for large nodes and along the
  * Morton order for nodes of at most 32 cells.  No host synchronisation is
- * added; the build takes a few times as long as rt_build_tree's (2-3 ms
- * against 0.3-0.5 ms at 10^5-10^6 triangles), and a trace visits 15-20 %
+ * added; the build takes a few times as long as rt_build_tree's (1.7-2.6 ms
+ * against 0.3-0.8 ms at 10^5-10^6 triangles), and a trace visits 15-35 %
  * fewer nodes, so it pays where traces are long or the tree is reused.
  * Traces give the same results on either tree.  Same arguments and
  * ownership as rt_build_tree; errors as rt_build_tree, plus RT_ERR_INTERNAL

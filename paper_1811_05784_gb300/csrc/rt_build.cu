@@ -623,6 +623,24 @@ static rt_status sah_top(const uint64_t* keys, int64_t M, int32_t* left, int32_t
     RR_TRY(tmp.alloc(&seg_a, M));
     RR_TRY(tmp.alloc(&seg_b, M));
     RR_TRY(tmp.alloc(&seg_small, M));
+    SahSeg *mid_a, *mid_b;
+    uint32_t* counts_mid;
+    RR_TRY(tmp.alloc(&mid_a, M));
+    RR_TRY(tmp.alloc(&mid_b, M));
+    RR_TRY(tmp.alloc(&counts_mid, SAH_LEVELS));
+    // the grid-wide first levels: at most C / WIDE_MIN segments of more than WIDE_MIN cells
+    const int64_t wcap = M / WIDE_MIN + 2, wchunks = (M + WIDE_CHUNK - 1) / WIDE_CHUNK + wcap;
+    SahSeg *wseg_a, *wseg_b;
+    uint32_t *wcounts, *chunk_left;
+    unsigned int *wbin_a, *wbin_b;
+    int4* wsplit;
+    RR_TRY(tmp.alloc(&wseg_a, wcap));
+    RR_TRY(tmp.alloc(&wseg_b, wcap));
+    RR_TRY(tmp.alloc(&wcounts, WIDE_LEVELS + 1));
+    RR_TRY(tmp.alloc(&wbin_a, 12 * wcap));
+    RR_TRY(tmp.alloc(&wbin_b, 12 * wcap));
+    RR_TRY(tmp.alloc(&wsplit, wcap));
+    RR_TRY(tmp.alloc(&chunk_left, wchunks));
     void* scan_tmp;
     RR_TRY(tmp.alloc((char**)&scan_tmp, scan_temp_bytes(M)));
     // cells and their records (boxes from the refit)
@@ -637,14 +655,35 @@ static rt_status sah_top(const uint64_t* keys, int64_t M, int32_t* left, int32_t
     RR_TRY(exclusive_scan_u32(is_top, top_pos, NI, n_top, scan_tmp, s));
     RR_LAUNCH(k_top_compact, grid_of(NI, 256), 256, 0, s, is_top, top_pos, NI, top_idx);
     RR_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (SAH_LEVELS + 1), s));
-    SahLists li{seg_a, seg_b, seg_small, counts, rec0, rec1};
-    RR_LAUNCH(k_sah_init, 1, 1, 0, s, n_cells, n_top, li, meta);
+    RR_CUDA(cudaMemsetAsync(wcounts, 0, sizeof(uint32_t) * (WIDE_LEVELS + 1), s));
+    RR_CUDA(cudaMemsetAsync(counts_mid, 0, sizeof(uint32_t) * SAH_LEVELS, s));
+    SahLists li{seg_a, seg_b, seg_small, counts, rec0, rec1, mid_a, mid_b, counts_mid};
+    SahWide wi{wseg_a, wseg_b, wcounts, wbin_a, wbin_b, wsplit, chunk_left, (uint32_t)wcap};
+    RR_LAUNCH(k_sah_init, 1, 1, 0, s, n_cells, n_top, li, wi, meta);
+    const unsigned wgrid = (unsigned)std::min<int64_t>(wchunks, SAH_GRID);
     for (int L = 0; L < SAH_LEVELS; L++) {
         SahLists ll = li;
         ll.seg_in = (L & 1) ? seg_b : seg_a;
         ll.seg_next = (L & 1) ? seg_a : seg_b;
-        RR_LAUNCH(k_sah_level, SAH_GRID, SAH_THREADS, 0, s, L, L == SAH_LEVELS - 1, ll, top_idx, n_top, M, left,
-                  right, first, last, pint, pleaf, node_box, meta);
+        ll.mid_in = (L & 1) ? mid_b : mid_a;
+        ll.mid_next = (L & 1) ? mid_a : mid_b;
+        if (L < WIDE_LEVELS) {  // this level's wide segments, split by the whole grid
+            SahWide wl = wi;
+            wl.in = (L & 1) ? wseg_b : wseg_a;
+            wl.next = (L & 1) ? wseg_a : wseg_b;
+            wl.bin = (L & 1) ? wbin_b : wbin_a;
+            wl.bnext = (L & 1) ? wbin_a : wbin_b;
+            RR_LAUNCH(k_wide_bounds, wgrid, WIDE_THREADS, 0, s, L, wl, rec0, rec1);
+            RR_LAUNCH(k_wide_decide, (unsigned)std::min<int64_t>(wcap, 152), WIDE_DECIDE_THREADS, 0, s, L, wl, rec0, rec1,
+                      top_idx, M, first, last, node_box);
+            RR_LAUNCH(k_wide_count, wgrid, WIDE_THREADS, 0, s, L, wl, rec0, rec1);
+            RR_LAUNCH(k_wide_scatter, wgrid, WIDE_THREADS, 0, s, L, wl, rec0, rec1, meta);
+            RR_LAUNCH(k_wide_children, 1, 1, 0, s, L, wl, ll, top_idx, n_top, M, left, right, pint, pleaf, meta);
+        }
+        RR_LAUNCH((k_sah_level<SAH_THREADS, false>), SAH_GRID, SAH_THREADS, 0, s, L, L == SAH_LEVELS - 1, ll, top_idx,
+                  n_top, M, left, right, first, last, pint, pleaf, node_box, meta);
+        RR_LAUNCH((k_sah_level<SAH_MID_THREADS, true>), SAH_MID_GRID, SAH_MID_THREADS, 0, s, L, L == SAH_LEVELS - 1, ll,
+                  top_idx, n_top, M, left, right, first, last, pint, pleaf, node_box, meta);
     }
     RR_LAUNCH(k_sah_small, SAH_GRID, 256, 0, s, li, top_idx, n_top, M, left, right, first, last, pint, pleaf,
               node_box, meta);

@@ -35,8 +35,13 @@
 // those of the cells after the partitions, which every segment knows.
 //
 // Construction, with no host synchronisation:
-//   * SAH_LEVELS launches of k_sah_level, one thread block per segment of
-//     more than SAH_SMALL cells: the block bins the cells' box centres
+//   * in the first WIDE_LEVELS levels, a segment of more than WIDE_MIN cells
+//     is split by the whole grid (k_wide_*, at the end of this file);
+//   * SAH_LEVELS launches of k_sah_level for the others, one thread block per
+//     segment of more than SAH_SMALL cells (blocks of SAH_THREADS, or of
+//     SAH_MID_THREADS for segments of at most SAH_MID cells, so that the
+//     many small segments of the deep levels find blocks to run on): the
+//     block bins the cells' box centres
 //     (SAH_BINS bins per axis over the centre bounds; counts and boxes in
 //     shared memory, combined per warp first; a segment of more than
 //     SAH_SAMPLE cells bins that many evenly spaced ones and counts its left
@@ -56,11 +61,13 @@
 //
 // Measured on one GB300 against rt_build_tree: the theatre (436,796
 // triangles) visits 15.7 instead of 19.6 nodes per query and its bounce loop
-// takes 2.43 instead of 2.83 ms; the closed L-room 12.5 instead of 14.7 and
-// 10.3 instead of 15.2 ms.  The build takes 2.0-3.0 ms instead of 0.3-0.5:
-// the top levels run one block per segment, so the first ones use few SMs.
-// Cells of 21 bits build in 1.6-1.8 ms but leave 16.3 and 12.6 nodes per
-// query; of 27 bits, 4.8 ms for the theatre and no fewer nodes.
+// takes 2.4 instead of 2.9 ms; the closed L-room 12.5 instead of 14.7 and
+// 10.4 instead of 15.4 ms.  The build takes 1.7-2.6 ms instead of 0.3-0.8
+// (one block per top-level segment: 2.0-4.2 ms): the latency of the deep
+// levels' many small segments is what remains.
+// With one block per top-level segment, cells of 21 bits built in 1.6-1.8 ms
+// but left 16.3 and 12.6 nodes per query; cells of 27 bits took 4.8 ms for
+// the theatre and left no fewer nodes than 24 bits.
 
 #pragma once
 
@@ -72,9 +79,12 @@ static constexpr int SAH_SMALL = 32;      // segments up to this size go to the 
 static constexpr int SAH_LEVELS = 14;     // block-per-segment levels
 static constexpr int SAH_SAMPLE = 4096;   // larger segments bin this many evenly spaced cells
 static constexpr int SAH_MAX_DEPTH = 26;  // from this depth of the top part on, only middle splits
-static constexpr int SAH_THREADS = 256;
+static constexpr int SAH_THREADS = 256;   // blocks for segments of more than SAH_MID cells
+static constexpr int SAH_MID = 1024;      // segments up to this size run on blocks of SAH_MID_THREADS
+static constexpr int SAH_MID_THREADS = 64;
 static constexpr int SAH_UNROLL = 4;      // records in flight per thread and pass
 static constexpr int SAH_GRID = 1216;     // 8 blocks per SM on 152 SMs; blocks loop over segments
+static constexpr int SAH_MID_GRID = 4864; // 32 blocks per SM
 
 // a cell in segment order: box, its subtree root (lo.w), its triangle count (hi.w)
 struct CellRec {
@@ -87,12 +97,26 @@ struct SahSeg {
     int16_t depth, buf;
 };
 
-// counts[0..SAH_LEVELS - 1]: large segments per level; counts[SAH_LEVELS]: small ones
+// counts[0..SAH_LEVELS - 1]: segments of more than SAH_MID cells per level;
+// counts[SAH_LEVELS]: segments of at most SAH_SMALL; counts_mid: the others
 struct SahLists {
     SahSeg *seg_in, *seg_next, *seg_small;
     uint32_t* counts;
     CellRec *rec0, *rec1;
+    SahSeg *mid_in, *mid_next;
+    uint32_t* counts_mid;
 };
+
+// queues a segment of at least two cells for the next level (by its size) or the warp kernel
+__device__ __forceinline__ void sah_queue(const SahLists& li, int level, bool last_level, const SahSeg& c) {
+    const uint32_t m = c.end - c.begin;
+    if (last_level || m <= (uint32_t)SAH_SMALL)
+        li.seg_small[atomicAdd(&li.counts[SAH_LEVELS], 1u)] = c;
+    else if (m > (uint32_t)SAH_MID)
+        li.seg_next[atomicAdd(&li.counts[level + 1], 1u)] = c;
+    else
+        li.mid_next[atomicAdd(&li.counts_mid[level + 1], 1u)] = c;
+}
 
 __device__ __forceinline__ uint32_t cell_key(uint64_t code) { return (uint32_t)(code >> (48 - CELL_BITS)); }
 
@@ -158,31 +182,6 @@ __global__ void k_top_compact(const uint32_t* __restrict__ is_top, const uint32_
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NI) return;
     if (is_top[i]) top_idx[pos[i]] = (uint32_t)i;
-}
-
-// the root segment when there are at least two cells; a top-node count other
-// than C - 1 is reported and nothing is built
-__global__ void k_sah_init(const uint32_t* __restrict__ n_cells_p, const uint32_t* __restrict__ n_top_p,
-                           SahLists li, BuildMeta* meta) {
-    const uint32_t C = *n_cells_p;
-    if (C < 2) return;
-    if (*n_top_p != C - 1) {
-        atomicAdd(&meta->sah_error, 1u);
-        return;
-    }
-    SahSeg s;
-    s.begin = 0;
-    s.end = C;
-    s.node = 0;
-    s.depth = 0;
-    s.buf = 0;
-    if (C > (uint32_t)SAH_SMALL) {
-        li.seg_in[0] = s;
-        li.counts[0] = 1u;
-    } else {
-        li.seg_small[0] = s;
-        li.counts[SAH_LEVELS] = 1u;
-    }
 }
 
 __device__ __forceinline__ float box_area(float lx, float ly, float lz, float hx, float hy, float hz) {
@@ -255,27 +254,134 @@ __device__ __forceinline__ int sah_bin(float c, float lo, float scale) {
     return min(SAH_BINS - 1, max(0, (int)((c - lo) * scale)));
 }
 
-// one level: one block per segment of more than SAH_SMALL cells
-__global__ void __launch_bounds__(SAH_THREADS)
+// shared-memory state of one block's binned SAH
+struct SahBins {
+    unsigned int lo[3][SAH_BINS][3], hi[3][SAH_BINS][3];  // bin boxes, order-preserving bits
+    unsigned int tri[3][SAH_BINS], cel[3][SAH_BINS];
+    float cost[3];
+    int split[3];
+    unsigned int nl[3];
+};
+
+// Bins the centres of the cells [begin, begin + n) of rin -- an even sample of
+// SAH_SAMPLE of them when n is larger -- and picks the SAH split: the axis (-1
+// when every centre is equal), the last bin of the left side, and the left
+// side's cell count (exact when nothing was sampled).  Every thread of a block
+// of T threads calls it with the same centre bounds (clo, ext, scale).
+template <int T>
+__device__ __forceinline__ void sah_choose(SahBins& sb, const CellRec* __restrict__ rin, uint32_t begin, uint32_t n,
+                                           const float* clo, const float* ext, const float* scale, int& axis,
+                                           int& split, uint32_t& nl) {
+    constexpr int U = SAH_UNROLL;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int t = tid; t < 3 * SAH_BINS; t += T) {  // empty bins
+        const int k = t / SAH_BINS, b = t % SAH_BINS;
+        sb.tri[k][b] = sb.cel[k][b] = 0u;
+        for (int d = 0; d < 3; d++) sb.lo[k][b][d] = f2ord(INFINITY), sb.hi[k][b][d] = f2ord(-INFINITY);
+    }
+    __syncthreads();
+    // bins of the three axes (triangles for the cost, cells for the
+    // partition).  Cells in Morton order are neighbours, so a warp's cells
+    // mostly share bins: the lanes of one bin combine their values first
+    // and one of them updates the bin.
+    const bool sampled = n > (uint32_t)SAH_SAMPLE;
+    const uint32_t nb = sampled ? (uint32_t)SAH_SAMPLE : n;
+    for (uint32_t i0 = tid; i0 < nb + (uint32_t)tid; i0 += T * U) {
+        float4 lo[U], hi[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t i = i0 + u * T;
+            const uint32_t k = begin + (sampled ? (uint32_t)(((uint64_t)i * n) / SAH_SAMPLE) : i);
+            if (i < nb) lo[u] = rin[k].lo, hi[u] = rin[k].hi;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const bool inr = i0 + u * T < nb;
+            const unsigned int act = __ballot_sync(0xffffffffu, inr);
+            if (!inr) continue;
+            const float cen[3] = {0.5f * (lo[u].x + hi[u].x), 0.5f * (lo[u].y + hi[u].y),
+                                  0.5f * (lo[u].z + hi[u].z)};
+            const unsigned int nt = (unsigned int)__float_as_int(hi[u].w);
+            const unsigned int o[6] = {f2ord(lo[u].x), f2ord(lo[u].y), f2ord(lo[u].z),
+                                       f2ord(hi[u].x), f2ord(hi[u].y), f2ord(hi[u].z)};
+            for (int a = 0; a < 3; a++) {
+                if (!(ext[a] > 0.f)) continue;  // the same for every lane
+                const int b = sah_bin(cen[a], clo[a], scale[a]);
+                const unsigned int grp = __match_any_sync(act, b);
+                const unsigned int tsum = __reduce_add_sync(grp, nt);
+                unsigned int r[6];
+                for (int d = 0; d < 3; d++)
+                    r[d] = __reduce_min_sync(grp, o[d]), r[3 + d] = __reduce_max_sync(grp, o[3 + d]);
+                if (lane == __ffs(grp) - 1) {
+                    atomicAdd(&sb.tri[a][b], tsum);
+                    atomicAdd(&sb.cel[a][b], (unsigned int)__popc(grp));
+                    for (int d = 0; d < 3; d++) atomicMin(&sb.lo[a][b][d], r[d]), atomicMax(&sb.hi[a][b][d], r[3 + d]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // SAH at the bin boundaries: a warp evaluates an axis, lane l the boundary after bin l
+    for (int a = warp; a < 3; a += T / 32) {
+        const bool in = lane < SAH_BINS && ext[a] > 0.f;
+        float pl[3], ph[3], ql[3], qh[3];
+        unsigned int pt = 0u, pc = 0u, qt = 0u;
+        for (int d = 0; d < 3; d++) {
+            pl[d] = in ? ord2f(sb.lo[a][lane][d]) : INFINITY;
+            ph[d] = in ? ord2f(sb.hi[a][lane][d]) : -INFINITY;
+            ql[d] = pl[d];
+            qh[d] = ph[d];
+        }
+        if (in) pt = qt = sb.tri[a][lane], pc = sb.cel[a][lane];
+        warp_prefix_suffix(lane, pl, ph, pt, pc, ql, qh, qt);
+        // the right side of boundary l is the suffix from bin l + 1
+        const unsigned int rt = __shfl_down_sync(0xffffffffu, qt, 1);
+        float rl[3], rh[3];
+        for (int d = 0; d < 3; d++)
+            rl[d] = __shfl_down_sync(0xffffffffu, ql[d], 1), rh[d] = __shfl_down_sync(0xffffffffu, qh[d], 1);
+        float cost = INFINITY;
+        if (in && lane < SAH_BINS - 1 && pt > 0u && rt > 0u)
+            cost = box_area(pl[0], pl[1], pl[2], ph[0], ph[1], ph[2]) * (float)pt +
+                   box_area(rl[0], rl[1], rl[2], rh[0], rh[1], rh[2]) * (float)rt;
+        const float best = warp_min(cost);
+        const unsigned int at = __ballot_sync(0xffffffffu, cost == best && best < INFINITY);
+        const int bl = at ? __ffs(at) - 1 : -1;
+        const unsigned int left_cells = __shfl_sync(0xffffffffu, pc, bl < 0 ? 0 : bl);
+        if (lane == 0) {
+            sb.cost[a] = bl < 0 ? INFINITY : best;
+            sb.split[a] = bl;
+            sb.nl[a] = left_cells;
+        }
+    }
+    __syncthreads();
+    axis = -1;
+    float bc = INFINITY;
+    for (int a = 0; a < 3; a++)
+        if (sb.split[a] >= 0 && sb.cost[a] < bc) bc = sb.cost[a], axis = a;
+    split = axis < 0 ? 0 : sb.split[axis];
+    nl = axis < 0 ? n / 2 : sb.nl[axis];  // all centres equal: split in the middle
+}
+
+// one level: one block per segment (T threads: segments of more than SAH_MID
+// cells, or of SAH_SMALL + 1 to SAH_MID cells when MID)
+template <int T, bool MID>
+__global__ void __launch_bounds__(T)
     k_sah_level(int level, bool last_level, SahLists li, const uint32_t* __restrict__ top_idx,
                 const uint32_t* __restrict__ n_top_p, int64_t M, int32_t* __restrict__ left,
                 int32_t* __restrict__ right, int32_t* __restrict__ first, int32_t* __restrict__ last,
                 int32_t* __restrict__ pint, int32_t* __restrict__ pleaf, float4* __restrict__ node_box,
                 BuildMeta* meta) {
-    constexpr int NW = SAH_THREADS / 32, T = SAH_THREADS, U = SAH_UNROLL;
-    __shared__ unsigned int s_lo[3][SAH_BINS][3], s_hi[3][SAH_BINS][3];  // bin boxes, order-preserving bits
-    __shared__ unsigned int s_tri[3][SAH_BINS], s_cel[3][SAH_BINS];
+    constexpr int NW = T / 32, U = SAH_UNROLL;
+    __shared__ SahBins sb;
     __shared__ float s_red[NW][12];
     __shared__ float s_b[12];  // node box lo, hi; centre bounds lo, hi
-    __shared__ float s_cost[3];
-    __shared__ int s_split[3];
-    __shared__ unsigned int s_nl[3];
     __shared__ unsigned int s_wl[U][NW], s_wr[U][NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint32_t n_seg = li.counts[level];
+    const uint32_t n_seg = MID ? li.counts_mid[level] : li.counts[level];
+    const SahSeg* seg_in = MID ? li.mid_in : li.seg_in;
     const uint32_t n_top = *n_top_p;
     for (uint32_t si = blockIdx.x; si < n_seg; si += gridDim.x) {
-        const SahSeg sg = li.seg_in[si];
+        const SahSeg sg = seg_in[si];
         const CellRec* rin = sg.buf ? li.rec1 : li.rec0;
         CellRec* rout = sg.buf ? li.rec0 : li.rec1;
         const uint32_t n = sg.end - sg.begin;
@@ -302,11 +408,6 @@ __global__ void __launch_bounds__(SAH_THREADS)
         for (int k = 0; k < 12; k++) v[k] = (k % 6) < 3 ? warp_min(v[k]) : warp_max(v[k]);
         if (lane == 0)
             for (int k = 0; k < 12; k++) s_red[warp][k] = v[k];
-        for (int t = tid; t < 3 * SAH_BINS; t += T) {  // empty bins
-            const int k = t / SAH_BINS, b = t % SAH_BINS;
-            s_tri[k][b] = s_cel[k][b] = 0u;
-            for (int d = 0; d < 3; d++) s_lo[k][b][d] = f2ord(INFINITY), s_hi[k][b][d] = f2ord(-INFINITY);
-        }
         __syncthreads();
         if (tid < 12) {
             float r = s_red[0][tid];
@@ -326,89 +427,12 @@ __global__ void __launch_bounds__(SAH_THREADS)
             first[parent_i] = 0;  // kept by the 4-wide collapse
             last[parent_i] = (int32_t)(M - 1);
         }
-        // pass 2: bins of the three axes (triangles for the cost, cells for the
-        // partition).  Cells in Morton order are neighbours, so a warp's cells
-        // mostly share bins: the lanes of one bin combine their values first
-        // and one of them updates the bin.
         const bool sampled = n > (uint32_t)SAH_SAMPLE;
-        const uint32_t nb = sampled ? (uint32_t)SAH_SAMPLE : n;
-        for (uint32_t i0 = tid; i0 < nb + (uint32_t)tid; i0 += T * U) {
-            float4 lo[U], hi[U];
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                const uint32_t i = i0 + u * T;
-                const uint32_t k = sg.begin + (sampled ? (uint32_t)(((uint64_t)i * n) / SAH_SAMPLE) : i);
-                if (i < nb) lo[u] = rin[k].lo, hi[u] = rin[k].hi;
-            }
-#pragma unroll
-            for (int u = 0; u < U; u++) {
-                const bool inr = i0 + u * T < nb;
-                const unsigned int act = __ballot_sync(0xffffffffu, inr);
-                if (!inr) continue;
-                const float cen[3] = {0.5f * (lo[u].x + hi[u].x), 0.5f * (lo[u].y + hi[u].y),
-                                      0.5f * (lo[u].z + hi[u].z)};
-                const unsigned int nt = (unsigned int)__float_as_int(hi[u].w);
-                const unsigned int o[6] = {f2ord(lo[u].x), f2ord(lo[u].y), f2ord(lo[u].z),
-                                           f2ord(hi[u].x), f2ord(hi[u].y), f2ord(hi[u].z)};
-                for (int a = 0; a < 3; a++) {
-                    if (!(ext[a] > 0.f)) continue;  // the same for every lane
-                    const int b = sah_bin(cen[a], clo[a], scale[a]);
-                    const unsigned int grp = __match_any_sync(act, b);
-                    const unsigned int tsum = __reduce_add_sync(grp, nt);
-                    unsigned int r[6];
-                    for (int d = 0; d < 3; d++)
-                        r[d] = __reduce_min_sync(grp, o[d]), r[3 + d] = __reduce_max_sync(grp, o[3 + d]);
-                    if (lane == __ffs(grp) - 1) {
-                        atomicAdd(&s_tri[a][b], tsum);
-                        atomicAdd(&s_cel[a][b], (unsigned int)__popc(grp));
-                        for (int d = 0; d < 3; d++) atomicMin(&s_lo[a][b][d], r[d]), atomicMax(&s_hi[a][b][d], r[3 + d]);
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // SAH at the bin boundaries: warp a evaluates axis a, lane l the boundary after bin l
-        if (warp < 3) {
-            const int a = warp;
-            const bool in = lane < SAH_BINS && ext[a] > 0.f;
-            float pl[3], ph[3], ql[3], qh[3];
-            unsigned int pt = 0u, pc = 0u, qt = 0u;
-            for (int d = 0; d < 3; d++) {
-                pl[d] = in ? ord2f(s_lo[a][lane][d]) : INFINITY;
-                ph[d] = in ? ord2f(s_hi[a][lane][d]) : -INFINITY;
-                ql[d] = pl[d];
-                qh[d] = ph[d];
-            }
-            if (in) pt = qt = s_tri[a][lane], pc = s_cel[a][lane];
-            warp_prefix_suffix(lane, pl, ph, pt, pc, ql, qh, qt);
-            // the right side of boundary l is the suffix from bin l + 1
-            const unsigned int rt = __shfl_down_sync(0xffffffffu, qt, 1);
-            float rl[3], rh[3];
-            for (int d = 0; d < 3; d++)
-                rl[d] = __shfl_down_sync(0xffffffffu, ql[d], 1), rh[d] = __shfl_down_sync(0xffffffffu, qh[d], 1);
-            float cost = INFINITY;
-            if (in && lane < SAH_BINS - 1 && pt > 0u && rt > 0u)
-                cost = box_area(pl[0], pl[1], pl[2], ph[0], ph[1], ph[2]) * (float)pt +
-                       box_area(rl[0], rl[1], rl[2], rh[0], rh[1], rh[2]) * (float)rt;
-            const float best = warp_min(cost);
-            const unsigned int at = __ballot_sync(0xffffffffu, cost == best && best < INFINITY);
-            const int bl = at ? __ffs(at) - 1 : -1;
-            const unsigned int nl = __shfl_sync(0xffffffffu, pc, bl < 0 ? 0 : bl);
-            if (lane == 0) {
-                s_cost[a] = bl < 0 ? INFINITY : best;
-                s_split[a] = bl;
-                s_nl[a] = nl;
-            }
-        }
-        __syncthreads();
-        int axis = -1;
-        float bc = INFINITY;
-        for (int a = 0; a < 3; a++)
-            if (s_split[a] >= 0 && s_cost[a] < bc) bc = s_cost[a], axis = a;
-        const int split = axis < 0 ? 0 : s_split[axis];
+        int axis, split;
+        uint32_t nL;
+        sah_choose<T>(sb, rin, sg.begin, n, clo, ext, scale, axis, split, nL);
         const float alo = axis < 0 ? 0.f : clo[axis], asc = axis < 0 ? 0.f : scale[axis];
         // the left side's cells: from the bins, or counted when they held a sample
-        uint32_t nL = axis < 0 ? n / 2 : s_nl[axis];  // all centres equal: split in the middle
         if (sampled && axis >= 0) {
             uint32_t cnt = 0;
             for (uint32_t k0 = sg.begin + tid; k0 < sg.end; k0 += T * U) {
@@ -497,10 +521,7 @@ __global__ void __launch_bounds__(SAH_THREADS)
                     if (c.end - c.begin < 2) continue;  // a single cell: linked above
                     c.node = (int32_t)(side ? c.begin : c.end - 1);
                     if ((uint32_t)c.node >= n_top) continue;  // reported by sah_link
-                    if (!last_level && c.end - c.begin > (uint32_t)SAH_SMALL)
-                        li.seg_next[atomicAdd(&li.counts[level + 1], 1u)] = c;
-                    else
-                        li.seg_small[atomicAdd(&li.counts[SAH_LEVELS], 1u)] = c;
+                    sah_queue(li, level, last_level, c);
                 }
             }
         }
@@ -651,6 +672,321 @@ __global__ void __launch_bounds__(256)
             stack[sp++] = L;
         }
         if (sp > 0 && lane == 0) atomicAdd(&meta->sah_error, 1u);  // iteration bound reached
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Wide segments.  The first levels hold few segments of many cells, which one
+// block each would stream through one SM.  A segment of more than WIDE_MIN
+// cells in the first WIDE_LEVELS levels is split by the whole grid instead,
+// in chunks of WIDE_CHUNK cells: its bounds (ordered atomics per segment),
+// its split (one block per segment, on the sample sah_choose takes), the
+// left count of every chunk, a stable scatter whose offsets sum the counts of
+// the segment's earlier chunks, and its children (one thread per segment).
+// ---------------------------------------------------------------------------
+static constexpr int WIDE_MIN = 16384;
+static constexpr int WIDE_LEVELS = 5;
+static constexpr int WIDE_CHUNK = 4096;
+static constexpr int WIDE_THREADS = 256;
+
+struct SahWide {
+    SahSeg *in, *next;          // this level's wide segments, the next level's
+    uint32_t* counts;           // [WIDE_LEVELS + 1] wide segments per level
+    unsigned int *bin, *bnext;  // [cap][12] bounds of this level's and of the next level's segments:
+                                // box lo, box hi, centre lo, centre hi (order-preserving bits)
+    int4* split;                // [cap] axis, split bin, centre lo on the axis, bin scale (float bits)
+    uint32_t* chunk_left;       // [chunks] left cells of every chunk of this level
+    uint32_t cap;               // entries of in, next, bin, bnext, split
+};
+
+__device__ __forceinline__ void wide_bounds_init(unsigned int* b) {
+    for (int k = 0; k < 12; k++) b[k] = (k % 6) < 3 ? f2ord(INFINITY) : f2ord(-INFINITY);
+}
+
+// the wide segment holding global chunk g, the index of its first chunk and
+// the chunk's first cell; false past the last chunk of the level
+__device__ __forceinline__ bool wide_chunk(const SahSeg* in, uint32_t n_wide, uint32_t g, uint32_t& s,
+                                           uint32_t& first_chunk, uint32_t& c0) {
+    uint32_t acc = 0;
+    for (uint32_t k = 0; k < n_wide; k++) {
+        const uint32_t nch = (in[k].end - in[k].begin + WIDE_CHUNK - 1) / WIDE_CHUNK;
+        if (g < acc + nch) {
+            s = k;
+            first_chunk = acc;
+            c0 = in[k].begin + (g - acc) * WIDE_CHUNK;
+            return true;
+        }
+        acc += nch;
+    }
+    return false;
+}
+
+// the side a cell goes to: by its centre's bin, or by position when every centre is equal
+__device__ __forceinline__ bool wide_left(const int4& sp, const CellRec& r, uint32_t k, const SahSeg& sg) {
+    if (sp.x < 0) return k - sg.begin < (sg.end - sg.begin) / 2;
+    const float cen = sp.x == 0 ? 0.5f * (r.lo.x + r.hi.x) : (sp.x == 1 ? 0.5f * (r.lo.y + r.hi.y) : 0.5f * (r.lo.z + r.hi.z));
+    return sah_bin(cen, __int_as_float(sp.z), __int_as_float(sp.w)) <= sp.y;
+}
+
+// bounds of every wide segment, one block per chunk
+__global__ void __launch_bounds__(WIDE_THREADS)
+    k_wide_bounds(int level, SahWide w, const CellRec* __restrict__ rec0, const CellRec* __restrict__ rec1) {
+    constexpr int NW = WIDE_THREADS / 32;
+    __shared__ float s_red[NW][12];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t n_wide = w.counts[level];
+    for (uint32_t g = blockIdx.x;; g += gridDim.x) {
+        uint32_t s, fc, c0;
+        if (!wide_chunk(w.in, n_wide, g, s, fc, c0)) break;  // the same for the whole block
+        const SahSeg sg = w.in[s];
+        const CellRec* rin = sg.buf ? rec1 : rec0;
+        const uint32_t c1 = min(c0 + (uint32_t)WIDE_CHUNK, sg.end);
+        float v[12];
+        for (int k = 0; k < 3; k++) v[k] = v[6 + k] = INFINITY, v[3 + k] = v[9 + k] = -INFINITY;
+        for (uint32_t k = c0 + tid; k < c1; k += WIDE_THREADS) {
+            const float4 lo = rin[k].lo, hi = rin[k].hi;
+            const float cx = 0.5f * (lo.x + hi.x), cy = 0.5f * (lo.y + hi.y), cz = 0.5f * (lo.z + hi.z);
+            v[0] = fminf(v[0], lo.x), v[1] = fminf(v[1], lo.y), v[2] = fminf(v[2], lo.z);
+            v[3] = fmaxf(v[3], hi.x), v[4] = fmaxf(v[4], hi.y), v[5] = fmaxf(v[5], hi.z);
+            v[6] = fminf(v[6], cx), v[7] = fminf(v[7], cy), v[8] = fminf(v[8], cz);
+            v[9] = fmaxf(v[9], cx), v[10] = fmaxf(v[10], cy), v[11] = fmaxf(v[11], cz);
+        }
+        for (int k = 0; k < 12; k++) v[k] = (k % 6) < 3 ? warp_min(v[k]) : warp_max(v[k]);
+        if (lane == 0)
+            for (int k = 0; k < 12; k++) s_red[warp][k] = v[k];
+        __syncthreads();
+        if (tid < 12) {
+            float r = s_red[0][tid];
+            for (int q = 1; q < NW; q++) r = (tid % 6) < 3 ? fminf(r, s_red[q][tid]) : fmaxf(r, s_red[q][tid]);
+            if ((tid % 6) < 3)
+                atomicMin(&w.bin[12 * s + tid], f2ord(r));
+            else
+                atomicMax(&w.bin[12 * s + tid], f2ord(r));
+        }
+        __syncthreads();
+    }
+}
+
+// the split of every wide segment, one block per segment (its SAH_SAMPLE
+// samples in one round of loads); writes the node's box
+static constexpr int WIDE_DECIDE_THREADS = 1024;
+__global__ void __launch_bounds__(WIDE_DECIDE_THREADS)
+    k_wide_decide(int level, SahWide w, const CellRec* __restrict__ rec0, const CellRec* __restrict__ rec1,
+                  const uint32_t* __restrict__ top_idx, int64_t M, int32_t* __restrict__ first,
+                  int32_t* __restrict__ last, float4* __restrict__ node_box) {
+    __shared__ SahBins sb;
+    const uint32_t n_wide = w.counts[level];
+    for (uint32_t si = blockIdx.x; si < n_wide; si += gridDim.x) {
+        const SahSeg sg = w.in[si];
+        const CellRec* rin = sg.buf ? rec1 : rec0;
+        const unsigned int* b = w.bin + 12 * si;
+        float clo[3], ext[3], scale[3];
+        for (int k = 0; k < 3; k++) {
+            clo[k] = ord2f(b[6 + k]);
+            ext[k] = ord2f(b[9 + k]) - clo[k];
+            scale[k] = ext[k] > 0.f ? (float)SAH_BINS / ext[k] : 0.f;
+        }
+        const int pi = (int)top_idx[sg.node];
+        if (threadIdx.x == 0) {
+            node_box[2 * (int64_t)pi] = make_float4(ord2f(b[0]), ord2f(b[1]), ord2f(b[2]), 0.f);
+            node_box[2 * (int64_t)pi + 1] = make_float4(ord2f(b[3]), ord2f(b[4]), ord2f(b[5]), 0.f);
+            first[pi] = 0;  // kept by the 4-wide collapse
+            last[pi] = (int32_t)(M - 1);
+        }
+        int axis, split;
+        uint32_t nl;
+        sah_choose<WIDE_DECIDE_THREADS>(sb, rin, sg.begin, sg.end - sg.begin, clo, ext, scale, axis, split, nl);
+        if (threadIdx.x == 0)
+            w.split[si] = make_int4(axis, split, __float_as_int(axis < 0 ? 0.f : clo[axis]),
+                                    __float_as_int(axis < 0 ? 0.f : scale[axis]));
+        __syncthreads();
+    }
+}
+
+// the left cells of every chunk
+__global__ void __launch_bounds__(WIDE_THREADS)
+    k_wide_count(int level, SahWide w, const CellRec* __restrict__ rec0, const CellRec* __restrict__ rec1) {
+    constexpr int NW = WIDE_THREADS / 32;
+    __shared__ uint32_t s_cnt[NW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t n_wide = w.counts[level];
+    for (uint32_t g = blockIdx.x;; g += gridDim.x) {
+        uint32_t s, fc, c0;
+        if (!wide_chunk(w.in, n_wide, g, s, fc, c0)) break;
+        const SahSeg sg = w.in[s];
+        const CellRec* rin = sg.buf ? rec1 : rec0;
+        const int4 sp = w.split[s];
+        const uint32_t c1 = min(c0 + (uint32_t)WIDE_CHUNK, sg.end);
+        uint32_t cnt = 0;
+        for (uint32_t k = c0 + tid; k < c1; k += WIDE_THREADS) {
+            const CellRec r = rin[k];
+            cnt += wide_left(sp, r, k, sg) ? 1u : 0u;
+        }
+        cnt = __reduce_add_sync(0xffffffffu, cnt);
+        if (lane == 0) s_cnt[warp] = cnt;
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t t = 0;
+            for (int q = 0; q < NW; q++) t += s_cnt[q];
+            w.chunk_left[g] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// stable partition of every wide segment into the other record array, one
+// block per chunk: its left cells follow the left cells of the segment's
+// earlier chunks, its right cells those of their right cells
+__global__ void __launch_bounds__(WIDE_THREADS)
+    k_wide_scatter(int level, SahWide w, CellRec* __restrict__ rec0, CellRec* __restrict__ rec1, BuildMeta* meta) {
+    constexpr int NW = WIDE_THREADS / 32;
+    __shared__ uint32_t s_wl[NW], s_wr[NW];
+    __shared__ uint32_t s_base[2];  // left cells of the earlier chunks, of the whole segment
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t n_wide = w.counts[level];
+    for (uint32_t g = blockIdx.x;; g += gridDim.x) {
+        uint32_t s, fc, c0;
+        if (!wide_chunk(w.in, n_wide, g, s, fc, c0)) break;
+        const SahSeg sg = w.in[s];
+        const CellRec* rin = sg.buf ? rec1 : rec0;
+        CellRec* rout = sg.buf ? rec0 : rec1;
+        const int4 sp = w.split[s];
+        const uint32_t c1 = min(c0 + (uint32_t)WIDE_CHUNK, sg.end);
+        if (tid == 0) {
+            const uint32_t nch = (sg.end - sg.begin + WIDE_CHUNK - 1) / WIDE_CHUNK;
+            uint32_t before = 0, total = 0;
+            for (uint32_t j = 0; j < nch; j++) {
+                const uint32_t c = w.chunk_left[fc + j];
+                if (fc + j < g) before += c;
+                total += c;
+            }
+            s_base[0] = before;
+            s_base[1] = total;
+        }
+        __syncthreads();
+        const uint32_t nL = s_base[1];
+        uint32_t lb = sg.begin + s_base[0];                        // next left slot
+        uint32_t rb = sg.begin + nL + (c0 - sg.begin) - s_base[0];  // next right slot
+        for (uint32_t r0 = c0; r0 < c1; r0 += WIDE_THREADS) {
+            const uint32_t k = r0 + tid;
+            const bool inr = k < c1;
+            CellRec r;
+            bool p = false;
+            if (inr) {
+                r = rin[k];
+                p = wide_left(sp, r, k, sg);
+            }
+            const bool q = inr && !p;
+            const unsigned int wl = __ballot_sync(0xffffffffu, p), wr = __ballot_sync(0xffffffffu, q);
+            if (lane == 0) s_wl[warp] = __popc(wl), s_wr[warp] = __popc(wr);
+            __syncthreads();
+            uint32_t offl = 0, offr = 0, totl = 0, totr = 0;
+            for (int x = 0; x < NW; x++) {
+                if (x < warp) offl += s_wl[x], offr += s_wr[x];
+                totl += s_wl[x], totr += s_wr[x];
+            }
+            const unsigned int below = (1u << lane) - 1u;
+            const uint32_t dl = lb + offl + __popc(wl & below), dr = rb + offr + __popc(wr & below);
+            // each side stays inside its part of the segment even if a count disagreed
+            if (p) {
+                if (dl < sg.begin + nL)
+                    rout[dl] = r;
+                else
+                    atomicAdd(&meta->sah_error, 1u);
+            }
+            if (q) {
+                if (dr >= sg.begin + nL && dr < sg.end)
+                    rout[dr] = r;
+                else
+                    atomicAdd(&meta->sah_error, 1u);
+            }
+            lb += totl;
+            rb += totr;
+            __syncthreads();
+        }
+    }
+}
+
+// the children of every wide segment, one thread per segment: links, and the
+// queues of the next level (wide or not) or of the warp kernel
+__global__ void k_wide_children(int level, SahWide w, SahLists li, const uint32_t* __restrict__ top_idx,
+                                const uint32_t* __restrict__ n_top_p, int64_t M, int32_t* __restrict__ left,
+                                int32_t* __restrict__ right, int32_t* __restrict__ pint, int32_t* __restrict__ pleaf,
+                                BuildMeta* meta) {
+    const uint32_t n_wide = w.counts[level];
+    const uint32_t n_top = *n_top_p;
+    uint32_t fc = 0;
+    for (uint32_t si = 0; si < n_wide; si++) {  // one thread: few segments, and fc runs through them
+        const SahSeg sg = w.in[si];
+        const uint32_t n = sg.end - sg.begin, nch = (n + WIDE_CHUNK - 1) / WIDE_CHUNK;
+        uint32_t nL = 0;
+        for (uint32_t j = 0; j < nch; j++) nL += w.chunk_left[fc + j];
+        fc += nch;
+        if (nL == 0 || nL >= n) {
+            atomicAdd(&meta->sah_error, 1u);
+            continue;
+        }
+        const CellRec* rout = sg.buf ? li.rec0 : li.rec1;
+        const int pi = (int)top_idx[sg.node];
+        const int32_t sl = __float_as_int(rout[sg.begin].lo.w), sr = __float_as_int(rout[sg.begin + nL].lo.w);
+        left[pi] = sah_link(true, sg.begin, sg.begin + nL, pi, sl, top_idx, n_top, M, pint, pleaf, meta);
+        right[pi] = sah_link(false, sg.begin + nL, sg.end, pi, sr, top_idx, n_top, M, pint, pleaf, meta);
+        SahSeg c;
+        c.depth = (int16_t)(sg.depth + 1);
+        c.buf = (int16_t)(1 - sg.buf);
+        for (int side = 0; side < 2; side++) {
+            c.begin = side ? sg.begin + nL : sg.begin;
+            c.end = side ? sg.end : sg.begin + nL;
+            if (c.end - c.begin < 2) continue;  // a single cell: linked above
+            c.node = (int32_t)(side ? c.begin : c.end - 1);
+            if ((uint32_t)c.node >= n_top) continue;  // reported by sah_link
+            const uint32_t m = c.end - c.begin;
+            if (m > (uint32_t)WIDE_MIN && level + 1 < WIDE_LEVELS) {
+                const uint32_t slot = atomicAdd(&w.counts[level + 1], 1u);
+                if (slot >= w.cap) {
+                    atomicAdd(&meta->sah_error, 1u);
+                    continue;
+                }
+                w.next[slot] = c;
+                wide_bounds_init(w.bnext + 12 * slot);
+            } else {
+                sah_queue(li, level, false, c);
+            }
+        }
+    }
+}
+
+
+// the root segment when there are at least two cells (queued for the grid-wide
+// kernels when it has more than WIDE_MIN cells); a top-node count other than
+// C - 1 is reported and nothing is built
+__global__ void k_sah_init(const uint32_t* __restrict__ n_cells_p, const uint32_t* __restrict__ n_top_p,
+                           SahLists li, SahWide w, BuildMeta* meta) {
+    const uint32_t C = *n_cells_p;
+    if (C < 2) return;
+    if (*n_top_p != C - 1) {
+        atomicAdd(&meta->sah_error, 1u);
+        return;
+    }
+    SahSeg s;
+    s.begin = 0;
+    s.end = C;
+    s.node = 0;
+    s.depth = 0;
+    s.buf = 0;
+    if (C > (uint32_t)WIDE_MIN) {
+        w.in[0] = s;
+        w.counts[0] = 1u;
+        wide_bounds_init(w.bin);
+    } else if (C > (uint32_t)SAH_MID) {
+        li.seg_in[0] = s;
+        li.counts[0] = 1u;
+    } else if (C > (uint32_t)SAH_SMALL) {
+        li.mid_in[0] = s;
+        li.counts_mid[0] = 1u;
+    } else {
+        li.seg_small[0] = s;
+        li.counts[SAH_LEVELS] = 1u;
     }
 }
 
