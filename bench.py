@@ -20,8 +20,8 @@ e2e        the same metric through the C ABI from pinned host buffers: mesh
 roofline   the bounce kernel's algorithmic L2-path bytes over its live
            duration, against the L2 read bandwidth measured in the same run
            (MEASURED_PEAKS.json has no L2 figure); HBM fraction beside it.
-           Bytes per query: 64 B per tree node visited and 48 B per
-           triangle tested (the survey's accounting), counted by an
+           Bytes per query: 64 B per tree node visited (a binary node's
+           two child boxes) and 48 B per triangle tested, counted by an
            instrumented pass; the kernel's own 4-wide nodes read 112 B per
            visit, reported beside it as "achieved_wide".
 surrogate  the metric's second half: RIRs/s of the surrogate-tail pipeline

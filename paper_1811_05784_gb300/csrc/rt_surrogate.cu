@@ -1,6 +1,6 @@
 // rt_surrogate.cu -- surrogate-tail mode: the learned late reverberation
 // behind the C ABI (no counterpart in the paper; the method itself stays the
-// fallback and the judge).
+// fallback and the reference the predictions are measured against).
 //
 // A room (one source, one receiver sphere) is traced twice with few rays: a
 // 0-50 ms trace (1 ms bins) and a 2 s tail probe (10 ms bins).  With the
