@@ -146,3 +146,14 @@ def test_binding_rejects_host_tensors_and_short_buffers_before_any_call():
     for bad in (np.zeros(79, np.float32), np.zeros(80, np.float64), torch.zeros(79)):
         with pytest.raises(ValueError):
             _Response().download(out=bad)
+
+
+def test_tree_builder_flags_exclude_each_other_before_any_call():
+    """rt_build_tree builds the LBVH, the paper's median-split tree or the
+    LBVH with SAH top levels; asking for two at once raises ValueError before
+    the library is reached (it need not even be built)."""
+    import numpy as np
+    from paper_1811_05784_gb300 import rt
+    V = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    with pytest.raises(ValueError):
+        rt.rt_build_tree(V, np.array([[0, 1, 2]], np.int32), np.zeros(1, np.int32), median=True, sah=True)
